@@ -1,0 +1,121 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module is shared by the tests, the CUDA-path binding's callers and the oracle's
+callers.  It holds none of the method's arithmetic: it only builds input matrices A
+(four real component planes) and names the sketch sizes of each workload.  The random
+test matrices Omega and Psi are NOT drawn here: each side draws them from the published
+Philox4x32-10 definition.
+
+Quaternion matrices are numpy arrays of shape (4, rows, cols) (planes w, x, y, z).
+
+Workloads (sizes from the paper's experiments, Sec. 5; synthetic stand-ins for data sets
+that are not available):
+  c1  512 x 384, FP64: A = U diag(0.5^i, i<=10) V* + 1e-6 E with quaternion Gaussian
+      factors U (512x10), V (384x10) whose planes are N(0, 1/4) and noise E of the same
+      law; k=10, s=21, l=43; Gaussian embeddings.
+  c2  8192 x 8192, FP32: A = U diag(i^-2) V* with random quaternion-orthonormal U, V;
+      the spectrum is truncated at R = 1024 (sigma_R = 9.5e-7; the dropped tail is
+      1.7e-5 of ||A||_F); k=50, s=101, l=203; Gaussian embeddings.
+Random quaternion-orthonormal factors are built as U = D Q W: Q real orthonormal (QR of a
+real Gaussian), W the unitary polar factor of an R x R quaternion Gaussian (from the
+eigendecomposition of its Hermitian complex form), D a diagonal of random unit
+quaternions.  Each factor is unitary, hence so is the product.
+"""
+import numpy as np
+
+WORKLOADS = {
+    "c1": dict(m=512, n=384, k=10, s=21, l=43, precision="fp64", emb="gaussian", seed=0),
+    "c2": dict(m=8192, n=8192, k=50, s=101, l=203, precision="bf16x3", emb="gaussian",
+               seed=0, rank_cap=1024),
+}
+
+
+def _qmul_planes(P, Q):
+    # entrywise product of quaternion arrays (broadcasting), used only to apply the
+    # unit-quaternion diagonal when building inputs
+    pw, px, py, pz = P
+    qw, qx, qy, qz = Q
+    return np.stack([pw * qw - px * qx - py * qy - pz * qz,
+                     pw * qx + px * qw + py * qz - pz * qy,
+                     pw * qy - px * qz + py * qw + pz * qx,
+                     pw * qz + px * qy - py * qx + pz * qw])
+
+
+def _unitary_quaternion(rng, R):
+    """Polar factor of an R x R quaternion Gaussian G: W = G (G*G)^{-1/2}, computed on the
+    2R x 2R complex form [[G0, G1], [-conj G1, conj G0]]; W is read back from its first
+    block column."""
+    G = rng.standard_normal((4, R, R))
+    G0, G1 = G[0] + 1j * G[1], G[2] + 1j * G[3]
+    C = np.block([[G0, G1], [-np.conj(G1), np.conj(G0)]])
+    lam, V = np.linalg.eigh(C.conj().T @ C)
+    P = C @ (V * (1.0 / np.sqrt(lam))[None, :]) @ V.conj().T
+    W0, W1 = P[:R, :R], P[:R, R:]
+    return np.stack([W0.real, W0.imag, W1.real, W1.imag])
+
+
+def random_orthonormal(rng, m, R):
+    """Random m x R quaternion matrix with orthonormal columns, U = D Q W."""
+    Q, _ = np.linalg.qr(rng.standard_normal((m, R)))
+    W = _unitary_quaternion(rng, R)
+    QW = np.stack([Q @ W[p] for p in range(4)])
+    d = rng.standard_normal((4, m, 1))
+    d /= np.sqrt(np.sum(d * d, axis=0, keepdims=True))
+    return _qmul_planes(d, QW)
+
+
+def _assemble(U, sigma, V, device=None, dtype=np.float64):
+    """A = U diag(sigma) V* (quaternion).  With a torch ``device`` the product runs there in
+    FP64 (untimed input construction); otherwise in numpy."""
+    Us = U * sigma[None, None, :]
+    Vt = np.stack([V[0].T, -V[1].T, -V[2].T, -V[3].T])
+    if device is not None:
+        import torch
+        a = torch.as_tensor(Us, device=device)
+        b = torch.as_tensor(Vt, device=device)
+        w = a[0] @ b[0] - a[1] @ b[1] - a[2] @ b[2] - a[3] @ b[3]
+        x = a[0] @ b[1] + a[1] @ b[0] + a[2] @ b[3] - a[3] @ b[2]
+        y = a[0] @ b[2] - a[1] @ b[3] + a[2] @ b[0] + a[3] @ b[1]
+        z = a[0] @ b[3] + a[1] @ b[2] - a[2] @ b[1] + a[3] @ b[0]
+        tdt = torch.float64 if dtype == np.float64 else torch.float32
+        return torch.stack([w, x, y, z]).to(tdt).contiguous()
+    Aw = Us[0] @ Vt[0] - Us[1] @ Vt[1] - Us[2] @ Vt[2] - Us[3] @ Vt[3]
+    Ax = Us[0] @ Vt[1] + Us[1] @ Vt[0] + Us[2] @ Vt[3] - Us[3] @ Vt[2]
+    Ay = Us[0] @ Vt[2] - Us[1] @ Vt[3] + Us[2] @ Vt[0] + Us[3] @ Vt[1]
+    Az = Us[0] @ Vt[3] + Us[1] @ Vt[2] - Us[2] @ Vt[1] + Us[3] @ Vt[0]
+    return np.stack([Aw, Ax, Ay, Az]).astype(dtype)
+
+
+def make_c1(seed=0, m=512, n=384, rank=10, noise=1e-6):
+    """c1: quaternion-Gaussian factors with N(0,1/4) planes, sigma_i = 0.5^i (i <= rank),
+    plus ``noise`` times a quaternion Gaussian with N(0,1/4) planes.  FP64."""
+    rng = np.random.default_rng(seed)
+    U = 0.5 * rng.standard_normal((4, m, rank))
+    V = 0.5 * rng.standard_normal((4, n, rank))
+    sigma = 0.5 ** np.arange(1, rank + 1)
+    A = _assemble(U, sigma, V)
+    return A + noise * 0.5 * rng.standard_normal((4, m, n))
+
+
+def make_decay(m, n, seed=0, rank_cap=1024, power=2.0, device=None, dtype=np.float32):
+    """c2-type: A = U diag(i^-power) V* with random quaternion-orthonormal U, V and the
+    spectrum truncated at R = min(m, n, rank_cap)."""
+    rng = np.random.default_rng(seed)
+    R = min(m, n, rank_cap)
+    U = random_orthonormal(rng, m, R)
+    V = random_orthonormal(rng, n, R)
+    sigma = np.arange(1, R + 1, dtype=np.float64) ** (-power)
+    return _assemble(U, sigma, V, device=device, dtype=dtype)
+
+
+def make_lowrank(m, n, rank, seed=0, dtype=np.float64):
+    """Exactly rank-``rank`` quaternion matrix (product of two quaternion Gaussians)."""
+    rng = np.random.default_rng(seed)
+    U = rng.standard_normal((4, m, rank))
+    V = rng.standard_normal((4, n, rank))
+    return _assemble(U, np.ones(rank), V, dtype=dtype)
+
+
+def make_gaussian(m, n, seed=0, dtype=np.float64):
+    """Quaternion Gaussian with N(0,1) planes."""
+    return np.random.default_rng(seed).standard_normal((4, m, n)).astype(dtype)
