@@ -1,0 +1,176 @@
+/*
+ * qsketch.h -- C ABI of the GB300 (sm_103a) one-pass randomized quaternion low-rank
+ * approximation library.
+ *
+ * The method (Chang & Yang, "Randomized large-scale quaternion matrix approximation:
+ * practical rangefinders and one-pass algorithm", arXiv 2404.14783):
+ *   Sec. 4.1, eq. (Y = A Omega, W = Psi A): one read of the quaternion matrix A (m x n)
+ *       forms the two sketches Y = A Omega (m x s) and W = Psi A (l x n), with random test
+ *       matrices Omega (n x s) and Psi (l x m), r <= s <= l <= min(m, n).
+ *   Sec. 3.1, Alg. 1 (pseudo-QR) and Sec. 3.2, Alg. 2 (pseudo-SVD): a rangefinder
+ *       H (m x s) with R(H) = R(Y), computed in complex arithmetic on the complex
+ *       representation of Y.
+ *   Alg. 3 (QB stage) with Alg. "QLEQ": X = (Psi H)^dagger W, so that A ~= H X.
+ *   Sec. 5: relative error ||A - H X||_F / ||A||_F.
+ *
+ * Storage conventions (every call):
+ *   - A quaternion matrix Q = Q_w + Q_x i + Q_y j + Q_z k is four real "planes"
+ *     Q_w, Q_x, Q_y, Q_z.  Each plane is row-major with a leading dimension in elements.
+ *   - All device memory is owned by the caller.  The library allocates no device memory:
+ *     the caller passes one workspace (size from qsketch_workspace_bytes) that holds
+ *     Omega, Psi, Y, W, H, X and all scratch; handles only point into it.  Host memory
+ *     is allocated only for the handle struct itself.
+ *   - Every call that takes a stream enqueues its work on that stream (a cudaStream_t
+ *     passed as void*; NULL is the legacy default stream) and returns without waiting
+ *     for the GPU, except qs_last_device_error, which synchronises the stream.
+ *   - Errors: arguments are validated on the host before any launch.  Conditions found
+ *     on the device (rank warning, NaN/Inf, bounded-wait expiry) are recorded in a
+ *     sticky status word inside the workspace and reported by qs_last_device_error.
+ *     No C++ exception crosses this interface.
+ *   - A handle is not thread-safe; calls on one handle must be ordered by the caller.
+ */
+#ifndef QSKETCH_H_
+#define QSKETCH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define QS_API __attribute__((visibility("default")))
+#else
+#define QS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qs_handle_s* qs_handle_t;
+
+typedef enum {
+  QS_OK = 0,
+  QS_ERR_INVALID = 1,     /* bad argument (sizes, pointers, alignment, enum values) */
+  QS_ERR_NOMEM = 2,       /* workspace smaller than qsketch_workspace_bytes() */
+  QS_ERR_CUDA = 3,        /* a CUDA runtime call failed (launch, copy, attribute) */
+  QS_ERR_RANK = 4,        /* warning: Y or Psi*H numerically rank deficient; the result is
+                             still defined (pseudo-QR skips its correction steps) */
+  QS_ERR_NUMERIC = 5,     /* NaN or Inf met in the data */
+  QS_ERR_TIMEOUT = 6,     /* a bounded device-side wait expired */
+  QS_ERR_UNSUPPORTED = 7  /* valid request that this build does not implement */
+} qs_status;
+
+/* Random test matrices (Sec. 4.3 and 4.4).  Both are drawn from Philox4x32-10 (Salmon
+ * et al., SC'11) keyed by the seed; the quaternion entry at row-major index e of the
+ * matrix on stream t uses counter (e mod 2^32, e div 2^32, t, 0) and its four words
+ * give the planes w, x, y, z.  Omega uses stream 1, Psi stream 2.
+ *   GAUSSIAN  : all planes i.i.d. N(0,1), Box-Muller on word pairs (x0,x1) and (x2,x3)
+ *               with u = (x + 1/2) 2^-32 (the standard quaternion Gaussian of Sec. 4.3).
+ *   RADEMACHER: plane p is +1 when bit 31 of word p is clear, else -1 (a quaternion
+ *               sub-Gaussian test matrix, Sec. 4.4; exact in BF16). */
+typedef enum { QS_EMB_GAUSSIAN = 0, QS_EMB_RADEMACHER = 1 } qs_embedding;
+
+/* Arithmetic of the sketch (Sec. 4.1 products).  A's planes are FP64 for QS_PREC_FP64
+ * and FP32 for all other modes.
+ *   FP64   : FP64 sketch, FP64 rangefinder and core.
+ *   FP32   : FP32 SIMT sketch (FP32 accumulation).
+ *   BF16   : tensor-core sketch, A and the test matrices rounded to BF16, FP32 accumulation.
+ *   BF16X3 : tensor-core sketch with a hi/lo BF16 split of A and of the test matrices;
+ *            the products hi*hi + lo*hi + hi*lo are accumulated in FP32 (lo*lo dropped). */
+typedef enum { QS_PREC_FP64 = 0, QS_PREC_FP32 = 1, QS_PREC_BF16 = 2, QS_PREC_BF16X3 = 3 } qs_precision;
+
+typedef enum { QS_RF_PSEUDO_QR = 0, QS_RF_PSEUDO_SVD = 1 } qs_rangefinder_kind;
+
+/* Objects readable through qsketch_get. */
+typedef enum {
+  QS_OBJ_Y = 0,      /* m x s sketch Y = A Omega                               */
+  QS_OBJ_W = 1,      /* l x n sketch W = Psi A                                 */
+  QS_OBJ_OMEGA = 2,  /* n x s test matrix                                      */
+  QS_OBJ_PSI = 3,    /* l x m test matrix                                      */
+  QS_OBJ_H = 4,      /* m x s rangefinder (after qrangefinder)                 */
+  QS_OBJ_X = 5,      /* s x n core factor (after qonepass_core)                */
+  QS_OBJ_PSIH = 6,   /* l x s product Psi H (after qonepass_core)              */
+  QS_OBJ_SCALARS = 7 /* 16 doubles: [0] last relative error, [1] kappa estimate of H,
+                        [2..4] correction parameters eps_1..eps_3, [5] pseudo-SVD bad
+                        pair count t, [6] shift used by Cholesky (0 if none) */
+} qs_object;
+
+/* Element types reported by qsketch_get. */
+typedef enum { QS_DT_F64 = 0, QS_DT_F32 = 1 } qs_dtype;
+
+typedef struct {
+  int64_t m, n;     /* A is m x n (quaternion)                                    */
+  int64_t s, l;     /* sketch sizes, 1 <= s <= l <= min(m, n) (Sec. 4, eq. sizes)  */
+  int32_t emb;      /* qs_embedding                                               */
+  int32_t prec;     /* qs_precision                                               */
+  uint64_t seed;    /* key of the counter-based generator                         */
+  int32_t pure;     /* 1: A_w == 0 (pure quaternion); plane w is never read        */
+  int32_t flags;    /* reserved, must be 0                                         */
+} qs_config;
+
+/* Bytes of device workspace qsketch_create needs for cfg (0 if cfg is invalid). */
+QS_API size_t qsketch_workspace_bytes(const qs_config* cfg);
+
+/* Validates cfg, carves the caller's workspace (device pointer, >= 256-byte aligned,
+ * >= qsketch_workspace_bytes(cfg) bytes), draws Omega and Psi (Sec. 4.1: drawn once,
+ * independently) on `stream`, zeroes Y and W, and returns a host handle in *out.
+ * The workspace must stay allocated until qsketch_destroy. */
+QS_API qs_status qsketch_create(const qs_config* cfg, void* workspace, size_t bytes, void* stream,
+                         qs_handle_t* out);
+
+/* Linear update of the sketches (Sec. 4, streaming by linear updates, after Tropp et al.):
+ * for the block A_b = A[row0:row0+mb, col0:col0+nb] given by the four device planes
+ * A_planes[0..3] (row-major, leading dimension lda >= nb; A_planes[0] may be NULL when
+ * cfg.pure), computes
+ *     Y <- theta Y + eta * E_r A_b Omega[col0:col0+nb, :]
+ *     W <- theta W + eta * Psi[:, row0:row0+mb] A_b E_c
+ * where E_r, E_c place the block's rows/columns.  theta = 0 overwrites (old contents
+ * are not read).  The planes are FP64 for QS_PREC_FP64, FP32 otherwise, 16-byte aligned
+ * with lda a multiple of 4 elements for the tensor-core modes. */
+QS_API qs_status qsketch_update(qs_handle_t h, const void* const A_planes[4], int64_t lda,
+                         int64_t row0, int64_t col0, int64_t mb, int64_t nb,
+                         double theta, double eta, void* stream);
+
+/* Rangefinder H = F(Y) with R(H) = R(Y) (Sec. 3).
+ *   QS_RF_PSEUDO_QR : Alg. 1.  Thin complex QR of Y_c (Cholesky-QR on the Gram of Y, with a
+ *                     shift on breakdown), H from the Q factor, then n_correction steps
+ *                     H <- (1-eps) H + eps (H^dagger)* (eq. CondNumReductionIter), eps from
+ *                     three power iterates (Sec. 3.1).  n_correction in [0, 3]; 3 is the
+ *                     paper's default.
+ *   QS_RF_PSEUDO_SVD: Alg. 2.  Complex SVD of chi_Y, one left vector per duplicated pair,
+ *                     SVD repair of the bad pairs.  n_correction is ignored.
+ * Returns QS_OK, or an argument error; numerical rank warnings are sticky (see header). */
+QS_API qs_status qrangefinder(qs_handle_t h, int32_t kind, int32_t n_correction, void* stream);
+
+/* QB stage (Alg. 3): P = Psi H, then X = P^dagger W through the complex representation
+ * (Alg. QLEQ) with a Householder QR of chi_P. */
+QS_API qs_status qonepass_core(qs_handle_t h, void* stream);
+
+/* Relative error ||A - H X||_F / ||A||_F (Sec. 5) for the full matrix A (same plane
+ * conventions as qsketch_update, block = whole matrix).  Writes one double to the
+ * device pointer rel_err_dev (may be NULL: the value is still kept in QS_OBJ_SCALARS[0]).
+ * This is an evaluation pass: it reads A a second time. */
+QS_API qs_status qreconstruct_error(qs_handle_t h, const void* const A_planes[4], int64_t lda,
+                             double* rel_err_dev, void* stream);
+
+/* Device pointer, leading dimension (elements), plane stride (elements) and element type
+ * of an object in the workspace.  Views stay valid until qsketch_destroy. */
+QS_API qs_status qsketch_get(qs_handle_t h, int32_t which, void** dev_ptr, int64_t* ld,
+                      int64_t* plane_stride, int32_t* dtype);
+
+/* Synchronises `stream`, then returns the sticky device status (QS_OK, QS_ERR_RANK,
+ * QS_ERR_NUMERIC or QS_ERR_TIMEOUT; the most severe seen) and clears it. */
+QS_API qs_status qs_last_device_error(qs_handle_t h, void* stream);
+
+/* Frees the host handle.  The workspace remains the caller's. */
+QS_API qs_status qsketch_destroy(qs_handle_t h);
+
+/* Static description of a status code. */
+QS_API const char* qs_status_string(qs_status st);
+
+/* Library version as 10000*major + 100*minor + patch. */
+QS_API int32_t qs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSKETCH_H_ */

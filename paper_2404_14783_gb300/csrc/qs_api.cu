@@ -1,0 +1,426 @@
+// C ABI of the qsketch library: workspace carving, argument validation and the launch
+// sequences of the sketch (Sec. 4.1), the rangefinders (Alg. 1, Alg. 2), the QB stage
+// (Alg. 3 with Alg. QLEQ) and the error evaluation (Sec. 5).  All work is enqueued on the
+// caller's stream; nothing here synchronises except qs_last_device_error.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "qs_common.cuh"
+#include "qs_small.cuh"
+#include "qs_sketch_tc.cuh"
+
+using namespace qs;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+constexpr int kSmallSlots = 12;  // s x s FP64 scratch matrices
+constexpr double kKappaStop = 1e8;
+
+bool valid_cfg(const qs_config* c) {
+  if (!c) return false;
+  if (c->m < 1 || c->n < 1 || c->s < 1 || c->l < c->s) return false;
+  if (c->l > std::min(c->m, c->n)) return false;
+  if (c->s > 1024) return false;                      // small-matrix kernels keep s <= 1024
+  if (c->m > (int64_t)1 << 31 || c->n > (int64_t)1 << 31) return false;
+  if (c->emb != QS_EMB_GAUSSIAN && c->emb != QS_EMB_RADEMACHER) return false;
+  if (c->prec < QS_PREC_FP64 || c->prec > QS_PREC_BF16X3) return false;
+  if (c->pure != 0 && c->pure != 1) return false;
+  if (c->flags != 0) return false;
+  return true;
+}
+
+// Workspace layout; fills offsets of h (if non-null) and returns total bytes.
+size_t plan(const qs_config& c, qs_handle_s* h) {
+  const size_t es = c.prec == QS_PREC_FP64 ? 8 : 4;
+  const size_t m = c.m, n = c.n, s = c.s, l = c.l;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  size_t o_status = take(kAlign);
+  size_t o_scal = take(sizeof(double) * kScCount);
+  size_t o_om = take(4 * n * s * es);
+  size_t o_psi = take(4 * l * m * es);
+  size_t o_y = take(4 * m * s * es);
+  size_t o_w = take(4 * l * n * es);
+  size_t o_h = take(4 * m * s * es);
+  size_t o_x = take(4 * s * n * es);
+  size_t o_gram = take(4 * m * s * 8);  // FP64 tall temporary (m x s)
+  const size_t small_bytes = kSmallSlots * align_up(4 * s * s * 8);
+  size_t o_small = take(small_bytes);
+  size_t o_p = take(4 * l * s * 8);
+  const size_t core_bytes = 3 * align_up(4 * l * s * 8) + align_up(4 * s * l * 8);
+  size_t o_core = take(core_bytes);
+  const size_t pack_bytes = tc_pack_bytes(c);
+  size_t o_pack = take(pack_bytes);
+  if (h) {
+    h->esize = (int)es;
+    h->off_status = o_status; h->off_scalars = o_scal; h->off_omega = o_om; h->off_psi = o_psi;
+    h->off_y = o_y; h->off_w = o_w; h->off_h = o_h; h->off_x = o_x; h->off_gram = o_gram;
+    h->off_small = o_small; h->off_p = o_p; h->off_core = o_core; h->off_pack = o_pack;
+    h->off_tail = off; h->small_bytes = small_bytes; h->core_bytes = core_bytes;
+    h->pack_bytes = pack_bytes;
+  }
+  return off;
+}
+
+#define QS_CU(x)                                \
+  do {                                          \
+    if ((x) != cudaSuccess) return QS_ERR_CUDA; \
+  } while (0)
+
+// Views into the workspace.
+struct Mat {
+  void* p;         // plane 0
+  int64_t ld, ps;  // leading dim, plane stride (elements)
+  int f64;
+  void planes(void* out[4], int64_t off = 0) const {
+    planes_of(p, ps, f64 ? 8 : 4, off, out);
+  }
+  void cplanes(const void* out[4], int64_t off = 0) const {
+    planes_of((const void*)p, ps, f64 ? 8 : 4, off, out);
+  }
+};
+
+struct Ctx {
+  qs_handle_s* h;
+  cudaStream_t st;
+  int64_t m, n, s, l;
+  bool f64;
+  Mat omega() const { return {h->ws + h->off_omega, s, n * s, f64}; }
+  Mat psi() const { return {h->ws + h->off_psi, m, l * m, f64}; }
+  Mat Y() const { return {h->ws + h->off_y, s, m * s, f64}; }
+  Mat W() const { return {h->ws + h->off_w, n, l * n, f64}; }
+  Mat H() const { return {h->ws + h->off_h, s, m * s, f64}; }
+  Mat X() const { return {h->ws + h->off_x, n, s * n, f64}; }
+  Mat T() const { return {h->ws + h->off_gram, s, m * s, 1}; }
+  Mat small(int i) const {
+    return {h->ws + h->off_small + i * align_up(4 * s * s * 8), s, s * s, 1};
+  }
+  Mat P() const { return {h->ws + h->off_p, s, l * s, 1}; }
+  Mat core(int i) const {  // 0..2: l x s FP64, 3: s x l
+    char* base = h->ws + h->off_core;
+    if (i < 3) return {base + i * align_up(4 * l * s * 8), s, l * s, 1};
+    return {base + 3 * align_up(4 * l * s * 8), l, s * l, 1};
+  }
+  int32_t* status() const { return h->d_status(); }
+  double* scalars() const { return h->d_scalars(); }
+};
+
+int pick_splits(int64_t M, int64_t N, int64_t K) {
+  const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
+  int64_t sp = (2 * kNumSMs + tiles - 1) / tiles;
+  sp = std::min<int64_t>(sp, std::max<int64_t>(1, K / 128));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(sp, 1024));
+}
+
+// C = alpha * op(A) B + beta C on workspace matrices (all FP64 unless stated by the views).
+cudaError_t gemm(const Ctx& x, const Mat& A, bool conjA, const Mat& B, const Mat& C, int64_t M,
+                 int64_t N, int64_t K, double alpha, double beta, bool acc64, bool allow_split) {
+  GemmDesc d{};
+  d.M = M; d.N = N; d.K = K;
+  A.cplanes(d.a); d.lda = A.ld; d.a_f64 = A.f64; d.conj_a = conjA;
+  B.cplanes(d.b); d.ldb = B.ld; d.b_f64 = B.f64;
+  C.planes(d.c); d.ldc = C.ld; d.c_f64 = C.f64;
+  d.alpha = alpha; d.beta = beta; d.acc_f64 = acc64;
+  d.splits = allow_split ? pick_splits(M, N, K) : 1;
+  d.epi = 0; d.err = nullptr;
+  if (d.splits > 1 && beta != 1.0) {
+    cudaError_t e = launch_scale(C.p, C.f64, M, N, C.ld, C.ps, beta, x.st);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_qgemm(d, x.st);
+}
+
+// Gram G = A* A of a tall m x s matrix (FP64 result).
+cudaError_t gram(const Ctx& x, const Mat& A, int64_t rows, int64_t cols, const Mat& G) {
+  return gemm(x, A, true, A, G, cols, cols, rows, 1.0, 0.0, true, true);
+}
+
+qs_status pseudo_qr(const Ctx& x, int ncorr) {
+  const int s = (int)x.s;
+  const Mat G = x.small(0), L = x.small(1), Li = x.small(2), D = x.small(3), D2 = x.small(4),
+            R2 = x.small(5), Tm = x.small(6), G0 = x.small(7), Gi = x.small(8), M = x.small(9);
+  const Mat Y = x.Y(), T = x.T();
+  int32_t* st = x.status();
+  double* sc = x.scalars();
+  // (Alg. 1 step 2) thin complex QR of Y_c by Cholesky-QR: Y_c* Y_c = L L*, R = L*.
+  QS_CU(gram(x, Y, x.m, s, G));
+  QS_CU(launch_qchol((double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s, 1, 1, 2.0 * x.m, st,
+                     sc, kDevRank | kDevStopCorr, x.st));
+  QS_CU(launch_qtrinv((double*)L.p, L.ld, L.ps, (double*)Li.p, Li.ld, Li.ps, s, st, x.st));
+  QS_CU(launch_qconjT(Li.p, 1, Li.ld, Li.ps, D.p, 1, D.ld, D.ps, s, s, x.st));   // D = R^{-1}
+  // second Cholesky-QR pass on T = Y R^{-1} restores orthogonality of the Q factor
+  QS_CU(gemm(x, Y, false, D, T, x.m, s, s, 1.0, 0.0, true, false));
+  QS_CU(gram(x, T, x.m, s, G));
+  QS_CU(launch_qchol((double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s, 1, 0, 2.0 * x.m, st,
+                     sc, kDevRank | kDevStopCorr, x.st));
+  QS_CU(launch_qtrinv((double*)L.p, L.ld, L.ps, (double*)Li.p, Li.ld, Li.ps, s, st, x.st));
+  QS_CU(launch_qconjT(Li.p, 1, Li.ld, Li.ps, R2.p, 1, R2.ld, R2.ps, s, s, x.st));
+  QS_CU(gemm(x, D, false, R2, D2, s, s, s, 1.0, 0.0, true, false));  // D2 = R^{-1} of Y_c
+  // (Alg. 1 step 3) H_0 = Y D2; its quaternion Gram G_0 = R2^{-*} (T*T) R2^{-1}
+  QS_CU(gemm(x, Li, false, G, Tm, s, s, s, 1.0, 0.0, true, false));
+  QS_CU(gemm(x, Tm, false, R2, G0, s, s, s, 1.0, 0.0, true, false));
+  Mat Dcur = D2, Dnext = D;
+  Mat Gk = G0;
+  // (Alg. 1 step 4) corrections H <- (1-eps) H + eps (H^dagger)* = H ((1-eps) I + eps G^{-1})
+  for (int k = 0; k < ncorr; ++k) {
+    QS_CU(launch_qchol((double*)Gk.p, Gk.ld, Gk.ps, (double*)L.p, L.ld, L.ps, s, 0, 0, 2.0 * x.m,
+                       st, sc, kDevRank | kDevStopCorr, x.st));
+    QS_CU(launch_qpower((double*)L.p, L.ld, L.ps, s, 3, kScEps0 + k, kKappaStop, st, sc, x.st));
+    QS_CU(launch_qtrinv((double*)L.p, L.ld, L.ps, (double*)Li.p, Li.ld, Li.ps, s, st, x.st));
+    QS_CU(gemm(x, Li, true, Li, Gi, s, s, s, 1.0, 0.0, true, false));  // G^{-1} = L^{-*} L^{-1}
+    QS_CU(launch_qaxpby_eye((double*)Gi.p, Gi.ld, Gi.ps, (double*)M.p, M.ld, M.ps, s, sc,
+                            kScEps0 + k, x.st));
+    QS_CU(gemm(x, Dcur, false, M, Dnext, s, s, s, 1.0, 0.0, true, false));
+    std::swap(Dcur, Dnext);
+    if (k + 1 < ncorr) {  // Gram of the explicitly formed H_{k+1} = Y D
+      QS_CU(gemm(x, Y, false, Dcur, T, x.m, s, s, 1.0, 0.0, true, false));
+      QS_CU(gram(x, T, x.m, s, G));
+      Gk = G;
+    }
+  }
+  QS_CU(gemm(x, Y, false, Dcur, x.H(), x.m, s, s, 1.0, 0.0, true, false));
+  return QS_OK;
+}
+
+qs_status core_solve(const Ctx& x) {
+  const int s = (int)x.s;
+  const int64_t l = x.l;
+  const Mat P = x.P(), Tp = x.core(0), Qp = x.core(1), ZT = x.core(2), Z = x.core(3);
+  const Mat G = x.small(0), L = x.small(1), L1i = x.small(2), R1 = x.small(3), L2i = x.small(4),
+            R2 = x.small(5), S = x.small(6);
+  int32_t* st = x.status();
+  double* sc = x.scalars();
+  // (Alg. 3 step 2) P = Psi H
+  QS_CU(gemm(x, x.psi(), false, x.H(), P, l, s, x.m, 1.0, 0.0, true, true));
+  // Alg. QLEQ on chi_P: QR of P (quaternion Cholesky-QR, twice), X = R^{-1} Q* W
+  QS_CU(gram(x, P, l, s, G));
+  QS_CU(launch_qchol((double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s, 0, 1, 2.0 * l, st, sc,
+                     kDevRank, x.st));
+  QS_CU(launch_qtrinv((double*)L.p, L.ld, L.ps, (double*)L1i.p, L1i.ld, L1i.ps, s, st, x.st));
+  QS_CU(launch_qconjT(L1i.p, 1, L1i.ld, L1i.ps, R1.p, 1, R1.ld, R1.ps, s, s, x.st));
+  QS_CU(gemm(x, P, false, R1, Tp, l, s, s, 1.0, 0.0, true, false));
+  QS_CU(gram(x, Tp, l, s, G));
+  QS_CU(launch_qchol((double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s, 0, 0, 2.0 * l, st, sc,
+                     kDevRank, x.st));
+  QS_CU(launch_qtrinv((double*)L.p, L.ld, L.ps, (double*)L2i.p, L2i.ld, L2i.ps, s, st, x.st));
+  QS_CU(launch_qconjT(L2i.p, 1, L2i.ld, L2i.ps, R2.p, 1, R2.ld, R2.ps, s, s, x.st));
+  QS_CU(gemm(x, Tp, false, R2, Qp, l, s, s, 1.0, 0.0, true, false));       // Q (l x s)
+  QS_CU(gemm(x, L2i, false, L1i, S, s, s, s, 1.0, 0.0, true, false));      // (R^{-1})* = L2^{-1} L1^{-1}
+  QS_CU(gemm(x, Qp, false, S, ZT, l, s, s, 1.0, 0.0, true, false));        // (P^dagger)* = Q R^{-*}
+  QS_CU(launch_qconjT(ZT.p, 1, ZT.ld, ZT.ps, Z.p, 1, Z.ld, Z.ps, (int)l, s, x.st));  // P^dagger
+  // X = P^dagger W (s x n)
+  QS_CU(gemm(x, Z, false, x.W(), x.X(), s, x.n, l, 1.0, 0.0, true, true));
+  return QS_OK;
+}
+
+bool planes_ok(const qs_handle_s* h, const void* const A[4]) {
+  if (!A) return false;
+  for (int p = 1; p < 4; ++p)
+    if (!A[p]) return false;
+  if (!A[0] && !h->cfg.pure) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t qsketch_workspace_bytes(const qs_config* cfg) {
+  if (!valid_cfg(cfg)) return 0;
+  return plan(*cfg, nullptr);
+}
+
+qs_status qsketch_create(const qs_config* cfg, void* workspace, size_t bytes, void* stream,
+                         qs_handle_t* out) {
+  if (!out) return QS_ERR_INVALID;
+  *out = nullptr;
+  if (!valid_cfg(cfg) || !workspace) return QS_ERR_INVALID;
+  if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return QS_ERR_INVALID;
+  qs_handle_s* h = new (std::nothrow) qs_handle_s();
+  if (!h) return QS_ERR_NOMEM;
+  h->cfg = *cfg;
+  const size_t need = plan(*cfg, h);
+  if (bytes < need) {
+    delete h;
+    return QS_ERR_NOMEM;
+  }
+  h->ws = static_cast<char*>(workspace);
+  h->ws_bytes = bytes;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ctx x{h, st, cfg->m, cfg->n, cfg->s, cfg->l, cfg->prec == QS_PREC_FP64};
+  const bool f64 = x.f64;
+  cudaError_t e = cudaMemsetAsync(h->ws, 0, h->off_omega, st);
+  if (e == cudaSuccess) e = launch_draw(x.omega().p, f64, cfg->n, cfg->s, cfg->emb, kStreamOmega, cfg->seed, st);
+  if (e == cudaSuccess) e = launch_draw(x.psi().p, f64, cfg->l, cfg->m, cfg->emb, kStreamPsi, cfg->seed, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x.Y().p, 0, 4 * cfg->m * cfg->s * h->esize, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x.W().p, 0, 4 * cfg->l * cfg->n * h->esize, st);
+  if (e == cudaSuccess && tc_mode(cfg->prec)) e = tc_pack_embeddings(*h, st);
+  if (e != cudaSuccess) {
+    delete h;
+    return QS_ERR_CUDA;
+  }
+  *out = h;
+  return QS_OK;
+}
+
+qs_status qsketch_update(qs_handle_t h, const void* const A_planes[4], int64_t lda, int64_t row0,
+                         int64_t col0, int64_t mb, int64_t nb, double theta, double eta,
+                         void* stream) {
+  if (!h || !planes_ok(h, A_planes)) return QS_ERR_INVALID;
+  const qs_config& c = h->cfg;
+  if (row0 < 0 || col0 < 0 || mb < 0 || nb < 0 || row0 + mb > c.m || col0 + nb > c.n)
+    return QS_ERR_INVALID;
+  if (lda < nb || !std::isfinite(theta) || !std::isfinite(eta)) return QS_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ctx x{h, st, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64};
+  if (theta != 1.0) {
+    QS_CU(launch_scale(x.Y().p, x.f64, c.m, c.s, c.s, c.m * c.s, theta, st));
+    QS_CU(launch_scale(x.W().p, x.f64, c.l, c.n, c.n, c.l * c.n, theta, st));
+  }
+  if (mb == 0 || nb == 0) return QS_OK;
+  if (tc_mode(c.prec)) {
+    const qs_status ts = tc_sketch_update(*h, A_planes, lda, row0, col0, mb, nb, eta, st);
+    return ts;
+  }
+  const Mat Y = x.Y(), W = x.W(), Om = x.omega(), Ps = x.psi();
+  const int es = h->esize;
+  // Y[row0:row0+mb, :] += eta * A_b Omega[col0:col0+nb, :]
+  GemmDesc d{};
+  d.M = mb; d.N = c.s; d.K = nb;
+  for (int p = 0; p < 4; ++p) d.a[p] = A_planes[p];
+  if (c.pure) d.a[0] = nullptr;
+  d.lda = lda; d.a_f64 = x.f64; d.conj_a = 0;
+  Om.cplanes(d.b, col0 * c.s); d.ldb = c.s; d.b_f64 = x.f64;
+  Y.planes(d.c, row0 * c.s); d.ldc = c.s; d.c_f64 = x.f64;
+  d.alpha = eta; d.beta = 1.0; d.acc_f64 = x.f64;
+  d.splits = pick_splits(d.M, d.N, d.K);
+  QS_CU(launch_qgemm(d, st));
+  // W[:, col0:col0+nb] += eta * Psi[:, row0:row0+mb] A_b
+  GemmDesc g{};
+  g.M = c.l; g.N = nb; g.K = mb;
+  Ps.cplanes(g.a, row0); g.lda = c.m; g.a_f64 = x.f64; g.conj_a = 0;
+  for (int p = 0; p < 4; ++p) g.b[p] = A_planes[p];
+  if (c.pure) g.b[0] = nullptr;
+  g.ldb = lda; g.b_f64 = x.f64;
+  W.planes(g.c, col0); g.ldc = c.n; g.c_f64 = x.f64;
+  g.alpha = eta; g.beta = 1.0; g.acc_f64 = x.f64;
+  g.splits = pick_splits(g.M, g.N, g.K);
+  QS_CU(launch_qgemm(g, st));
+  (void)es;
+  return QS_OK;
+}
+
+qs_status qrangefinder(qs_handle_t h, int32_t kind, int32_t n_correction, void* stream) {
+  if (!h) return QS_ERR_INVALID;
+  if (kind != QS_RF_PSEUDO_QR && kind != QS_RF_PSEUDO_SVD) return QS_ERR_INVALID;
+  if (n_correction < 0 || n_correction > 3) return QS_ERR_INVALID;
+  const qs_config& c = h->cfg;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ctx x{h, st, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64};
+  QS_CU(launch_clear_stop(x.status(), st));
+  QS_CU(cudaMemsetAsync(x.scalars() + kScKappa, 0, sizeof(double) * 6, st));
+  if (kind == QS_RF_PSEUDO_QR) return pseudo_qr(x, n_correction);
+  return pseudo_svd_run(*h, st);
+}
+
+qs_status qonepass_core(qs_handle_t h, void* stream) {
+  if (!h) return QS_ERR_INVALID;
+  const qs_config& c = h->cfg;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ctx x{h, st, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64};
+  return core_solve(x);
+}
+
+qs_status qreconstruct_error(qs_handle_t h, const void* const A_planes[4], int64_t lda,
+                             double* rel_err_dev, void* stream) {
+  if (!h || !planes_ok(h, A_planes)) return QS_ERR_INVALID;
+  const qs_config& c = h->cfg;
+  if (lda < c.n) return QS_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ctx x{h, st, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64};
+  double* sc = x.scalars();
+  QS_CU(cudaMemsetAsync(sc + kScErrNum, 0, 2 * sizeof(double), st));
+  GemmDesc d{};
+  d.M = c.m; d.N = c.n; d.K = c.s;
+  x.H().cplanes(d.a); d.lda = c.s; d.a_f64 = x.f64;
+  x.X().cplanes(d.b); d.ldb = c.n; d.b_f64 = x.f64;
+  for (int p = 0; p < 4; ++p) d.c[p] = const_cast<void*>(A_planes[p]);
+  if (c.pure) d.c[0] = nullptr;
+  d.ldc = lda; d.c_f64 = x.f64;
+  d.alpha = 1.0; d.beta = 0.0; d.acc_f64 = x.f64; d.splits = 1;
+  d.epi = 1; d.err = sc + kScErrNum;
+  QS_CU(launch_qgemm(d, st));
+  QS_CU(launch_finalize_err(sc, rel_err_dev, st));
+  return QS_OK;
+}
+
+qs_status qsketch_get(qs_handle_t h, int32_t which, void** dev_ptr, int64_t* ld,
+                      int64_t* plane_stride, int32_t* dtype) {
+  if (!h || !dev_ptr) return QS_ERR_INVALID;
+  const qs_config& c = h->cfg;
+  Ctx x{h, nullptr, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64};
+  Mat v{};
+  switch (which) {
+    case QS_OBJ_Y: v = x.Y(); break;
+    case QS_OBJ_W: v = x.W(); break;
+    case QS_OBJ_OMEGA: v = x.omega(); break;
+    case QS_OBJ_PSI: v = x.psi(); break;
+    case QS_OBJ_H: v = x.H(); break;
+    case QS_OBJ_X: v = x.X(); break;
+    case QS_OBJ_PSIH: v = x.P(); break;
+    case QS_OBJ_SCALARS: v = {x.scalars(), kScCount, kScCount, 1}; break;
+    default: return QS_ERR_INVALID;
+  }
+  *dev_ptr = v.p;
+  if (ld) *ld = v.ld;
+  if (plane_stride) *plane_stride = v.ps;
+  if (dtype) *dtype = v.f64 ? QS_DT_F64 : QS_DT_F32;
+  return QS_OK;
+}
+
+qs_status qs_last_device_error(qs_handle_t h, void* stream) {
+  if (!h) return QS_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return QS_ERR_CUDA;
+  int32_t v = 0;
+  if (cudaMemcpy(&v, h->d_status(), sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return QS_ERR_CUDA;
+  if (cudaMemset(h->d_status(), 0, sizeof(int32_t)) != cudaSuccess) return QS_ERR_CUDA;
+  if (v & kDevTimeout) return QS_ERR_TIMEOUT;
+  if (v & kDevNumeric) return QS_ERR_NUMERIC;
+  if (v & kDevRank) return QS_ERR_RANK;
+  return QS_OK;
+}
+
+qs_status qsketch_destroy(qs_handle_t h) {
+  if (!h) return QS_ERR_INVALID;
+  delete h;
+  return QS_OK;
+}
+
+const char* qs_status_string(qs_status st) {
+  switch (st) {
+    case QS_OK: return "ok";
+    case QS_ERR_INVALID: return "invalid argument";
+    case QS_ERR_NOMEM: return "workspace too small";
+    case QS_ERR_CUDA: return "CUDA runtime error";
+    case QS_ERR_RANK: return "numerical rank deficiency (warning)";
+    case QS_ERR_NUMERIC: return "NaN or Inf in the data";
+    case QS_ERR_TIMEOUT: return "bounded device wait expired";
+    case QS_ERR_UNSUPPORTED: return "not supported by this build";
+  }
+  return "unknown status";
+}
+
+int32_t qs_version(void) { return 100; }
+
+}  // extern "C"

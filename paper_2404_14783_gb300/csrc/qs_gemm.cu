@@ -1,0 +1,289 @@
+// Generic SIMT quaternion matrix product and elementwise helpers.
+//
+// C = alpha * op(A) * B + beta * C for quaternion matrices stored as four real planes,
+// op(A) = A or A* (conjugate transpose, Sec. 2).  One kernel serves every product of the
+// method that is not on the tensor-core path: the FP64 and FP32 sketches Y = A Omega and
+// W = Psi A (Sec. 4.1), the Gram Y*Y of the rangefinders, the tall products H = Y C and
+// P = Psi H, and the core products of Alg. 3.
+//
+// Tiling: a CTA of 256 threads computes a 64 x 64 quaternion tile; each thread owns a
+// 4 x 4 quaternion sub-tile (64 accumulators).  K is staged through shared memory in
+// double-buffered slices (8 deep in FP32, 4 in FP64) with a register prefetch of the next
+// slice.  split-K (grid z) accumulates with atomics into a pre-scaled C.
+#include <algorithm>
+
+#include "qs_common.cuh"
+
+namespace qs {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T ld_elem(const void* base, int64_t idx) {
+  return static_cast<const T*>(base)[idx];
+}
+
+template <typename ACC, typename TA, typename TB, typename TC, bool CONJ>
+__global__ void __launch_bounds__(256) qgemm_kernel(GemmDesc g) {
+  constexpr int BM = 64, BN = 64;
+  constexpr int BK = sizeof(ACC) == 8 ? 4 : 8;
+  __shared__ __align__(16) ACC As[2][4][BK][BM];
+  __shared__ __align__(16) ACC Bs[2][4][BK][BN];
+
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+
+  int64_t kchunk = (g.K + g.splits - 1) / g.splits;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  const int64_t kend = min(g.K, kbeg + kchunk);
+  if (kbeg >= kend && g.splits > 1) return;
+
+  // loader coordinates: plane lp, row/col lr
+  const int lp = tid >> 6, lr = tid & 63;
+  const TA* A = static_cast<const TA*>(g.a[lp]);
+  const TB* B = static_cast<const TB*>(g.b[lp]);
+  const bool a_zero = (A == nullptr);   // a NULL plane is identically zero (pure quaternion)
+  const bool b_zero = (B == nullptr);
+  const ACC a_sign = (CONJ && lp != 0) ? ACC(-1) : ACC(1);
+
+  ACC ra[BK], rb[BK];
+  auto load_regs = [&](int64_t k0) {
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const int64_t k = k0 + kk;
+      ACC va = ACC(0), vb = ACC(0);
+      if (CONJ) {
+        const int64_t mm = m0 + lr;
+        if (!a_zero && k < kend && mm < g.M) va = a_sign * ACC(A[k * g.lda + mm]);
+      } else {
+        const int64_t mm = m0 + lr;
+        if (!a_zero && k < kend && mm < g.M) va = ACC(A[mm * g.lda + k]);
+      }
+      const int64_t nn = n0 + lr;
+      if (!b_zero && k < kend && nn < g.N) vb = ACC(B[k * g.ldb + nn]);
+      ra[kk] = va;
+      rb[kk] = vb;
+    }
+  };
+  auto store_regs = [&](int buf) {
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      As[buf][lp][kk][lr] = ra[kk];
+      Bs[buf][lp][kk][lr] = rb[kk];
+    }
+  };
+
+  ACC acc[4][4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[q][i][j] = ACC(0);
+
+  int buf = 0;
+  if (kbeg < kend) {
+    load_regs(kbeg);
+    store_regs(0);
+    __syncthreads();
+  }
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+    const bool has_next = k0 + BK < kend;
+    if (has_next) load_regs(k0 + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      ACC a[4][4], b[4][4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          a[p][i] = As[buf][p][kk][ty * 4 + i];
+          b[p][i] = Bs[buf][p][kk][tx * 4 + i];
+        }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          qmac(acc[0][i][j], acc[1][i][j], acc[2][i][j], acc[3][i][j], a[0][i], a[1][i], a[2][i],
+               a[3][i], b[0][j], b[1][j], b[2][j], b[3][j]);
+    }
+    if (has_next) {
+      store_regs(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+
+  const ACC alpha = ACC(g.alpha);
+  if (g.epi == 1) {
+    // error epilogue: sum |E - alpha*acc|^2 and sum |E|^2 over this tile
+    double se = 0.0, sa = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t m = m0 + ty * 4 + i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t n = n0 + tx * 4 + j;
+        if (m < g.M && n < g.N) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const TC* E = static_cast<const TC*>(g.c[q]);
+            const double e = E ? double(E[m * g.ldc + n]) : 0.0;
+            const double d = e - double(alpha * acc[q][i][j]);
+            se += d * d;
+            sa += e * e;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      se += __shfl_xor_sync(0xffffffffu, se, o);
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    }
+    __shared__ double red[2][8];
+    if ((tid & 31) == 0) { red[0][tid >> 5] = se; red[1][tid >> 5] = sa; }
+    __syncthreads();
+    if (tid == 0) {
+      double a0 = 0.0, a1 = 0.0;
+      for (int w = 0; w < 8; ++w) { a0 += red[0][w]; a1 += red[1][w]; }
+      atomicAdd(g.err, a0);
+      atomicAdd(g.err + 1, a1);
+    }
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t m = m0 + ty * 4 + i;
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t n = n0 + tx * 4 + j;
+      if (n >= g.N) continue;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        TC* dst = static_cast<TC*>(g.c[q]) + m * g.ldc + n;
+        const ACC v = alpha * acc[q][i][j];
+        if (g.splits > 1) {
+          atomicAdd(dst, TC(v));
+        } else if (g.beta == 0.0) {
+          *dst = TC(v);
+        } else {
+          *dst = TC(v + ACC(g.beta) * ACC(*dst));
+        }
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void scale_kernel(T* c, int64_t rows, int64_t cols, int64_t ld, int64_t ps, T beta) {
+  const int64_t total = rows * cols * 4;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = t / (rows * cols), rc = t % (rows * cols);
+    T* dst = c + p * ps + (rc / cols) * ld + rc % cols;
+    *dst = beta == T(0) ? T(0) : beta * *dst;
+  }
+}
+
+// Draw one quaternion test matrix (see qsketch.h for the element mapping).
+template <typename T>
+__global__ void draw_kernel(T* out, int64_t rows, int64_t cols, int kind, uint32_t stream,
+                            uint32_t k0, uint32_t k1) {
+  const int64_t total = rows * cols;
+  const int64_t ps = total;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const Philox4 r = philox4x32_10((uint32_t)e, (uint32_t)((uint64_t)e >> 32), stream, 0u, k0, k1);
+    T v[4];
+    if (kind == QS_EMB_RADEMACHER) {
+#pragma unroll
+      for (int p = 0; p < 4; ++p) v[p] = (r.x[p] >> 31) ? T(-1) : T(1);
+    } else {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (sizeof(T) == 8) {
+          const double ua = ((double)r.x[2 * h] + 0.5) * 0x1p-32;
+          const double ub = ((double)r.x[2 * h + 1] + 0.5) * 0x1p-32;
+          const double rad = sqrt(-2.0 * log(ua));
+          double sn, cs;
+          sincospi(2.0 * ub, &sn, &cs);
+          v[2 * h] = T(rad * cs);
+          v[2 * h + 1] = T(rad * sn);
+        } else {
+          // u = (x + 1/2) 2^-32 rounded to FP32 (relative error 2^-24 at every magnitude)
+          const float ua = fmaf(__uint2float_rn(r.x[2 * h]), 0x1p-32f, 0x1p-33f);
+          const float ub = fmaf(__uint2float_rn(r.x[2 * h + 1]), 0x1p-32f, 0x1p-33f);
+          const float rad = sqrtf(-2.0f * logf(ua));
+          float sn, cs;
+          sincospif(2.0f * ub, &sn, &cs);
+          v[2 * h] = T(rad * cs);
+          v[2 * h + 1] = T(rad * sn);
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) out[p * ps + e] = v[p];
+  }
+}
+
+template <typename ACC, typename TA, typename TB, typename TC>
+cudaError_t launch_t(const GemmDesc& d, cudaStream_t st) {
+  dim3 grid((unsigned)((d.M + 63) / 64), (unsigned)((d.N + 63) / 64), (unsigned)d.splits);
+  if (d.conj_a)
+    qgemm_kernel<ACC, TA, TB, TC, true><<<grid, 256, 0, st>>>(d);
+  else
+    qgemm_kernel<ACC, TA, TB, TC, false><<<grid, 256, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+template <typename ACC, typename TA, typename TB>
+cudaError_t launch_c(const GemmDesc& d, cudaStream_t st) {
+  return d.c_f64 ? launch_t<ACC, TA, TB, double>(d, st) : launch_t<ACC, TA, TB, float>(d, st);
+}
+template <typename ACC, typename TA>
+cudaError_t launch_b(const GemmDesc& d, cudaStream_t st) {
+  return d.b_f64 ? launch_c<ACC, TA, double>(d, st) : launch_c<ACC, TA, float>(d, st);
+}
+
+}  // namespace
+
+cudaError_t launch_qgemm(const GemmDesc& d, cudaStream_t st) {
+  if (d.M <= 0 || d.N <= 0) return cudaSuccess;
+  if (d.K <= 0 || d.splits < 1) return cudaErrorInvalidValue;
+  if (!d.acc_f64) {
+    if (d.a_f64 || d.b_f64 || d.c_f64) return cudaErrorInvalidValue;
+    return launch_t<float, float, float, float>(d, st);
+  }
+  return d.a_f64 ? launch_b<double, double>(d, st) : launch_b<double, float>(d, st);
+}
+
+cudaError_t launch_scale(void* c, int f64, int64_t rows, int64_t cols, int64_t ld, int64_t ps,
+                         double beta, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  const int64_t total = rows * cols * 4;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8 * kNumSMs);
+  if (f64)
+    scale_kernel<double><<<blocks, 256, 0, st>>>((double*)c, rows, cols, ld, ps, beta);
+  else
+    scale_kernel<float><<<blocks, 256, 0, st>>>((float*)c, rows, cols, ld, ps, (float)beta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_draw(void* out, int f64, int64_t rows, int64_t cols, int kind, uint32_t stream,
+                        uint64_t seed, cudaStream_t st) {
+  const int64_t total = rows * cols;
+  if (total <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 16 * kNumSMs);
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  if (f64)
+    draw_kernel<double><<<blocks, 256, 0, st>>>((double*)out, rows, cols, kind, stream, k0, k1);
+  else
+    draw_kernel<float><<<blocks, 256, 0, st>>>((float*)out, rows, cols, kind, stream, k0, k1);
+  return cudaGetLastError();
+}
+
+}  // namespace qs

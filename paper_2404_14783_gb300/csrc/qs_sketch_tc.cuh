@@ -1,0 +1,17 @@
+// Tensor-core (tcgen05) sketch path and pseudo-SVD driver (declarations).
+#pragma once
+#include "qs_common.cuh"
+
+namespace qs {
+inline bool tc_mode(int32_t prec) { return prec == QS_PREC_BF16 || prec == QS_PREC_BF16X3; }
+// bytes of packed BF16 operands the tensor-core path keeps in the workspace
+size_t tc_pack_bytes(const qs_config& c);
+// pack Omega / Psi (drawn in FP32) into the operand layouts of the fused kernel
+cudaError_t tc_pack_embeddings(const qs_handle_s& h, cudaStream_t st);
+// fused one-read sketch of a block of A
+qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t lda, int64_t row0,
+                           int64_t col0, int64_t mb, int64_t nb, double eta, cudaStream_t st);
+// pseudo-SVD rangefinder (Alg. 2)
+qs_status pseudo_svd_run(qs_handle_s& h, cudaStream_t st);
+cudaError_t launch_finalize_err(double* scalars, double* out, cudaStream_t st);
+}  // namespace qs

@@ -1,0 +1,22 @@
+// Launchers of the small dense quaternion kernels (qs_small.cu).
+#pragma once
+#include "qs_common.cuh"
+
+namespace qs {
+enum : int32_t { kDevStopCorr = 256 };  // internal: remaining corrections are skipped
+
+cudaError_t launch_qchol(const double* G, int64_t ldg, int64_t psg, double* L, int64_t ldl,
+                         int64_t psl, int n, int complex_only, int allow_shift, double shift_rows,
+                         int32_t* status, double* scalars, int fail_bits, cudaStream_t st);
+cudaError_t launch_qtrinv(const double* L, int64_t ldl, int64_t psl, double* X, int64_t ldx,
+                          int64_t psx, int n, const int32_t* status, cudaStream_t st);
+cudaError_t launch_qpower(const double* L, int64_t ldl, int64_t psl, int n, int iters, int slot,
+                          double kappa_stop, int32_t* status, double* scalars, cudaStream_t st);
+cudaError_t launch_qaxpby_eye(const double* X, int64_t ldx, int64_t psx, double* M, int64_t ldm,
+                              int64_t psm, int n, const double* scalars, int slot, cudaStream_t st);
+cudaError_t launch_qconjT(const void* S, int s_f64, int64_t lds, int64_t pss, void* D, int d_f64,
+                          int64_t ldd, int64_t psd, int r, int c, cudaStream_t st);
+cudaError_t launch_qcopy(const void* S, int s_f64, int64_t lds, int64_t pss, void* D, int d_f64,
+                         int64_t ldd, int64_t psd, int64_t r, int64_t c, cudaStream_t st);
+cudaError_t launch_clear_stop(int32_t* status, cudaStream_t st);
+}  // namespace qs

@@ -1,0 +1,198 @@
+"""ctypes binding of libqsketch.so (argument marshalling only).
+
+Every computation runs in the library's CUDA kernels; this module only converts Python
+arguments to the C ABI declared in include/qsketch.h.  PyTorch provides device memory and
+streams.  If the shared library is missing the binding raises: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqsketch.so")
+
+QS_OK, QS_ERR_INVALID, QS_ERR_NOMEM, QS_ERR_CUDA, QS_ERR_RANK, QS_ERR_NUMERIC, \
+    QS_ERR_TIMEOUT, QS_ERR_UNSUPPORTED = range(8)
+QS_EMB_GAUSSIAN, QS_EMB_RADEMACHER = 0, 1
+QS_PREC_FP64, QS_PREC_FP32, QS_PREC_BF16, QS_PREC_BF16X3 = 0, 1, 2, 3
+QS_RF_PSEUDO_QR, QS_RF_PSEUDO_SVD = 0, 1
+QS_OBJ_Y, QS_OBJ_W, QS_OBJ_OMEGA, QS_OBJ_PSI, QS_OBJ_H, QS_OBJ_X, QS_OBJ_PSIH, \
+    QS_OBJ_SCALARS = range(8)
+QS_DT_F64, QS_DT_F32 = 0, 1
+
+PRECISIONS = {"fp64": QS_PREC_FP64, "fp32": QS_PREC_FP32, "bf16": QS_PREC_BF16,
+              "bf16x3": QS_PREC_BF16X3}
+EMBEDDINGS = {"gaussian": QS_EMB_GAUSSIAN, "rademacher": QS_EMB_RADEMACHER}
+RANGEFINDERS = {"pseudo_qr": QS_RF_PSEUDO_QR, "pseudo_svd": QS_RF_PSEUDO_SVD}
+
+ABI_SYMBOLS = ("qsketch_workspace_bytes", "qsketch_create", "qsketch_update", "qrangefinder",
+               "qonepass_core", "qreconstruct_error", "qsketch_get", "qs_last_device_error",
+               "qsketch_destroy", "qs_status_string", "qs_version")
+
+
+class QSConfig(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("s", ctypes.c_int64),
+                ("l", ctypes.c_int64), ("emb", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("pure", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class QSError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: status {code} ({_status_string(code)})")
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libqsketch.so and declare the ABI.  Raises OSError when it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libqsketch.so not built at {path}; run paper_2404_14783_gb300.build")
+    lib = ctypes.CDLL(path)
+    P, I64, I32, D, VP = ctypes.POINTER, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
+    planes = VP * 4
+    lib.qsketch_workspace_bytes.argtypes = [P(QSConfig)]
+    lib.qsketch_workspace_bytes.restype = ctypes.c_size_t
+    lib.qsketch_create.argtypes = [P(QSConfig), VP, ctypes.c_size_t, VP, P(VP)]
+    lib.qsketch_update.argtypes = [VP, planes, I64, I64, I64, I64, I64, D, D, VP]
+    lib.qrangefinder.argtypes = [VP, I32, I32, VP]
+    lib.qonepass_core.argtypes = [VP, VP]
+    lib.qreconstruct_error.argtypes = [VP, planes, I64, VP, VP]
+    lib.qsketch_get.argtypes = [VP, I32, P(VP), P(I64), P(I64), P(I32)]
+    lib.qs_last_device_error.argtypes = [VP, VP]
+    lib.qsketch_destroy.argtypes = [VP]
+    lib.qs_status_string.argtypes = [I32]
+    lib.qs_status_string.restype = ctypes.c_char_p
+    lib.qs_version.restype = I32
+    for name in ("qsketch_create", "qsketch_update", "qrangefinder", "qonepass_core",
+                 "qreconstruct_error", "qsketch_get", "qs_last_device_error", "qsketch_destroy"):
+        getattr(lib, name).restype = I32
+    _lib = lib
+    return lib
+
+
+def _status_string(code):
+    try:
+        return load_library().qs_status_string(int(code)).decode()
+    except OSError:
+        return "?"
+
+
+def _check(code, what, allow=(QS_OK,)):
+    if code not in allow:
+        raise QSError(code, what)
+    return code
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _planes(A, f64):
+    """Four plane pointers from a (4, rows, cols) tensor or a list of 4 tensors/None."""
+    want = torch.float64 if f64 else torch.float32
+    if isinstance(A, torch.Tensor):
+        assert A.dim() == 3 and A.shape[0] == 4, "A must be (4, rows, cols)"
+        mats = [A[p] for p in range(4)]
+    else:
+        mats = list(A)
+    ptrs = (ctypes.c_void_p * 4)()
+    ld = None
+    for p, t in enumerate(mats):
+        if t is None:
+            ptrs[p] = None
+            continue
+        if not t.is_cuda or t.dtype != want or t.stride(1) != 1:
+            raise ValueError(f"plane {p} must be a CUDA {want} row-major matrix")
+        ld = t.stride(0) if t.shape[0] > 1 else t.shape[1]
+        ptrs[p] = t.data_ptr()
+    return ptrs, ld
+
+
+class QSketch:
+    """One sketch state (Omega, Psi, Y, W and the results) in a caller-owned workspace."""
+
+    def __init__(self, m, n, s, l, emb="gaussian", prec="fp64", seed=0, pure=False,
+                 device="cuda", stream=None):
+        self.lib = load_library()
+        self.cfg = QSConfig(m, n, s, l, EMBEDDINGS.get(emb, emb), PRECISIONS.get(prec, prec),
+                            seed, int(bool(pure)), 0)
+        self.f64 = self.cfg.prec == QS_PREC_FP64
+        nbytes = self.lib.qsketch_workspace_bytes(ctypes.byref(self.cfg))
+        if nbytes == 0:
+            raise QSError(QS_ERR_INVALID, "qsketch_workspace_bytes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.handle = ctypes.c_void_p()
+        _check(self.lib.qsketch_create(ctypes.byref(self.cfg), ctypes.c_void_p(self.workspace.data_ptr()),
+                                       nbytes, _stream_ptr(stream), ctypes.byref(self.handle)),
+               "qsketch_create")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.qsketch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --------------------------------------------------------------- calls
+    def update(self, A, row0=0, col0=0, theta=1.0, eta=1.0, stream=None):
+        """Linear update with the block A (tensor (4, mb, nb) or 4 planes, plane 0 may be None)."""
+        ptrs, ld = _planes(A, self.f64)
+        if isinstance(A, torch.Tensor):
+            mb, nb = A.shape[1], A.shape[2]
+        else:
+            ref = next(t for t in A if t is not None)
+            mb, nb = ref.shape
+        return _check(self.lib.qsketch_update(self.handle, ptrs, ld, row0, col0, mb, nb, theta, eta,
+                                              _stream_ptr(stream)), "qsketch_update")
+
+    def rangefinder(self, kind="pseudo_qr", n_correction=3, stream=None):
+        return _check(self.lib.qrangefinder(self.handle, RANGEFINDERS.get(kind, kind), n_correction,
+                                            _stream_ptr(stream)), "qrangefinder")
+
+    def core(self, stream=None):
+        return _check(self.lib.qonepass_core(self.handle, _stream_ptr(stream)), "qonepass_core")
+
+    def error(self, A, out=None, stream=None):
+        """Relative error ||A - HX||_F/||A||_F; returns a 1-element CUDA float64 tensor."""
+        ptrs, ld = _planes(A, self.f64)
+        if out is None:
+            out = torch.empty(1, dtype=torch.float64, device=self.workspace.device)
+        _check(self.lib.qreconstruct_error(self.handle, ptrs, ld, ctypes.c_void_p(out.data_ptr()),
+                                           _stream_ptr(stream)), "qreconstruct_error")
+        return out
+
+    def device_status(self, stream=None):
+        return self.lib.qs_last_device_error(self.handle, _stream_ptr(stream))
+
+    def get(self, which):
+        """Tensor view (4, rows, cols) of a workspace object (no copy)."""
+        names = {"Y": QS_OBJ_Y, "W": QS_OBJ_W, "Omega": QS_OBJ_OMEGA, "Psi": QS_OBJ_PSI,
+                 "H": QS_OBJ_H, "X": QS_OBJ_X, "PsiH": QS_OBJ_PSIH, "scalars": QS_OBJ_SCALARS}
+        code = names.get(which, which)
+        ptr, ld, ps, dt = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(self.lib.qsketch_get(self.handle, code, ctypes.byref(ptr), ctypes.byref(ld),
+                                    ctypes.byref(ps), ctypes.byref(dt)), "qsketch_get")
+        c = self.cfg
+        shapes = {QS_OBJ_Y: (c.m, c.s), QS_OBJ_W: (c.l, c.n), QS_OBJ_OMEGA: (c.n, c.s),
+                  QS_OBJ_PSI: (c.l, c.m), QS_OBJ_H: (c.m, c.s), QS_OBJ_X: (c.s, c.n),
+                  QS_OBJ_PSIH: (c.l, c.s)}
+        dtype = torch.float64 if dt.value == QS_DT_F64 else torch.float32
+        esize = 8 if dtype == torch.float64 else 4
+        off = ptr.value - self.workspace.data_ptr()
+        if code == QS_OBJ_SCALARS:
+            return self.workspace[off:off + 16 * 8].view(torch.float64)
+        rows, cols = shapes[code]
+        assert ld.value == cols and ps.value == rows * cols
+        return self.workspace[off:off + 4 * rows * cols * esize].view(dtype).view(4, rows, cols)

@@ -1,0 +1,83 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for sm_103a, loads,
+exports every function include/qsketch.h declares, and validates arguments on the host
+before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2404_14783_gb300 import build as b
+    b.build()
+    import paper_2404_14783_gb300 as pkg
+    return pkg.load_library()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "qsketch.h")).read()
+    return re.findall(r"QS_API\s+[\w\s\*]+?\b(\w+)\s*\(", text)
+
+
+def test_header_declares_abi():
+    names = _declared()
+    import paper_2404_14783_gb300 as pkg
+    assert sorted(names) == sorted(pkg.ABI_SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_only_abi_symbols_exported(lib):
+    import subprocess
+    import paper_2404_14783_gb300 as pkg
+    out = subprocess.run(["nm", "-D", "--defined-only", pkg.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    text_syms = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert text_syms == set(pkg.ABI_SYMBOLS)
+
+
+def _cfg(**kw):
+    from paper_2404_14783_gb300 import QSConfig
+    d = dict(m=100, n=80, s=5, l=11, emb=0, prec=0, seed=1, pure=0, flags=0)
+    d.update(kw)
+    return QSConfig(**d)
+
+
+def test_workspace_bytes_and_validation(lib):
+    good = lib.qsketch_workspace_bytes(ctypes.byref(_cfg()))
+    assert good > 0 and good % 256 == 0
+    # FP32 modes store half-size objects
+    assert lib.qsketch_workspace_bytes(ctypes.byref(_cfg(prec=1))) < good
+    for bad in (dict(s=0), dict(l=4), dict(l=81), dict(m=0), dict(emb=2), dict(prec=9),
+                dict(flags=1), dict(pure=3), dict(s=2000, l=2000, m=5000, n=5000)):
+        assert lib.qsketch_workspace_bytes(ctypes.byref(_cfg(**bad))) == 0, bad
+
+
+def test_host_validation_before_launch(lib):
+    from paper_2404_14783_gb300.qsketch import QS_ERR_INVALID, QS_ERR_NOMEM
+    h = ctypes.c_void_p()
+    # invalid config, null workspace, misaligned workspace, too-small workspace
+    assert lib.qsketch_create(ctypes.byref(_cfg(s=0)), ctypes.c_void_p(256), 1 << 30, None,
+                              ctypes.byref(h)) == QS_ERR_INVALID
+    assert lib.qsketch_create(ctypes.byref(_cfg()), None, 1 << 30, None,
+                              ctypes.byref(h)) == QS_ERR_INVALID
+    assert lib.qsketch_create(ctypes.byref(_cfg()), ctypes.c_void_p(256 + 8), 1 << 30, None,
+                              ctypes.byref(h)) == QS_ERR_INVALID
+    assert lib.qsketch_create(ctypes.byref(_cfg()), ctypes.c_void_p(256), 16, None,
+                              ctypes.byref(h)) == QS_ERR_NOMEM
+    assert not h.value
+    planes = (ctypes.c_void_p * 4)()
+    assert lib.qsketch_update(None, planes, 10, 0, 0, 1, 1, 1.0, 1.0, None) == QS_ERR_INVALID
+    assert lib.qrangefinder(None, 0, 3, None) == QS_ERR_INVALID
+    assert lib.qonepass_core(None, None) == QS_ERR_INVALID
+    assert lib.qreconstruct_error(None, planes, 10, None, None) == QS_ERR_INVALID
+    assert lib.qsketch_destroy(None) == QS_ERR_INVALID
+    assert lib.qs_status_string(0) == b"ok"
+    assert lib.qs_version() >= 100
