@@ -1,0 +1,371 @@
+"""Benchmark of the one-pass randomized quaternion low-rank approximation on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--prec P]
+
+Workload c2 (quaternion A 8192 x 8192, FP32 planes, sigma_i = i^-2, k=50, s=101, l=203,
+Gaussian test matrices).  One step is one pass of the whole path: draw Omega and Psi,
+sketch Y = A Omega and W = Psi A from one read of A (Sec. 4.1), pseudo-QR rangefinder with
+three corrections (Alg. 1), QB stage X = (Psi H)^dagger W (Alg. 3) and the relative error
+||A - HX||_F / ||A||_F (Sec. 5, a second read of A).  The metric is A bytes per second
+through that step ("A GB/s"), with TFLOP/s and the FP32 SIMT path at equal error beside it.
+
+Under torchrun each rank runs its own independent replica (weak scaling, no collective on
+the data path); rank 0 prints one JSON line with the max time over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+N_SMS = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        d["_source"] = "measured"
+        return d
+    d = dict(PEAKS_FALLBACK)
+    d["_source"] = "fallback"
+    return d
+
+
+def workload(name):
+    import workloads as WL
+    w = dict(WL.WORKLOADS[name])
+    w["name"] = name
+    return w
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def algorithmic(cfg):
+    """Useful flops of the sketch (32 real flops per quaternion MAC, 24 if A is pure) and
+    A bytes as stored."""
+    m, n, s, l = cfg["m"], cfg["n"], cfg["s"], cfg["l"]
+    per = 24 if cfg.get("pure") else 32
+    esz = 8 if cfg["prec"] == "fp64" else 4
+    planes = 3 if cfg.get("pure") else 4
+    return per * m * n * (s + l), planes * m * n * esz
+
+
+def make_A(w, device, prec):
+    import numpy as np
+    import torch
+    import workloads as WL
+    dt = np.float64 if prec == "fp64" else np.float32
+    if w["name"] == "c1":
+        A = torch.as_tensor(WL.make_c1(seed=w["seed"]).astype(dt), device=device)
+    else:
+        A = WL.make_decay(w["m"], w["n"], seed=w["seed"], rank_cap=w.get("rank_cap", 1024),
+                          device=device, dtype=dt)
+    return A.contiguous()
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2404_14783_gb300 as pkg
+    pkg.load_library()     # fails loudly when the CUDA library is not built
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = workload(args.workload)
+    cfg = dict(m=w["m"], n=w["n"], s=w["s"], l=w["l"], prec=args.prec, emb=w["emb"],
+               pure=False)
+    A = make_A(w, dev, args.prec)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    qs = pkg.QSketch(cfg["m"], cfg["n"], cfg["s"], cfg["l"], emb=cfg["emb"], prec=args.prec,
+                     seed=w["seed"] + rank)
+    err_out = torch.zeros(1, dtype=torch.float64, device=dev)
+    E = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+
+    def step(ev=None, A_in=A):
+        if ev: ev[0].record(stream)
+        qs.reset(seed=w["seed"] + rank)                    # draw Omega, Psi; zero Y, W
+        if ev: ev[1].record(stream)
+        qs.update(A_in, theta=0.0)                         # fused one-read sketch
+        if ev: ev[2].record(stream)
+        qs.rangefinder(args.rangefinder, 3)
+        if ev: ev[3].record(stream)
+        qs.core()
+        if ev: ev[4].record(stream)
+        qs.error(A_in, out=err_out)
+        if ev: ev[5].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    launches0 = pkg.launch_count()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    stage_ms = {k: 0.0 for k in ("draw", "sketch", "rangefinder", "core", "error")}
+    per_step_events = []
+    t0.record(stream)
+    for _ in range(args.steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        step(ev)
+        per_step_events.append(ev)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = pkg.launch_count() - launches0
+    clocks = sampler.stop()
+    total_ms = t0.elapsed_time(t1)
+    for ev in per_step_events:
+        for i, k in enumerate(stage_ms):
+            stage_ms[k] += ev[i].elapsed_time(ev[i + 1]) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    final_err = float(err_out.item())
+    status = qs.device_status()
+
+    # end to end through the public API: pinned host A copied in every step, error read back
+    A_host = A.cpu().pin_memory()
+    A_dev2 = torch.empty_like(A)
+    err_host = torch.zeros(1, dtype=torch.float64).pin_memory()
+    for _ in range(max(1, args.warmup // 2)):
+        A_dev2.copy_(A_host, non_blocking=True)
+        step(A_in=A_dev2)
+        err_host.copy_(err_out, non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        A_dev2.copy_(A_host, non_blocking=True)
+        step(A_in=A_dev2)
+        err_host.copy_(err_out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    del A_dev2, A_host
+
+    flops, abytes = algorithmic(cfg)
+    ms = total_ms / args.steps
+    gbs = world * abytes / (ms * 1e-3) / 1e9
+    result = dict(ms=ms, gbs=gbs, stage_ms=stage_ms, clocks=clocks, launches=launches / args.steps,
+                  final_err=final_err, status=status, e2e_ms=e2e_ms, flops=flops, abytes=abytes,
+                  cfg=cfg, w=w, e2e_gbs=world * abytes / (e2e_ms * 1e-3) / 1e9,
+                  h2d=A.numel() * A.element_size(), d2h=8)
+    # FP32 SIMT comparison path at equal error (rank 0 only, device resident)
+    if rank == 0 and args.prec != "fp32" and not args.no_compare:
+        qs32 = pkg.QSketch(cfg["m"], cfg["n"], cfg["s"], cfg["l"], emb=cfg["emb"], prec="fp32",
+                           seed=w["seed"])
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        for it in range(2):
+            s0.record(stream)
+            qs32.reset(seed=w["seed"])
+            qs32.update(A, theta=0.0)
+            s1.record(stream)
+            qs32.rangefinder(args.rangefinder, 3)
+            qs32.core()
+            e32 = float(qs32.error(A).item())
+        torch.cuda.synchronize()
+        result["fp32"] = dict(sketch_ms=s0.elapsed_time(s1), err=e32)
+        qs32.close()
+    qs.close()
+    return result
+
+
+def cpu_baseline(w, rows, reps=1):
+    """The FP64 oracle on the host cores on a bounded sample: the first ``rows`` rows of the
+    workload's matrix with the same s and l.  Returns (A GB/s, seconds, threads)."""
+    import numpy as np
+    import oracle as O
+    import workloads as WL
+    if w["name"] == "c1":
+        A = WL.make_c1(seed=w["seed"])[:, :rows]
+    else:
+        A = WL.make_decay(w["m"], w["n"], seed=w["seed"], rank_cap=w.get("rank_cap", 1024),
+                          dtype=np.float64)[:, :rows]
+    m, n = A.shape[1], A.shape[2]
+    Om = O.draw_embedding(n, w["s"], O.EMB_GAUSSIAN, O.STREAM_OMEGA, w["seed"])
+    Psi = O.draw_embedding(w["l"], m, O.EMB_GAUSSIAN, O.STREAM_PSI, w["seed"])
+    times = []
+    for _ in range(reps):
+        t = time.perf_counter()
+        O.onepass(A, Om, Psi, "pseudo_qr", 3)
+        times.append(time.perf_counter() - t)
+    sec = min(times)
+    abytes = 4 * m * n * 4      # A bytes as stored in the FP32 workload
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return abytes / sec / 1e9, sec, threads, f"first {m} rows x {n} cols of {w['name']}"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--rangefinder", default="pseudo_qr")
+    ap.add_argument("--cpu-rows", type=int, default=1024)
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    w = workload(args.workload)
+    metric = "one-pass quaternion approx: A GB/s & TFLOPS, split-BF16 vs FP32 at equal error"
+    config = {"workload": f"{w['name']}: quaternion A {w['m']}x{w['n']} FP32 planes, "
+                          f"sigma_i=i^-2, k={w['k']}, s={w['s']}, l={w['l']}, Gaussian Omega/Psi",
+              "m": w["m"], "n": w["n"], "s": w["s"], "l": w["l"], "prec": args.prec,
+              "rangefinder": args.rangefinder, "n_correction": 3,
+              "l2": "inputs larger than L2 (A is 1.07 GB per step)", "parallelism": "replicas"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        vals = []
+        for i in range(args.warmup + args.steps):
+            gbs, sec, thr, sample = cpu_baseline(w, args.cpu_rows)
+            if i >= args.warmup:
+                vals.append((gbs, sec))
+        v = statistics.median([g for g, _ in vals])
+        out = {"impl": "reference", "metric": metric, "value": v, "unit": "GB/s",
+               "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": statistics.median([s for _, s in vals]) * 1e3,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": config,
+               "cpu_baseline": {"value": v, "unit": "GB/s", "cores": thr, "kind": "oracle",
+                                "sample": sample},
+               "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
+        return
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    peaks = load_peaks()
+    flops, abytes = res["flops"], res["abytes"]
+    sk_ms = res["stage_ms"]["sketch"]
+    tc = args.prec in ("bf16", "bf16x3")
+    products = {"bf16x3": 3 if w["emb"] == "gaussian" else 2, "bf16": 1}.get(args.prec, 1)
+    if tc:
+        peak = peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
+        roof = {"bound": "tensor", "achieved": flops / (sk_ms * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s"}
+    else:
+        clk = peaks.get("sm_max_mhz", 2070.0)
+        per_sm = FP32_LANES_PER_SM * 2 if args.prec == "fp32" else 4.0
+        peak = N_SMS * per_sm * clk * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops / (sk_ms * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = "fused sketch (qsketch_update)"
+    roof["peak_source"] = peaks["_source"] + (" bf16 burst" if tc else " derived FP32 ALU")
+    out = {"metric": metric, "value": res["gbs"], "unit": "GB/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": {"bf16x3": "bf16x3+f64", "bf16": "bf16+f64", "fp32": "f32+f64",
+                     "fp64": "f64"}[args.prec],
+           "data": "synthetic", "config": config, "roofline": roof,
+           "tflops": {"useful_step": world * flops / (res["ms"] * 1e-3) / 1e12,
+                      "useful_sketch": flops / (sk_ms * 1e-3) / 1e12,
+                      "issued_sketch": products * flops / (sk_ms * 1e-3) / 1e12 if tc else None},
+           "sketch_gbs": abytes / (sk_ms * 1e-3) / 1e9,
+           "stages_ms": res["stage_ms"], "final_rel_error": res["final_err"],
+           "device_status": res["status"],
+           "e2e": {"value": res["e2e_gbs"], "unit": "GB/s", "h2d_bytes_per_step": res["h2d"],
+                   "d2h_bytes_per_step": res["d2h"]},
+           "gpu_launches": res["launches"], "clocks": res["clocks"]}
+    if "fp32" in res:
+        out["fp32_path"] = {"sketch_ms": res["fp32"]["sketch_ms"],
+                            "final_rel_error": res["fp32"]["err"],
+                            "sketch_speedup_vs_fp32": res["fp32"]["sketch_ms"] / sk_ms,
+                            "error_ratio": res["final_err"] / res["fp32"]["err"]}
+    if not args.no_cpu:
+        gbs, sec, thr, sample = cpu_baseline(w, args.cpu_rows)
+        out["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": thr, "kind": "oracle",
+                               "sample": sample, "seconds": sec}
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -167,6 +167,10 @@ QS_API qs_status qsketch_destroy(qs_handle_t h);
 /* Static description of a status code. */
 QS_API const char* qs_status_string(qs_status st);
 
+/* Number of kernel launches this library has enqueued in the process so far (all handles,
+ * all streams).  Tracing aid: the difference around a region counts its launches. */
+QS_API int64_t qs_launch_count(void);
+
 /* Library version as 10000*major + 100*minor + patch. */
 QS_API int32_t qs_version(void);
 

@@ -3,6 +3,7 @@
 // (Alg. 3 with Alg. QLEQ) and the error evaluation (Sec. 5).  All work is enqueued on the
 // caller's stream; nothing here synchronises except qs_last_device_error.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -13,6 +14,9 @@
 #include "qs_sketch_tc.cuh"
 
 using namespace qs;
+
+static std::atomic<int64_t> g_launches{0};
+void qs::count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace {
 
@@ -420,6 +424,8 @@ const char* qs_status_string(qs_status st) {
   }
   return "unknown status";
 }
+
+int64_t qs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int32_t qs_version(void) { return 100; }
 

@@ -89,6 +89,8 @@ struct qs_handle_s {
 };
 
 namespace qs {
+// Process-wide count of kernel launches (qs_launch_count); every launcher bumps it.
+void count_launch(int n = 1);
 // Launchers implemented in the .cu files (return cudaError_t of the launch).
 struct GemmDesc {
   int64_t M, N, K;

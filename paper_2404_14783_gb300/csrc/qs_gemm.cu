@@ -237,6 +237,7 @@ cudaError_t launch_t(const GemmDesc& d, cudaStream_t st) {
     qgemm_kernel<ACC, TA, TB, TC, true><<<grid, 256, 0, st>>>(d);
   else
     qgemm_kernel<ACC, TA, TB, TC, false><<<grid, 256, 0, st>>>(d);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -270,6 +271,7 @@ cudaError_t launch_scale(void* c, int f64, int64_t rows, int64_t cols, int64_t l
     scale_kernel<double><<<blocks, 256, 0, st>>>((double*)c, rows, cols, ld, ps, beta);
   else
     scale_kernel<float><<<blocks, 256, 0, st>>>((float*)c, rows, cols, ld, ps, (float)beta);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -283,6 +285,7 @@ cudaError_t launch_draw(void* out, int f64, int64_t rows, int64_t cols, int kind
     draw_kernel<double><<<blocks, 256, 0, st>>>((double*)out, rows, cols, kind, stream, k0, k1);
   else
     draw_kernel<float><<<blocks, 256, 0, st>>>((float*)out, rows, cols, kind, stream, k0, k1);
+  count_launch();
   return cudaGetLastError();
 }
 

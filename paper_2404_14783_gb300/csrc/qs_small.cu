@@ -352,12 +352,14 @@ cudaError_t launch_qchol(const double* G, int64_t ldg, int64_t psg, double* L, i
                          int32_t* status, double* scalars, int fail_bits, cudaStream_t st) {
   qchol_kernel<<<1, 1024, 0, st>>>(G, ldg, psg, L, ldl, psl, n, complex_only, allow_shift,
                                    shift_rows, status, scalars, fail_bits);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_qtrinv(const double* L, int64_t ldl, int64_t psl, double* X, int64_t ldx,
                           int64_t psx, int n, const int32_t* status, cudaStream_t st) {
   qtrinv_kernel<<<1, 1024, 0, st>>>(L, ldl, psl, X, ldx, psx, n, status);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -371,6 +373,7 @@ cudaError_t launch_qpower(const double* L, int64_t ldl, int64_t psl, int n, int 
     if (e != cudaSuccess) return e;
   }
   qpower_kernel<<<1, 64, smem, st>>>(L, ldl, psl, n, iters, slot, kappa_stop, status, scalars);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -378,6 +381,7 @@ cudaError_t launch_qaxpby_eye(const double* X, int64_t ldx, int64_t psx, double*
                               int64_t psm, int n, const double* scalars, int slot, cudaStream_t st) {
   const int blocks = std::max(1, std::min(64, (n * n + 255) / 256));
   qaxpby_eye_kernel<<<blocks, 256, 0, st>>>(X, ldx, psx, M, ldm, psm, n, scalars, slot);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -394,6 +398,7 @@ cudaError_t launch_qconjT(const void* S, int s_f64, int64_t lds, int64_t pss, vo
     qconjT_kernel<float, double><<<blocks, 256, 0, st>>>((const float*)S, lds, pss, (double*)D, ldd, psd, r, c);
   else
     qconjT_kernel<float, float><<<blocks, 256, 0, st>>>((const float*)S, lds, pss, (float*)D, ldd, psd, r, c);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -410,11 +415,13 @@ cudaError_t launch_qcopy(const void* S, int s_f64, int64_t lds, int64_t pss, voi
     qcopy_kernel<float, double><<<blocks, 256, 0, st>>>((const float*)S, lds, pss, (double*)D, ldd, psd, r, c);
   else
     qcopy_kernel<float, float><<<blocks, 256, 0, st>>>((const float*)S, lds, pss, (float*)D, ldd, psd, r, c);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_clear_stop(int32_t* status, cudaStream_t st) {
   clear_stop_kernel<<<1, 32, 0, st>>>(status);
+  count_launch();
   return cudaGetLastError();
 }
 

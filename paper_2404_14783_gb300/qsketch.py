@@ -28,7 +28,7 @@ RANGEFINDERS = {"pseudo_qr": QS_RF_PSEUDO_QR, "pseudo_svd": QS_RF_PSEUDO_SVD}
 
 ABI_SYMBOLS = ("qsketch_workspace_bytes", "qsketch_create", "qsketch_update", "qrangefinder",
                "qonepass_core", "qreconstruct_error", "qsketch_get", "qs_last_device_error",
-               "qsketch_destroy", "qs_status_string", "qs_version")
+               "qsketch_destroy", "qs_status_string", "qs_launch_count", "qs_version")
 
 
 class QSConfig(ctypes.Structure):
@@ -69,11 +69,17 @@ def load_library(path=LIB_PATH):
     lib.qs_status_string.argtypes = [I32]
     lib.qs_status_string.restype = ctypes.c_char_p
     lib.qs_version.restype = I32
+    lib.qs_launch_count.restype = I64
     for name in ("qsketch_create", "qsketch_update", "qrangefinder", "qonepass_core",
                  "qreconstruct_error", "qsketch_get", "qs_last_device_error", "qsketch_destroy"):
         getattr(lib, name).restype = I32
     _lib = lib
     return lib
+
+
+def launch_count():
+    """Kernel launches the library has enqueued in this process."""
+    return int(load_library().qs_launch_count())
 
 
 def _status_string(code):
@@ -133,6 +139,18 @@ class QSketch:
         _check(self.lib.qsketch_create(ctypes.byref(self.cfg), ctypes.c_void_p(self.workspace.data_ptr()),
                                        nbytes, _stream_ptr(stream), ctypes.byref(self.handle)),
                "qsketch_create")
+
+    def reset(self, seed=None, stream=None):
+        """Re-run qsketch_create on the same workspace: redraw Omega and Psi (same seed unless
+        given) and zero Y and W."""
+        if seed is not None:
+            self.cfg.seed = seed
+        if self.handle:
+            self.lib.qsketch_destroy(self.handle)
+        self.handle = ctypes.c_void_p()
+        _check(self.lib.qsketch_create(ctypes.byref(self.cfg), ctypes.c_void_p(self.workspace.data_ptr()),
+                                       self.workspace.numel(), _stream_ptr(stream),
+                                       ctypes.byref(self.handle)), "qsketch_create")
 
     def close(self):
         if getattr(self, "handle", None):
