@@ -52,7 +52,8 @@ size_t plan(const qs_config& c, qs_handle_s* h) {
   size_t o_scal = take(sizeof(double) * kScCount);
   size_t o_om = take(4 * n * s * es);
   size_t o_psi = take(4 * l * m * es);
-  size_t o_y = take(4 * m * s * es);
+  const size_t sy = (s + 3) / 4 * 4;   // Y rows padded to 16 bytes (vector reductions)
+  size_t o_y = take(4 * m * sy * es);
   size_t o_w = take(4 * l * n * es);
   size_t o_h = take(4 * m * s * es);
   size_t o_x = take(4 * s * n * es);
@@ -100,7 +101,8 @@ struct Ctx {
   bool f64;
   Mat omega() const { return {h->ws + h->off_omega, s, n * s, f64}; }
   Mat psi() const { return {h->ws + h->off_psi, m, l * m, f64}; }
-  Mat Y() const { return {h->ws + h->off_y, s, m * s, f64}; }
+  int64_t sy() const { return (s + 3) / 4 * 4; }
+  Mat Y() const { return {h->ws + h->off_y, sy(), m * sy(), f64}; }
   Mat W() const { return {h->ws + h->off_w, n, l * n, f64}; }
   Mat H() const { return {h->ws + h->off_h, s, m * s, f64}; }
   Mat X() const { return {h->ws + h->off_x, n, s * n, f64}; }
@@ -114,6 +116,8 @@ struct Ctx {
     if (i < 3) return {base + i * align_up(4 * l * s * 8), s, l * s, 1};
     return {base + 3 * align_up(4 * l * s * 8), l, s * l, 1};
   }
+  // FP64-class accumulation: native FP64 in the FP64 mode, double-float otherwise
+  int acc_hi() const { return f64 ? 1 : 2; }
   int32_t* status() const { return h->d_status(); }
   double* scalars() const { return h->d_scalars(); }
 };
@@ -121,19 +125,20 @@ struct Ctx {
 int pick_splits(int64_t M, int64_t N, int64_t K) {
   const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
   int64_t sp = (2 * kNumSMs + tiles - 1) / tiles;
-  sp = std::min<int64_t>(sp, std::max<int64_t>(1, K / 128));
+  sp = std::min<int64_t>(sp, std::max<int64_t>(1, K / 32));
   return (int)std::max<int64_t>(1, std::min<int64_t>(sp, 1024));
 }
 
 // C = alpha * op(A) B + beta C on workspace matrices (all FP64 unless stated by the views).
+// acc: 0 = FP32 (all operands FP32), 1 = FP64, 2 = double-float on the FP32 pipes.
 cudaError_t gemm(const Ctx& x, const Mat& A, bool conjA, const Mat& B, const Mat& C, int64_t M,
-                 int64_t N, int64_t K, double alpha, double beta, bool acc64, bool allow_split) {
+                 int64_t N, int64_t K, double alpha, double beta, int acc, bool allow_split) {
   GemmDesc d{};
   d.M = M; d.N = N; d.K = K;
   A.cplanes(d.a); d.lda = A.ld; d.a_f64 = A.f64; d.conj_a = conjA;
   B.cplanes(d.b); d.ldb = B.ld; d.b_f64 = B.f64;
   C.planes(d.c); d.ldc = C.ld; d.c_f64 = C.f64;
-  d.alpha = alpha; d.beta = beta; d.acc_f64 = acc64;
+  d.alpha = alpha; d.beta = beta; d.acc_f64 = acc;
   d.splits = allow_split ? pick_splits(M, N, K) : 1;
   d.epi = 0; d.err = nullptr;
   if (d.splits > 1 && beta != 1.0) {
@@ -145,7 +150,7 @@ cudaError_t gemm(const Ctx& x, const Mat& A, bool conjA, const Mat& B, const Mat
 
 // Gram G = A* A of a tall m x s matrix (FP64 result).
 cudaError_t gram(const Ctx& x, const Mat& A, int64_t rows, int64_t cols, const Mat& G) {
-  return gemm(x, A, true, A, G, cols, cols, rows, 1.0, 0.0, true, true);
+  return gemm(x, A, true, A, G, cols, cols, rows, 1.0, 0.0, x.acc_hi(), true);
 }
 
 qs_status pseudo_qr(const Ctx& x, int ncorr) {
@@ -162,16 +167,16 @@ qs_status pseudo_qr(const Ctx& x, int ncorr) {
   QS_CU(launch_qtrinv((double*)L.p, L.ld, L.ps, (double*)Li.p, Li.ld, Li.ps, s, st, x.st));
   QS_CU(launch_qconjT(Li.p, 1, Li.ld, Li.ps, D.p, 1, D.ld, D.ps, s, s, x.st));   // D = R^{-1}
   // second Cholesky-QR pass on T = Y R^{-1} restores orthogonality of the Q factor
-  QS_CU(gemm(x, Y, false, D, T, x.m, s, s, 1.0, 0.0, true, false));
+  QS_CU(gemm(x, Y, false, D, T, x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
   QS_CU(gram(x, T, x.m, s, G));
   QS_CU(launch_qchol((double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s, 1, 0, 2.0 * x.m, st,
                      sc, kDevRank | kDevStopCorr, x.st));
   QS_CU(launch_qtrinv((double*)L.p, L.ld, L.ps, (double*)Li.p, Li.ld, Li.ps, s, st, x.st));
   QS_CU(launch_qconjT(Li.p, 1, Li.ld, Li.ps, R2.p, 1, R2.ld, R2.ps, s, s, x.st));
-  QS_CU(gemm(x, D, false, R2, D2, s, s, s, 1.0, 0.0, true, false));  // D2 = R^{-1} of Y_c
+  QS_CU(gemm(x, D, false, R2, D2, s, s, s, 1.0, 0.0, x.acc_hi(), false));  // D2 = R^{-1} of Y_c
   // (Alg. 1 step 3) H_0 = Y D2; its quaternion Gram G_0 = R2^{-*} (T*T) R2^{-1}
-  QS_CU(gemm(x, Li, false, G, Tm, s, s, s, 1.0, 0.0, true, false));
-  QS_CU(gemm(x, Tm, false, R2, G0, s, s, s, 1.0, 0.0, true, false));
+  QS_CU(gemm(x, Li, false, G, Tm, s, s, s, 1.0, 0.0, x.acc_hi(), false));
+  QS_CU(gemm(x, Tm, false, R2, G0, s, s, s, 1.0, 0.0, x.acc_hi(), false));
   Mat Dcur = D2, Dnext = D;
   Mat Gk = G0;
   // (Alg. 1 step 4) corrections H <- (1-eps) H + eps (H^dagger)* = H ((1-eps) I + eps G^{-1})
@@ -180,18 +185,18 @@ qs_status pseudo_qr(const Ctx& x, int ncorr) {
                        st, sc, kDevRank | kDevStopCorr, x.st));
     QS_CU(launch_qpower((double*)L.p, L.ld, L.ps, s, 3, kScEps0 + k, kKappaStop, st, sc, x.st));
     QS_CU(launch_qtrinv((double*)L.p, L.ld, L.ps, (double*)Li.p, Li.ld, Li.ps, s, st, x.st));
-    QS_CU(gemm(x, Li, true, Li, Gi, s, s, s, 1.0, 0.0, true, false));  // G^{-1} = L^{-*} L^{-1}
+    QS_CU(gemm(x, Li, true, Li, Gi, s, s, s, 1.0, 0.0, x.acc_hi(), false));  // G^{-1} = L^{-*} L^{-1}
     QS_CU(launch_qaxpby_eye((double*)Gi.p, Gi.ld, Gi.ps, (double*)M.p, M.ld, M.ps, s, sc,
                             kScEps0 + k, x.st));
-    QS_CU(gemm(x, Dcur, false, M, Dnext, s, s, s, 1.0, 0.0, true, false));
+    QS_CU(gemm(x, Dcur, false, M, Dnext, s, s, s, 1.0, 0.0, x.acc_hi(), false));
     std::swap(Dcur, Dnext);
     if (k + 1 < ncorr) {  // Gram of the explicitly formed H_{k+1} = Y D
-      QS_CU(gemm(x, Y, false, Dcur, T, x.m, s, s, 1.0, 0.0, true, false));
+      QS_CU(gemm(x, Y, false, Dcur, T, x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
       QS_CU(gram(x, T, x.m, s, G));
       Gk = G;
     }
   }
-  QS_CU(gemm(x, Y, false, Dcur, x.H(), x.m, s, s, 1.0, 0.0, true, false));
+  QS_CU(gemm(x, Y, false, Dcur, x.H(), x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
   return QS_OK;
 }
 
@@ -203,26 +208,35 @@ qs_status core_solve(const Ctx& x) {
             R2 = x.small(5), S = x.small(6);
   int32_t* st = x.status();
   double* sc = x.scalars();
-  // (Alg. 3 step 2) P = Psi H
-  QS_CU(gemm(x, x.psi(), false, x.H(), P, l, s, x.m, 1.0, 0.0, true, true));
+  // (Alg. 3 step 2) P = Psi H.  FP32 modes: the inputs carry FP32-level error and
+  // kappa(P) is small, so the product runs in FP32 and is widened for the small solve.
+  if (x.f64) {
+    QS_CU(gemm(x, x.psi(), false, x.H(), P, l, s, x.m, 1.0, 0.0, 1, true));
+  } else {
+    const Mat P32{x.core(0).p, s, l * s, 0};
+    QS_CU(gemm(x, x.psi(), false, x.H(), P32, l, s, x.m, 1.0, 0.0, 0, true));
+    QS_CU(launch_qcopy(P32.p, 0, P32.ld, P32.ps, P.p, 1, P.ld, P.ps, l, s, x.st));
+  }
   // Alg. QLEQ on chi_P: QR of P (quaternion Cholesky-QR, twice), X = R^{-1} Q* W
   QS_CU(gram(x, P, l, s, G));
   QS_CU(launch_qchol((double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s, 0, 1, 2.0 * l, st, sc,
                      kDevRank, x.st));
   QS_CU(launch_qtrinv((double*)L.p, L.ld, L.ps, (double*)L1i.p, L1i.ld, L1i.ps, s, st, x.st));
   QS_CU(launch_qconjT(L1i.p, 1, L1i.ld, L1i.ps, R1.p, 1, R1.ld, R1.ps, s, s, x.st));
-  QS_CU(gemm(x, P, false, R1, Tp, l, s, s, 1.0, 0.0, true, false));
+  QS_CU(gemm(x, P, false, R1, Tp, l, s, s, 1.0, 0.0, x.acc_hi(), false));
   QS_CU(gram(x, Tp, l, s, G));
   QS_CU(launch_qchol((double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s, 0, 0, 2.0 * l, st, sc,
                      kDevRank, x.st));
   QS_CU(launch_qtrinv((double*)L.p, L.ld, L.ps, (double*)L2i.p, L2i.ld, L2i.ps, s, st, x.st));
   QS_CU(launch_qconjT(L2i.p, 1, L2i.ld, L2i.ps, R2.p, 1, R2.ld, R2.ps, s, s, x.st));
-  QS_CU(gemm(x, Tp, false, R2, Qp, l, s, s, 1.0, 0.0, true, false));       // Q (l x s)
-  QS_CU(gemm(x, L2i, false, L1i, S, s, s, s, 1.0, 0.0, true, false));      // (R^{-1})* = L2^{-1} L1^{-1}
-  QS_CU(gemm(x, Qp, false, S, ZT, l, s, s, 1.0, 0.0, true, false));        // (P^dagger)* = Q R^{-*}
-  QS_CU(launch_qconjT(ZT.p, 1, ZT.ld, ZT.ps, Z.p, 1, Z.ld, Z.ps, (int)l, s, x.st));  // P^dagger
+  QS_CU(gemm(x, Tp, false, R2, Qp, l, s, s, 1.0, 0.0, x.acc_hi(), false));       // Q (l x s)
+  QS_CU(gemm(x, L2i, false, L1i, S, s, s, s, 1.0, 0.0, x.acc_hi(), false));      // (R^{-1})* = L2^{-1} L1^{-1}
+  QS_CU(gemm(x, Qp, false, S, ZT, l, s, s, 1.0, 0.0, x.acc_hi(), false));        // (P^dagger)* = Q R^{-*}
+  // P^dagger (s x l), in the working precision of W
+  const Mat Zw{Z.p, Z.ld, Z.ps, x.f64 ? 1 : 0};
+  QS_CU(launch_qconjT(ZT.p, 1, ZT.ld, ZT.ps, Zw.p, Zw.f64, Zw.ld, Zw.ps, (int)l, s, x.st));
   // X = P^dagger W (s x n)
-  QS_CU(gemm(x, Z, false, x.W(), x.X(), s, x.n, l, 1.0, 0.0, true, true));
+  QS_CU(gemm(x, Zw, false, x.W(), x.X(), s, x.n, l, 1.0, 0.0, x.f64 ? 1 : 0, true));
   return QS_OK;
 }
 
@@ -265,7 +279,7 @@ qs_status qsketch_create(const qs_config* cfg, void* workspace, size_t bytes, vo
   cudaError_t e = cudaMemsetAsync(h->ws, 0, h->off_omega, st);
   if (e == cudaSuccess) e = launch_draw(x.omega().p, f64, cfg->n, cfg->s, cfg->emb, kStreamOmega, cfg->seed, st);
   if (e == cudaSuccess) e = launch_draw(x.psi().p, f64, cfg->l, cfg->m, cfg->emb, kStreamPsi, cfg->seed, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(x.Y().p, 0, 4 * cfg->m * cfg->s * h->esize, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x.Y().p, 0, 4 * cfg->m * x.sy() * h->esize, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(x.W().p, 0, 4 * cfg->l * cfg->n * h->esize, st);
   if (e == cudaSuccess && tc_mode(cfg->prec)) e = tc_pack_embeddings(*h, st);
   if (e != cudaSuccess) {
@@ -287,7 +301,7 @@ qs_status qsketch_update(qs_handle_t h, const void* const A_planes[4], int64_t l
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Ctx x{h, st, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64};
   if (theta != 1.0) {
-    QS_CU(launch_scale(x.Y().p, x.f64, c.m, c.s, c.s, c.m * c.s, theta, st));
+    QS_CU(launch_scale(x.Y().p, x.f64, c.m, c.s, x.Y().ld, x.Y().ps, theta, st));
     QS_CU(launch_scale(x.W().p, x.f64, c.l, c.n, c.n, c.l * c.n, theta, st));
   }
   if (mb == 0 || nb == 0) return QS_OK;
@@ -304,7 +318,7 @@ qs_status qsketch_update(qs_handle_t h, const void* const A_planes[4], int64_t l
   if (c.pure) d.a[0] = nullptr;
   d.lda = lda; d.a_f64 = x.f64; d.conj_a = 0;
   Om.cplanes(d.b, col0 * c.s); d.ldb = c.s; d.b_f64 = x.f64;
-  Y.planes(d.c, row0 * c.s); d.ldc = c.s; d.c_f64 = x.f64;
+  Y.planes(d.c, row0 * Y.ld); d.ldc = Y.ld; d.c_f64 = x.f64;
   d.alpha = eta; d.beta = 1.0; d.acc_f64 = x.f64;
   d.splits = pick_splits(d.M, d.N, d.K);
   QS_CU(launch_qgemm(d, st));

@@ -99,7 +99,7 @@ struct GemmDesc {
   const void* b[4]; int64_t ldb; int b_f64;
   void* c[4]; int64_t ldc; int c_f64;
   double alpha, beta;
-  int acc_f64;   // accumulate in FP64 (else FP32)
+  int acc_f64;   // accumulator: 0 = FP32, 1 = FP64, 2 = df64 (double-float on FP32 pipes)
   int splits;    // >1: split-K with atomic accumulation into C (C must be pre-scaled)
   // epi == 1: C holds a matrix E (read only); instead of writing, accumulate
   // sum |E - alpha*acc|^2 into err[0] and sum |E|^2 into err[1] (FP64 atomics).

@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "qs_common.cuh"
+#include "qs_df64.cuh"
 
 namespace qs {
 
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(256) qgemm_kernel(GemmDesc g) {
           for (int q = 0; q < 4; ++q) {
             const TC* E = static_cast<const TC*>(g.c[q]);
             const double e = E ? double(E[m * g.ldc + n]) : 0.0;
-            const double d = e - double(alpha * acc[q][i][j]);
+            const double d = e - static_cast<double>(alpha * acc[q][i][j]);
             se += d * d;
             sa += e * e;
           }
@@ -167,11 +168,11 @@ __global__ void __launch_bounds__(256) qgemm_kernel(GemmDesc g) {
         TC* dst = static_cast<TC*>(g.c[q]) + m * g.ldc + n;
         const ACC v = alpha * acc[q][i][j];
         if (g.splits > 1) {
-          atomicAdd(dst, TC(v));
+          atomicAdd(dst, static_cast<TC>(v));
         } else if (g.beta == 0.0) {
-          *dst = TC(v);
+          *dst = static_cast<TC>(v);
         } else {
-          *dst = TC(v + ACC(g.beta) * ACC(*dst));
+          *dst = static_cast<TC>(v + ACC(g.beta) * ACC(*dst));
         }
       }
     }
@@ -255,10 +256,12 @@ cudaError_t launch_b(const GemmDesc& d, cudaStream_t st) {
 cudaError_t launch_qgemm(const GemmDesc& d, cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0) return cudaSuccess;
   if (d.K <= 0 || d.splits < 1) return cudaErrorInvalidValue;
-  if (!d.acc_f64) {
+  if (d.acc_f64 == 0) {
     if (d.a_f64 || d.b_f64 || d.c_f64) return cudaErrorInvalidValue;
     return launch_t<float, float, float, float>(d, st);
   }
+  if (d.acc_f64 == 2)
+    return d.a_f64 ? launch_b<df64, double>(d, st) : launch_b<df64, float>(d, st);
   return d.a_f64 ? launch_b<double, double>(d, st) : launch_b<double, float>(d, st);
 }
 

@@ -1,11 +1,635 @@
-// Tensor-core fused sketch (placeholder until the tcgen05 kernel lands).
+// Fused one-read sketch on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// Computes, for a block A_b of the quaternion matrix A (Sec. 4.1, eq. Y = A Omega, W = Psi A):
+//     Y[rows, :] += eta * A_b Omega[cols, :]      W[:, cols] += eta * Psi[:, rows] A_b
+// reading every A tile from HBM exactly once.  The quaternion products are expanded into
+// real products of component planes with the signs of the Hamilton product (Sec. 2): for
+// output plane q of Y, Y_q = sum_p sign * A_p Omega_pi(q,p), and for W,
+// W_q = sum_p sign * Psi_pi'(q,p) A_p.  Each real product is one tcgen05.mma whose negative
+// signs come from the instruction descriptor's negate-A bit, so only the four planes of
+// Omega and Psi are stored (no expanded block matrix).
+//
+// Precision: A (FP32) is split on chip into BF16 hi = bf16(a) and lo = bf16(a - hi); the
+// test matrices are packed the same way.  QS_PREC_BF16X3 accumulates hi*hi + lo*hi + hi*lo
+// in FP32 (TMEM); QS_PREC_BF16 only hi*hi.
+//
+// One CTA per SM (persistent).  Tile = 128 rows x 64 columns of A, all four planes:
+//   warp 0      TMA producer: A tile (FP32, 4 x 32 KB) and a 3-stage ring of BF16 operand
+//               chunks of Psi (128 rows x 64) and Omega^T (NS rows x 64), SW128 layout.
+//   warp 1      TMEM owner and MMA issuer (one elected thread).
+//   warps 2-5   converters: FP32 -> BF16 hi/lo in place (an 8-row group of 2 KB becomes a
+//               1 KB hi atom and a 1 KB lo atom, so the operand's 8-row stride is 2048 B).
+//   warps 6-9   epilogue: TMEM -> registers -> red.global.add.v4.f32 into Y and W (L2).
+// TMEM (512 columns) is used by two phases per tile: the W phase (accumulators W_q for
+// 128-row slices of Psi: N = 64 columns each) and then the Y phase (Y_q: N = NS columns).
+// Every wait is bounded (2 s of %globaltimer); on expiry the CTA records QS_ERR_TIMEOUT in
+// the workspace status word, stops issuing work, waits (bounded) for its own copies and
+// MMAs, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+
 #include "qs_sketch_tc.cuh"
 
 namespace qs {
-size_t tc_pack_bytes(const qs_config&) { return 0; }
-cudaError_t tc_pack_embeddings(const qs_handle_s&, cudaStream_t) { return cudaSuccess; }
-qs_status tc_sketch_update(const qs_handle_s&, const void* const*, int64_t, int64_t, int64_t,
-                           int64_t, int64_t, double, cudaStream_t) {
-  return QS_ERR_UNSUPPORTED;
+
+namespace {
+
+constexpr int kBM = 128, kBN = 64;
+constexpr int kStages = 3;
+constexpr int kStageBytes = 32768;
+constexpr int kABytes = 4 * 32768;
+constexpr int kThreads = 320;
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+// Hamilton-product tables (Sec. 2).  Y = A Omega: output plane q, Omega plane b -> A plane a.
+// W = Psi A: output plane q, Psi plane a -> A plane b.  Signs +1 / -1.
+__constant__ int8_t kYPlaneA[4][4] = {{0, 1, 2, 3}, {1, 0, 3, 2}, {2, 3, 0, 1}, {3, 2, 1, 0}};
+__constant__ int8_t kYSign[4][4] = {{1, -1, -1, -1}, {1, 1, -1, 1}, {1, 1, 1, -1}, {1, -1, 1, 1}};
+__constant__ int8_t kWPlaneB[4][4] = {{0, 1, 2, 3}, {1, 0, 3, 2}, {2, 3, 0, 1}, {3, 2, 1, 0}};
+__constant__ int8_t kWSign[4][4] = {{1, -1, -1, -1}, {1, 1, 1, -1}, {1, -1, 1, 1}, {1, 1, -1, 1}};
+
+struct TcParams {
+  int mb, nb, row0, col0;
+  int tiles_m, tiles_n;
+  int s, l, NS, MT, LS;
+  int pure, nprod;
+  float eta;
+  float* Y[4];
+  int64_t ldy;
+  float* W[4];
+  int64_t ldw;
+  int32_t* status;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void red_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
+// SMEM matrix descriptor (tcgen05): start >> 4, LBO >> 4, SBO >> 4, version 1, 128B swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// Instruction descriptor, kind::f16 with BF16 inputs and FP32 accumulation.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int b_mn_major, int neg_a) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)neg_a << 13) |
+         ((uint32_t)b_mn_major << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+struct Shared {
+  uint64_t a_full, a_ready, a_free, tm_full, tm_empty, done;
+  uint64_t st_full[kStages], st_empty[kStages];
+  uint32_t tmem_base;
+  volatile int abort;
+};
+
+__device__ bool wait_bar(uint64_t* bar, uint32_t parity, Shared* sh, int32_t* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gtime();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 255) {
+      if (sh->abort) return false;
+      if (gtime() - t0 > kWaitNs) {
+        sh->abort = 1;
+        atomicOr(status, kDevTimeout);
+        return false;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- the kernel
+__global__ void __launch_bounds__(kThreads, 1)
+    fused_sketch_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+                        const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tA3,
+                        const __grid_constant__ CUtensorMap tOm, const __grid_constant__ CUtensorMap tPsi,
+                        const TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sRing = smem + kABytes;
+  Shared* sh = reinterpret_cast<Shared*>(smem + kABytes + kStages * kStageBytes);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const CUtensorMap* tA[4] = {&tA0, &tA1, &tA2, &tA3};
+  const int ntiles = p.tiles_m * p.tiles_n;
+  const int nplanes_a = p.pure ? 3 : 4;
+  const int p0 = p.pure ? 1 : 0;  // first A plane present
+
+  if (threadIdx.x == 0) {
+    mbar_init(&sh->a_full, 1);
+    mbar_init(&sh->a_ready, 4);
+    mbar_init(&sh->a_free, 1);
+    mbar_init(&sh->tm_full, 1);
+    mbar_init(&sh->tm_empty, 4);
+    mbar_init(&sh->done, 1);
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&sh->st_full[i], 1);
+      mbar_init(&sh->st_empty[i], 1);
+    }
+    sh->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(&sh->tmem_base, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sh->tmem_base;
+  const int wstages = 2 * 4 * p.MT;  // (k-half, Psi plane, M-slice)
+  const int ystages = 4;             // Omega plane
+  const uint32_t hl_tx = (p.nprod == 3) ? 2u : 1u;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int slot = 0;
+      uint32_t slot_uses[kStages] = {0, 0, 0};
+      int t_local = 0;
+      bool a_outstanding = false;
+      uint32_t a_fills = 0;
+      for (int t = blockIdx.x; t < ntiles && !sh->abort; t += gridDim.x, ++t_local) {
+        const int ti = t / p.tiles_n, tj = t % p.tiles_n;
+        if (t_local > 0 && !wait_bar(&sh->a_free, (t_local - 1) & 1, sh, p.status)) break;
+        mbar_expect_tx(&sh->a_full, nplanes_a * 32768u);
+        for (int q = p0; q < 4; ++q) tma_load_2d(sA + q * 32768, tA[q], tj * kBN, ti * kBM, &sh->a_full);
+        a_outstanding = true;
+        ++a_fills;
+        const int nst = wstages + ystages;
+        for (int st = 0; st < nst && !sh->abort; ++st) {
+          if (slot_uses[slot] > 0 &&
+              !wait_bar(&sh->st_empty[slot], (slot_uses[slot] - 1) & 1, sh, p.status))
+            break;
+          uint8_t* dst = sRing + slot * kStageBytes;
+          if (st < wstages) {
+            const int kh = st / (4 * p.MT), rem = st % (4 * p.MT), pl = rem / p.MT, mt = rem % p.MT;
+            mbar_expect_tx(&sh->st_full[slot], hl_tx * 16384u);
+            for (int hl = 0; hl < (int)hl_tx; ++hl)
+              tma_load_2d(dst + hl * 16384, &tPsi, p.row0 + ti * kBM + kh * 64,
+                          (pl * 2 + hl) * p.LS + mt * 128, &sh->st_full[slot]);
+          } else {
+            const int pl = st - wstages;
+            mbar_expect_tx(&sh->st_full[slot], hl_tx * (uint32_t)(p.NS * 128));
+            for (int hl = 0; hl < (int)hl_tx; ++hl)
+              tma_load_2d(dst + hl * 16384, &tOm, p.col0 + tj * kBN, (pl * 2 + hl) * p.NS,
+                          &sh->st_full[slot]);
+          }
+          ++slot_uses[slot];
+          slot = (slot + 1) % kStages;
+        }
+      }
+      // wait (bounded) for our own copies before leaving
+      if (a_outstanding) wait_bar(&sh->a_full, (a_fills - 1) & 1, sh, p.status);
+      for (int s = 0; s < kStages; ++s)
+        if (slot_uses[s] > 0) wait_bar(&sh->st_full[s], (slot_uses[s] - 1) & 1, sh, p.status);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int slot = 0;
+      uint32_t slot_uses[kStages] = {0, 0, 0};
+      uint32_t tm_uses = 0;
+      int t_local = 0;
+      const uint32_t a_base = smem_u32(sA), r_base = smem_u32(sRing);
+      for (int t = blockIdx.x; t < ntiles && !sh->abort; t += gridDim.x, ++t_local) {
+        if (!wait_bar(&sh->a_ready, t_local & 1, sh, p.status)) break;
+        tc_fence_after();
+        // ---------------- W phase: W_q[mt] += sign Psi_a A_b  (M=128 Psi rows, N=64 A cols)
+        if (tm_uses > 0 && !wait_bar(&sh->tm_empty, (tm_uses - 1) & 1, sh, p.status)) break;
+        tc_fence_after();
+        uint32_t wstarted = 0;  // bit (q*MT+mt)
+        bool ok = true;
+        for (int st = 0; st < wstages && ok; ++st) {
+          const int kh = st / (4 * p.MT), rem = st % (4 * p.MT), pa = rem / p.MT, mt = rem % p.MT;
+          if (!wait_bar(&sh->st_full[slot], slot_uses[slot] & 1, sh, p.status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t stage = r_base + slot * kStageBytes;
+          for (int q = 0; q < 4; ++q) {
+            const int b = kWPlaneB[q][pa];
+            if (p.pure && b == 0) continue;
+            const int neg = kWSign[q][pa] < 0;
+            const uint32_t idesc = idesc_bf16(128, 64, 1, neg);
+            const uint32_t d = tmem + (uint32_t)((q * p.MT + mt) * 64);
+            const uint32_t bit = 1u << (q * p.MT + mt);
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint32_t arow = (uint32_t)(kh * 64 + ks * 16);
+              for (int pr = 0; pr < p.nprod; ++pr) {
+                const int ha = (pr == 2) ? 1 : 0;  // Psi lo
+                const int hb = (pr == 1) ? 1 : 0;  // A lo
+                const uint64_t ad = sdesc(stage + ha * 16384 + ks * 32, 16, 1024);
+                const uint64_t bd = sdesc(a_base + b * 32768 + hb * 1024 + (arow / 8) * 2048, 32768, 2048);
+                umma(d, ad, bd, idesc, (wstarted & bit) ? 1u : 0u);
+                wstarted |= bit;
+              }
+            }
+          }
+          umma_commit(&sh->st_empty[slot]);
+          ++slot_uses[slot];
+          slot = (slot + 1) % kStages;
+        }
+        if (!ok) break;
+        umma_commit(&sh->tm_full);
+        ++tm_uses;
+        // ---------------- Y phase: Y_q += sign A_a Omega_b  (M=128 A rows, N=NS)
+        if (!wait_bar(&sh->tm_empty, (tm_uses - 1) & 1, sh, p.status)) break;
+        tc_fence_after();
+        uint32_t ystarted = 0;
+        for (int st = 0; st < ystages && ok; ++st) {
+          const int pb = st;  // Omega plane
+          if (!wait_bar(&sh->st_full[slot], slot_uses[slot] & 1, sh, p.status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t stage = r_base + slot * kStageBytes;
+          for (int q = 0; q < 4; ++q) {
+            const int a = kYPlaneA[q][pb];
+            if (p.pure && a == 0) continue;
+            const int neg = kYSign[q][pb] < 0;
+            const uint32_t idesc = idesc_bf16(128, p.NS, 0, neg);
+            const uint32_t d = tmem + (uint32_t)(q * p.NS);
+            for (int ks = 0; ks < 4; ++ks) {
+              for (int pr = 0; pr < p.nprod; ++pr) {
+                const int ha = (pr == 1) ? 1 : 0;  // A lo
+                const int hb = (pr == 2) ? 1 : 0;  // Omega lo
+                const uint64_t ad = sdesc(a_base + a * 32768 + ha * 1024 + ks * 32, 16, 2048);
+                const uint64_t bd = sdesc(stage + hb * 16384 + ks * 32, 16, 1024);
+                umma(d, ad, bd, idesc, (ystarted >> q) & 1u);
+                ystarted |= 1u << q;
+              }
+            }
+          }
+          umma_commit(&sh->st_empty[slot]);
+          ++slot_uses[slot];
+          slot = (slot + 1) % kStages;
+        }
+        if (!ok) break;
+        umma_commit(&sh->a_free);
+        umma_commit(&sh->tm_full);
+        ++tm_uses;
+      }
+      // drain: every MMA issued so far completes before TMEM is released
+      umma_commit(&sh->done);
+      wait_bar(&sh->done, 0, sh, p.status);
+    }
+  } else if (warp >= 2 && warp <= 5) {
+    // ------------------------------------------------------------ converters
+    const int cw = warp - 2;
+    int t_local = 0;
+    for (int t = blockIdx.x; t < ntiles && !sh->abort; t += gridDim.x, ++t_local) {
+      if (!wait_bar(&sh->a_full, t_local & 1, sh, p.status)) break;
+      // 4 planes x 16 groups of 8 rows; each warp takes 16 groups
+      for (int gi = cw; gi < 64; gi += 4) {
+        const int plane = gi >> 4, grp = gi & 15;
+        if (p.pure && plane == 0) continue;
+        uint8_t* g = sA + plane * 32768 + grp * 2048;
+        const int r = lane >> 2, c0 = (lane & 3) * 16;
+        const float4* src = reinterpret_cast<const float4*>(g + r * 256 + c0 * 4);
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float4 f = src[k];
+          v[4 * k] = f.x; v[4 * k + 1] = f.y; v[4 * k + 2] = f.z; v[4 * k + 3] = f.w;
+        }
+        __syncwarp();
+        uint32_t hi[8], lo[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * k]), h1 = __float2bfloat16_rn(v[2 * k + 1]);
+          const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * k] - __bfloat162float(h0));
+          const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * k + 1] - __bfloat162float(h1));
+          hi[k] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+          lo[k] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        // 16 columns = two 16-byte chunks: logical chunks c0/8 and c0/8+1 of row r
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int chunk = (c0 >> 3) + h;
+          const int phys = (chunk ^ r) & 7;
+          uint4* dh = reinterpret_cast<uint4*>(g + r * 128 + phys * 16);
+          uint4* dl = reinterpret_cast<uint4*>(g + 1024 + r * 128 + phys * 16);
+          *dh = make_uint4(hi[4 * h], hi[4 * h + 1], hi[4 * h + 2], hi[4 * h + 3]);
+          *dl = make_uint4(lo[4 * h], lo[4 * h + 1], lo[4 * h + 2], lo[4 * h + 3]);
+        }
+        __syncwarp();
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh->a_ready);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int lq = warp & 3;  // TMEM lane quarter this warp may access
+    uint32_t tm_uses = 0;
+    int t_local = 0;
+    const bool wvec = ((p.col0 & 3) == 0) && ((p.ldw & 3) == 0);
+    for (int t = blockIdx.x; t < ntiles && !sh->abort; t += gridDim.x, ++t_local) {
+      const int ti = t / p.tiles_n, tj = t % p.tiles_n;
+      // ---- W phase: lanes = Psi rows of slice mt, 64 columns of A
+      if (!wait_bar(&sh->tm_full, tm_uses & 1, sh, p.status)) break;
+      tc_fence_after();
+      ++tm_uses;
+      for (int q = 0; q < 4; ++q) {
+        for (int mt = 0; mt < p.MT; ++mt) {
+          const int prow = mt * 128 + lq * 32 + lane;
+          const int cbase = tj * kBN;
+          float* wrow = p.W[q] + (int64_t)prow * p.ldw + p.col0 + cbase;
+          for (int c16 = 0; c16 < 64; c16 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)((q * p.MT + mt) * 64 + c16), v);
+            if (prow < p.l) {
+              for (int k = 0; k < 16; k += 4) {
+                const int col = cbase + c16 + k;
+                if (wvec && col + 3 < p.nb) {
+                  red_v4(wrow + c16 + k, p.eta * v[k], p.eta * v[k + 1], p.eta * v[k + 2], p.eta * v[k + 3]);
+                } else {
+                  for (int u = 0; u < 4; ++u)
+                    if (col + u < p.nb) atomicAdd(wrow + c16 + k + u, p.eta * v[k + u]);
+                }
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh->tm_empty);
+      // ---- Y phase: lanes = A rows, NS columns per output plane
+      if (!wait_bar(&sh->tm_full, tm_uses & 1, sh, p.status)) break;
+      tc_fence_after();
+      ++tm_uses;
+      const int arow = ti * kBM + lq * 32 + lane;
+      for (int q = 0; q < 4; ++q) {
+        float* yrow = p.Y[q] + (int64_t)(p.row0 + arow) * p.ldy;
+        for (int c16 = 0; c16 < p.NS; c16 += 16) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(q * p.NS + c16), v);
+          if (arow < p.mb) {
+            for (int k = 0; k < 16; k += 4) {
+              const int col = c16 + k;
+              if (col + 3 < p.s) {
+                red_v4(yrow + col, p.eta * v[k], p.eta * v[k + 1], p.eta * v[k + 2], p.eta * v[k + 3]);
+              } else {
+                for (int u = 0; u < 4; ++u)
+                  if (col + u < p.s) atomicAdd(yrow + col + u, p.eta * v[k + u]);
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh->tm_empty);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ---------------------------------------------------------------- packing of Omega / Psi
+// Omega (n x s, FP32 planes) -> OmT[plane][hl][NS rows][ldo] BF16 (row j = column j of
+// Omega, padded rows zero).  Psi (l x m) -> PsP[plane][hl][LS rows][ldp] BF16.
+__global__ void pack_kernel(const float* __restrict__ src, int64_t rows, int64_t cols,
+                            int transpose, __nv_bfloat16* __restrict__ dst, int64_t drows,
+                            int64_t dld, int64_t dcols) {
+  const int64_t per_plane = drows * dcols;
+  const int64_t total = 4 * per_plane;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pl = e / per_plane, rc = e % per_plane;
+    const int64_t r = rc / dcols, c = rc % dcols;
+    float v = 0.f;
+    if (transpose) {  // dst row r = src column r
+      if (r < cols && c < rows) v = src[pl * rows * cols + c * cols + r];
+    } else {
+      if (r < rows && c < cols) v = src[pl * rows * cols + r * cols + c];
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(h));
+    dst[(pl * 2 + 0) * drows * dld + r * dld + c] = h;
+    dst[(pl * 2 + 1) * drows * dld + r * dld + c] = lo;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+struct PackGeom {
+  int64_t NS, LS, ldo, ldp;
+  size_t om_bytes, ps_bytes;
+};
+PackGeom geom(const qs_config& c) {
+  PackGeom g;
+  g.NS = (c.s + 15) / 16 * 16;
+  g.LS = (c.l + 127) / 128 * 128;
+  g.ldo = (c.n + 7) / 8 * 8;
+  g.ldp = (c.m + 7) / 8 * 8;
+  g.om_bytes = (size_t)4 * 2 * g.NS * g.ldo * 2;
+  g.ps_bytes = (size_t)4 * 2 * g.LS * g.ldp * 2;
+  return g;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, CUtensorMapDataType dt, int esize, const void* base, uint64_t cols,
+              uint64_t rows, uint64_t ld, uint32_t box_c, uint32_t box_r, CUtensorMapSwizzle sw) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {ld * (uint64_t)esize};
+  cuuint32_t box[2] = {box_c, box_r};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, dt, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t smem_bytes() { return 1024 + kABytes + kStages * kStageBytes + sizeof(Shared); }
+
+}  // namespace
+
+size_t tc_pack_bytes(const qs_config& c) {
+  if (!tc_mode(c.prec)) return 0;
+  const PackGeom g = geom(c);
+  return ((g.om_bytes + 255) / 256 * 256) + g.ps_bytes;
+}
+
+cudaError_t tc_pack_embeddings(const qs_handle_s& h, cudaStream_t st) {
+  const qs_config& c = h.cfg;
+  const PackGeom g = geom(c);
+  __nv_bfloat16* om = reinterpret_cast<__nv_bfloat16*>(h.ws + h.off_pack);
+  __nv_bfloat16* ps = reinterpret_cast<__nv_bfloat16*>(h.ws + h.off_pack + (g.om_bytes + 255) / 256 * 256);
+  cudaError_t e = cudaMemsetAsync(om, 0, g.om_bytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ps, 0, g.ps_bytes, st);
+  if (e != cudaSuccess) return e;
+  const float* omega = reinterpret_cast<const float*>(h.ws + h.off_omega);
+  const float* psi = reinterpret_cast<const float*>(h.ws + h.off_psi);
+  auto blocks = [](int64_t tot) { return (int)std::min<int64_t>((tot + 255) / 256, 16 * kNumSMs); };
+  pack_kernel<<<blocks(4 * g.NS * c.n), 256, 0, st>>>(omega, c.n, c.s, 1, om, g.NS, g.ldo, c.n);
+  count_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  pack_kernel<<<blocks(4 * g.LS * c.m), 256, 0, st>>>(psi, c.l, c.m, 0, ps, g.LS, g.ldp, c.m);
+  count_launch();
+  return cudaGetLastError();
+}
+
+qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t lda, int64_t row0,
+                           int64_t col0, int64_t mb, int64_t nb, double eta, cudaStream_t st) {
+  const qs_config& c = h.cfg;
+  const PackGeom g = geom(c);
+  if (g.NS > 128 || g.LS > 256) return QS_ERR_UNSUPPORTED;   // TMEM plan of this kernel
+  if (lda % 4) return QS_ERR_INVALID;                         // TMA: 16-byte row pitch
+  for (int q = 0; q < 4; ++q)
+    if (A[q] && (reinterpret_cast<uintptr_t>(A[q]) & 15)) return QS_ERR_INVALID;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(fused_sketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes()) != cudaSuccess)
+      return QS_ERR_CUDA;
+    attr_set = true;
+  }
+  CUtensorMap tA[4], tOm, tPsi;
+  memset(tA, 0, sizeof(tA));
+  for (int q = 0; q < 4; ++q) {
+    const void* base = A[q] ? A[q] : A[c.pure ? 1 : q];   // plane w of a pure A is never loaded
+    if (!make_map(&tA[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, nb, mb, lda, kBN, kBM,
+                  CU_TENSOR_MAP_SWIZZLE_NONE))
+      return QS_ERR_CUDA;
+  }
+  const __nv_bfloat16* om = reinterpret_cast<const __nv_bfloat16*>(h.ws + h.off_pack);
+  const __nv_bfloat16* ps =
+      reinterpret_cast<const __nv_bfloat16*>(h.ws + h.off_pack + (g.om_bytes + 255) / 256 * 256);
+  if (!make_map(&tOm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, om, c.n, 4 * 2 * g.NS, g.ldo, 64,
+                (uint32_t)g.NS, CU_TENSOR_MAP_SWIZZLE_128B))
+    return QS_ERR_CUDA;
+  if (!make_map(&tPsi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ps, c.m, 4 * 2 * g.LS, g.ldp, 64, 128,
+                CU_TENSOR_MAP_SWIZZLE_128B))
+    return QS_ERR_CUDA;
+  TcParams prm{};
+  prm.mb = (int)mb; prm.nb = (int)nb; prm.row0 = (int)row0; prm.col0 = (int)col0;
+  prm.tiles_m = (int)((mb + kBM - 1) / kBM);
+  prm.tiles_n = (int)((nb + kBN - 1) / kBN);
+  prm.s = (int)c.s; prm.l = (int)c.l; prm.NS = (int)g.NS; prm.LS = (int)g.LS;
+  prm.MT = (int)(g.LS / 128);
+  prm.pure = c.pure;
+  prm.nprod = c.prec == QS_PREC_BF16X3 ? 3 : 1;
+  prm.eta = (float)eta;
+  const int64_t sy = (c.s + 3) / 4 * 4;
+  for (int q = 0; q < 4; ++q) {
+    prm.Y[q] = reinterpret_cast<float*>(h.ws + h.off_y) + q * c.m * sy;
+    prm.W[q] = reinterpret_cast<float*>(h.ws + h.off_w) + q * c.l * c.n;
+  }
+  prm.ldy = sy;
+  prm.ldw = c.n;
+  prm.status = reinterpret_cast<int32_t*>(h.ws + h.off_status);
+  const int ntiles = prm.tiles_m * prm.tiles_n;
+  const int grid = std::min(ntiles, kNumSMs);
+  fused_sketch_kernel<<<grid, kThreads, smem_bytes(), st>>>(tA[0], tA[1], tA[2], tA[3], tOm, tPsi, prm);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}
+
 }  // namespace qs

@@ -212,5 +212,6 @@ class QSketch:
         if code == QS_OBJ_SCALARS:
             return self.workspace[off:off + 16 * 8].view(torch.float64)
         rows, cols = shapes[code]
-        assert ld.value == cols and ps.value == rows * cols
-        return self.workspace[off:off + 4 * rows * cols * esize].view(dtype).view(4, rows, cols)
+        nel = 3 * ps.value + (rows - 1) * ld.value + cols
+        flat = self.workspace[off:off + nel * esize].view(dtype)
+        return flat.as_strided((4, rows, cols), (ps.value, ld.value, 1))
