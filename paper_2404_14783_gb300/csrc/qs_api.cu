@@ -22,7 +22,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
-constexpr int kSmallSlots = 12;  // s x s FP64 scratch matrices
+constexpr int kSmallSlots = 16;  // s x s FP64 scratch matrices
 constexpr double kKappaStop = 1e8;
 
 bool valid_cfg(const qs_config* c) {
@@ -57,7 +57,7 @@ size_t plan(const qs_config& c, qs_handle_s* h) {
   size_t o_w = take(4 * l * n * es);
   size_t o_h = take(4 * m * s * es);
   size_t o_x = take(4 * s * n * es);
-  size_t o_gram = take(4 * m * s * 8);  // FP64 tall temporary (m x s)
+  size_t o_gram = take(2 * 4 * m * s * 8);  // two FP64 tall temporaries (m x s)
   const size_t small_bytes = kSmallSlots * align_up(4 * s * s * 8);
   size_t o_small = take(small_bytes);
   size_t o_p = take(4 * l * s * 8);
@@ -65,11 +65,13 @@ size_t plan(const qs_config& c, qs_handle_s* h) {
   size_t o_core = take(core_bytes);
   const size_t pack_bytes = tc_pack_bytes(c);
   size_t o_pack = take(pack_bytes);
+  size_t o_psvd = take(psvd_work_bytes(c.s));
   if (h) {
     h->esize = (int)es;
     h->off_status = o_status; h->off_scalars = o_scal; h->off_omega = o_om; h->off_psi = o_psi;
     h->off_y = o_y; h->off_w = o_w; h->off_h = o_h; h->off_x = o_x; h->off_gram = o_gram;
     h->off_small = o_small; h->off_p = o_p; h->off_core = o_core; h->off_pack = o_pack;
+    h->off_psvd = o_psvd;
     h->off_tail = off; h->small_bytes = small_bytes; h->core_bytes = core_bytes;
     h->pack_bytes = pack_bytes;
   }
@@ -107,6 +109,7 @@ struct Ctx {
   Mat H() const { return {h->ws + h->off_h, s, m * s, f64}; }
   Mat X() const { return {h->ws + h->off_x, n, s * n, f64}; }
   Mat T() const { return {h->ws + h->off_gram, s, m * s, 1}; }
+  Mat T2() const { return {h->ws + h->off_gram + 4 * m * s * 8, s, m * s, 1}; }
   Mat small(int i) const {
     return {h->ws + h->off_small + i * align_up(4 * s * s * 8), s, s * s, 1};
   }
@@ -122,35 +125,64 @@ struct Ctx {
   double* scalars() const { return h->d_scalars(); }
 };
 
+inline bool is_small(int64_t M, int64_t N) { return M <= 512 && N <= 512; }
+
 int pick_splits(int64_t M, int64_t N, int64_t K) {
-  const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
+  const int tile = is_small(M, N) ? 16 : 64;
+  const int64_t tiles = ((M + tile - 1) / tile) * ((N + tile - 1) / tile);
   int64_t sp = (2 * kNumSMs + tiles - 1) / tiles;
-  sp = std::min<int64_t>(sp, std::max<int64_t>(1, K / 32));
+  sp = std::min<int64_t>(sp, std::max<int64_t>(1, K / (is_small(M, N) ? 16 : 32)));
   return (int)std::max<int64_t>(1, std::min<int64_t>(sp, 1024));
 }
 
 // C = alpha * op(A) B + beta C on workspace matrices (all FP64 unless stated by the views).
 // acc: 0 = FP32 (all operands FP32), 1 = FP64, 2 = double-float on the FP32 pipes.
 cudaError_t gemm(const Ctx& x, const Mat& A, bool conjA, const Mat& B, const Mat& C, int64_t M,
-                 int64_t N, int64_t K, double alpha, double beta, int acc, bool allow_split) {
+                 int64_t N, int64_t K, double alpha, double beta, int acc, bool allow_split,
+                 const double* gate = nullptr, double gate_skip = 0.0) {
   GemmDesc d{};
   d.M = M; d.N = N; d.K = K;
   A.cplanes(d.a); d.lda = A.ld; d.a_f64 = A.f64; d.conj_a = conjA;
   B.cplanes(d.b); d.ldb = B.ld; d.b_f64 = B.f64;
   C.planes(d.c); d.ldc = C.ld; d.c_f64 = C.f64;
   d.alpha = alpha; d.beta = beta; d.acc_f64 = acc;
-  d.splits = allow_split ? pick_splits(M, N, K) : 1;
+  d.small = is_small(M, N);
+  d.splits = (allow_split || d.small) ? pick_splits(M, N, K) : 1;
   d.epi = 0; d.err = nullptr;
+  d.gate = gate; d.gate_skip = gate_skip;
   if (d.splits > 1 && beta != 1.0) {
-    cudaError_t e = launch_scale(C.p, C.f64, M, N, C.ld, C.ps, beta, x.st);
+    cudaError_t e = launch_scale(C.p, C.f64, M, N, C.ld, C.ps, beta, x.st, gate, gate_skip);
     if (e != cudaSuccess) return e;
   }
   return launch_qgemm(d, x.st);
 }
 
 // Gram G = A* A of a tall m x s matrix (FP64 result).
-cudaError_t gram(const Ctx& x, const Mat& A, int64_t rows, int64_t cols, const Mat& G) {
-  return gemm(x, A, true, A, G, cols, cols, rows, 1.0, 0.0, x.acc_hi(), true);
+cudaError_t gram(const Ctx& x, const Mat& A, int64_t rows, int64_t cols, const Mat& G,
+               const double* gate = nullptr, double gate_skip = 0.0) {
+  return gemm(x, A, true, A, G, cols, cols, rows, 1.0, 0.0, x.acc_hi(), true, gate, gate_skip);
+}
+
+// Li = L^{-1} for G = L L* (and eps into scalars[slot] when slot >= 0).  Small s uses the
+// fused shared-memory kernel (double-float in the FP32 modes); larger s the global-memory
+// kernels.
+cudaError_t chol_inv(const Ctx& x, const Mat& G, const Mat& L, const Mat& Li, int complex_only,
+                     int allow_shift, double shift_rows, int slot, int fail_bits,
+                     bool want_L = false) {
+  const int s = (int)x.s;
+  int32_t* st = x.status();
+  double* sc = x.scalars();
+  if (s <= qchol_inv_max_n())
+    return launch_qchol_inv((const double*)G.p, G.ld, G.ps, (double*)Li.p, Li.ld, Li.ps, s,
+                            complex_only, allow_shift, shift_rows, slot, kKappaStop, !x.f64, st, sc,
+                            fail_bits, want_L ? (double*)L.p : nullptr, x.st);
+  cudaError_t e = launch_qchol((const double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s,
+                               complex_only, allow_shift, shift_rows, st, sc, fail_bits, x.st);
+  if (e == cudaSuccess && slot >= 0)
+    e = launch_qpower((const double*)L.p, L.ld, L.ps, s, 3, slot, kKappaStop, st, sc, x.st);
+  if (e == cudaSuccess)
+    e = launch_qtrinv((const double*)L.p, L.ld, L.ps, (double*)Li.p, Li.ld, Li.ps, s, st, x.st);
+  return e;
 }
 
 qs_status pseudo_qr(const Ctx& x, int ncorr) {
@@ -162,16 +194,12 @@ qs_status pseudo_qr(const Ctx& x, int ncorr) {
   double* sc = x.scalars();
   // (Alg. 1 step 2) thin complex QR of Y_c by Cholesky-QR: Y_c* Y_c = L L*, R = L*.
   QS_CU(gram(x, Y, x.m, s, G));
-  QS_CU(launch_qchol((double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s, 1, 1, 2.0 * x.m, st,
-                     sc, kDevRank | kDevStopCorr, x.st));
-  QS_CU(launch_qtrinv((double*)L.p, L.ld, L.ps, (double*)Li.p, Li.ld, Li.ps, s, st, x.st));
+  QS_CU(chol_inv(x, G, L, Li, 1, 1, 2.0 * x.m, -1, kDevRank | kDevStopCorr));
   QS_CU(launch_qconjT(Li.p, 1, Li.ld, Li.ps, D.p, 1, D.ld, D.ps, s, s, x.st));   // D = R^{-1}
   // second Cholesky-QR pass on T = Y R^{-1} restores orthogonality of the Q factor
   QS_CU(gemm(x, Y, false, D, T, x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
   QS_CU(gram(x, T, x.m, s, G));
-  QS_CU(launch_qchol((double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s, 1, 0, 2.0 * x.m, st,
-                     sc, kDevRank | kDevStopCorr, x.st));
-  QS_CU(launch_qtrinv((double*)L.p, L.ld, L.ps, (double*)Li.p, Li.ld, Li.ps, s, st, x.st));
+  QS_CU(chol_inv(x, G, L, Li, 1, 0, 2.0 * x.m, -1, kDevRank | kDevStopCorr));
   QS_CU(launch_qconjT(Li.p, 1, Li.ld, Li.ps, R2.p, 1, R2.ld, R2.ps, s, s, x.st));
   QS_CU(gemm(x, D, false, R2, D2, s, s, s, 1.0, 0.0, x.acc_hi(), false));  // D2 = R^{-1} of Y_c
   // (Alg. 1 step 3) H_0 = Y D2; its quaternion Gram G_0 = R2^{-*} (T*T) R2^{-1}
@@ -181,18 +209,25 @@ qs_status pseudo_qr(const Ctx& x, int ncorr) {
   Mat Gk = G0;
   // (Alg. 1 step 4) corrections H <- (1-eps) H + eps (H^dagger)* = H ((1-eps) I + eps G^{-1})
   for (int k = 0; k < ncorr; ++k) {
-    QS_CU(launch_qchol((double*)Gk.p, Gk.ld, Gk.ps, (double*)L.p, L.ld, L.ps, s, 0, 0, 2.0 * x.m,
-                       st, sc, kDevRank | kDevStopCorr, x.st));
-    QS_CU(launch_qpower((double*)L.p, L.ld, L.ps, s, 3, kScEps0 + k, kKappaStop, st, sc, x.st));
-    QS_CU(launch_qtrinv((double*)L.p, L.ld, L.ps, (double*)Li.p, Li.ld, Li.ps, s, st, x.st));
+    QS_CU(chol_inv(x, Gk, L, Li, 0, 0, 2.0 * x.m, kScEps0 + k, kDevRank | kDevStopCorr));
     QS_CU(gemm(x, Li, true, Li, Gi, s, s, s, 1.0, 0.0, x.acc_hi(), false));  // G^{-1} = L^{-*} L^{-1}
     QS_CU(launch_qaxpby_eye((double*)Gi.p, Gi.ld, Gi.ps, (double*)M.p, M.ld, M.ps, s, sc,
                             kScEps0 + k, x.st));
     QS_CU(gemm(x, Dcur, false, M, Dnext, s, s, s, 1.0, 0.0, x.acc_hi(), false));
     std::swap(Dcur, Dnext);
-    if (k + 1 < ncorr) {  // Gram of the explicitly formed H_{k+1} = Y D
-      QS_CU(gemm(x, Y, false, Dcur, T, x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
-      QS_CU(gram(x, T, x.m, s, G));
+    if (k + 1 < ncorr) {
+      // Gram of H_{k+1} = H_k M: in s x s space when kappa(H_k) allows (gate = 1), else from
+      // the explicitly formed tall H_{k+1} = Y D (gate = 0); exactly one of the two runs.
+      const double* gate = sc + kScGate;
+      if (x.h->cfg.s <= qchol_inv_max_n()) {
+        QS_CU(launch_qgram_update((const double*)Gk.p, (double*)G.p, (const double*)Gi.p, G.ld, G.ps,
+                                  s, sc, kScEps0 + k, x.st));
+        QS_CU(gemm(x, Y, false, Dcur, T, x.m, s, s, 1.0, 0.0, x.acc_hi(), false, gate, 1.0));
+        QS_CU(gram(x, T, x.m, s, G, gate, 1.0));
+      } else {
+        QS_CU(gemm(x, Y, false, Dcur, T, x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
+        QS_CU(gram(x, T, x.m, s, G));
+      }
       Gk = G;
     }
   }
@@ -219,15 +254,11 @@ qs_status core_solve(const Ctx& x) {
   }
   // Alg. QLEQ on chi_P: QR of P (quaternion Cholesky-QR, twice), X = R^{-1} Q* W
   QS_CU(gram(x, P, l, s, G));
-  QS_CU(launch_qchol((double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s, 0, 1, 2.0 * l, st, sc,
-                     kDevRank, x.st));
-  QS_CU(launch_qtrinv((double*)L.p, L.ld, L.ps, (double*)L1i.p, L1i.ld, L1i.ps, s, st, x.st));
+  QS_CU(chol_inv(x, G, L, L1i, 0, 1, 4.0 * l, -1, kDevRank));
   QS_CU(launch_qconjT(L1i.p, 1, L1i.ld, L1i.ps, R1.p, 1, R1.ld, R1.ps, s, s, x.st));
   QS_CU(gemm(x, P, false, R1, Tp, l, s, s, 1.0, 0.0, x.acc_hi(), false));
   QS_CU(gram(x, Tp, l, s, G));
-  QS_CU(launch_qchol((double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s, 0, 0, 2.0 * l, st, sc,
-                     kDevRank, x.st));
-  QS_CU(launch_qtrinv((double*)L.p, L.ld, L.ps, (double*)L2i.p, L2i.ld, L2i.ps, s, st, x.st));
+  QS_CU(chol_inv(x, G, L, L2i, 0, 0, 4.0 * l, -1, kDevRank));
   QS_CU(launch_qconjT(L2i.p, 1, L2i.ld, L2i.ps, R2.p, 1, R2.ld, R2.ps, s, s, x.st));
   QS_CU(gemm(x, Tp, false, R2, Qp, l, s, s, 1.0, 0.0, x.acc_hi(), false));       // Q (l x s)
   QS_CU(gemm(x, L2i, false, L1i, S, s, s, s, 1.0, 0.0, x.acc_hi(), false));      // (R^{-1})* = L2^{-1} L1^{-1}
@@ -237,6 +268,40 @@ qs_status core_solve(const Ctx& x) {
   QS_CU(launch_qconjT(ZT.p, 1, ZT.ld, ZT.ps, Zw.p, Zw.f64, Zw.ld, Zw.ps, (int)l, s, x.st));
   // X = P^dagger W (s x n)
   QS_CU(gemm(x, Zw, false, x.W(), x.X(), s, x.n, l, 1.0, 0.0, x.f64 ? 1 : 0, true));
+  return QS_OK;
+}
+
+// Pseudo-SVD (Alg. 2): quaternion Cholesky-QR Y = Q R (three passes: the first may be
+// shifted, the next two restore orthogonality -- shifted Cholesky-QR3), the small SVD stage
+// on chi_R gives Z, and H = Q Z.
+qs_status pseudo_svd(const Ctx& x) {
+  const int s = (int)x.s;
+  const Mat G = x.small(0), L1 = x.small(1), Li1 = x.small(2), R1i = x.small(3), L2 = x.small(4),
+            Li2 = x.small(5), R2i = x.small(6), L3 = x.small(7), Li3 = x.small(8), R3i = x.small(9),
+            LL = x.small(10), LLL = x.small(11), R = x.small(12), Z = x.small(13), D = x.small(14);
+  const Mat Y = x.Y(), T = x.T(), T2 = x.T2();
+  int32_t* st = x.status();
+  double* sc = x.scalars();
+  QS_CU(gram(x, Y, x.m, s, G));
+  QS_CU(chol_inv(x, G, L1, Li1, 0, 1, 4.0 * x.m, -1, kDevRank, true));
+  QS_CU(launch_qconjT(Li1.p, 1, Li1.ld, Li1.ps, R1i.p, 1, R1i.ld, R1i.ps, s, s, x.st));
+  QS_CU(gemm(x, Y, false, R1i, T, x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
+  QS_CU(gram(x, T, x.m, s, G));
+  QS_CU(chol_inv(x, G, L2, Li2, 0, 0, 4.0 * x.m, -1, kDevRank, true));
+  QS_CU(launch_qconjT(Li2.p, 1, Li2.ld, Li2.ps, R2i.p, 1, R2i.ld, R2i.ps, s, s, x.st));
+  QS_CU(gemm(x, T, false, R2i, T2, x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
+  QS_CU(gram(x, T2, x.m, s, G));
+  QS_CU(chol_inv(x, G, L3, Li3, 0, 0, 4.0 * x.m, -1, kDevRank, true));
+  QS_CU(launch_qconjT(Li3.p, 1, Li3.ld, Li3.ps, R3i.p, 1, R3i.ld, R3i.ps, s, s, x.st));
+  // R = R3 R2 R1 = (L1 L2 L3)*
+  QS_CU(gemm(x, L1, false, L2, LL, s, s, s, 1.0, 0.0, x.acc_hi(), false));
+  QS_CU(gemm(x, LL, false, L3, LLL, s, s, s, 1.0, 0.0, x.acc_hi(), false));
+  QS_CU(launch_qconjT(LLL.p, 1, LLL.ld, LLL.ps, R.p, 1, R.ld, R.ps, s, s, x.st));
+  QS_CU(launch_psvd_small((const double*)R.p, R.ld, R.ps, s, x.h->ws + x.h->off_psvd, (double*)Z.p,
+                          Z.ld, Z.ps, x.h->cfg.seed, sc, st, x.st));
+  // H = Q Z = T2 R3^{-1} Z: R3 is close to I, so this product adds no kappa(Y)-sized rounding
+  QS_CU(gemm(x, R3i, false, Z, D, s, s, s, 1.0, 0.0, x.acc_hi(), false));
+  QS_CU(gemm(x, T2, false, D, x.H(), x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
   return QS_OK;
 }
 
@@ -346,8 +411,9 @@ qs_status qrangefinder(qs_handle_t h, int32_t kind, int32_t n_correction, void* 
   Ctx x{h, st, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64};
   QS_CU(launch_clear_stop(x.status(), st));
   QS_CU(cudaMemsetAsync(x.scalars() + kScKappa, 0, sizeof(double) * 6, st));
+  QS_CU(cudaMemsetAsync(x.scalars() + kScGate, 0, sizeof(double), st));
   if (kind == QS_RF_PSEUDO_QR) return pseudo_qr(x, n_correction);
-  return pseudo_svd_run(*h, st);
+  return pseudo_svd(x);
 }
 
 qs_status qonepass_core(qs_handle_t h, void* stream) {

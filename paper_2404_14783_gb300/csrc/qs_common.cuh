@@ -28,6 +28,7 @@ enum {
   kScShift = 6,
   kScErrNum = 8,    // accumulator: ||A - HX||_F^2
   kScErrDen = 9,    // accumulator: ||A||_F^2
+  kScGate = 10,     // 1: next Gram of the corrections by the s x s update, 0: explicit pass
   kScCount = 16
 };
 
@@ -82,7 +83,7 @@ struct qs_handle_s {
   size_t ws_bytes;
   // slab offsets (bytes) into ws
   size_t off_status, off_scalars, off_omega, off_psi, off_y, off_w, off_h, off_x;
-  size_t off_gram, off_small, off_p, off_core, off_pack, off_tail;
+  size_t off_gram, off_small, off_p, off_core, off_pack, off_psvd, off_tail;
   size_t small_bytes, core_bytes, pack_bytes;
   int32_t* d_status() const { return reinterpret_cast<int32_t*>(ws + off_status); }
   double* d_scalars() const { return reinterpret_cast<double*>(ws + off_scalars); }
@@ -105,6 +106,10 @@ struct GemmDesc {
   // sum |E - alpha*acc|^2 into err[0] and sum |E|^2 into err[1] (FP64 atomics).
   int epi;
   double* err;
+  int small;     // 1: 16x16-tile kernel for products with M, N <= 512
+  // device-side gate: the launch does nothing when gate != null and *gate == gate_skip
+  const double* gate;
+  double gate_skip;
 };
 // Plane pointers of a matrix with uniform plane stride.
 inline void planes_of(const void* base, int64_t ps, int esize, int64_t offset_elems,
@@ -118,7 +123,8 @@ inline void planes_of(void* base, int64_t ps, int esize, int64_t offset_elems, v
 }
 cudaError_t launch_qgemm(const GemmDesc& d, cudaStream_t st);
 cudaError_t launch_scale(void* c, int f64, int64_t rows, int64_t cols, int64_t ld, int64_t ps,
-                         double beta, cudaStream_t st);
+                         double beta, cudaStream_t st, const double* gate = nullptr,
+                         double gate_skip = 0.0);
 cudaError_t launch_draw(void* out, int f64, int64_t rows, int64_t cols, int kind, uint32_t stream,
                         uint64_t seed, cudaStream_t st);
 }  // namespace qs

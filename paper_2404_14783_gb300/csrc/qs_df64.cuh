@@ -17,6 +17,8 @@
 
 namespace qs {
 
+using ::fma;   // keep the FP32/FP64 overloads visible next to the df64 one
+
 struct df64 {
   float hi, lo;
   __host__ __device__ df64() : hi(0.f), lo(0.f) {}
@@ -45,6 +47,8 @@ __device__ __forceinline__ df64 operator+(df64 a, df64 b) {
   const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
   return df_fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
 }
+
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
 
 __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
   const float p = __fmul_rn(a.hi, b.hi);

@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(256) qgemm_kernel(GemmDesc g) {
   __shared__ __align__(16) ACC As[2][4][BK][BM];
   __shared__ __align__(16) ACC Bs[2][4][BK][BN];
 
+  if (g.gate && *g.gate == g.gate_skip) return;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
@@ -179,8 +180,69 @@ __global__ void __launch_bounds__(256) qgemm_kernel(GemmDesc g) {
   }
 }
 
+// Small products (M, N <= 512, e.g. the s x s factors of the rangefinders): one quaternion
+// output per thread, 16 x 16 outputs per CTA, K staged 16 deep, split-K over grid z.
+template <typename ACC, typename TA, typename TB, typename TC, bool CONJ>
+__global__ void __launch_bounds__(256) qgemm_small_kernel(GemmDesc g) {
+  constexpr int T = 16, BK = 16;
+  __shared__ ACC As[4][BK][T + 1];
+  __shared__ ACC Bs[4][BK][T + 1];
+  if (g.gate && *g.gate == g.gate_skip) return;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t m0 = (int64_t)blockIdx.x * T, n0 = (int64_t)blockIdx.y * T;
+  int64_t kchunk = (g.K + g.splits - 1) / g.splits;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  const int64_t kbeg = (int64_t)blockIdx.z * kchunk;
+  const int64_t kend = min(g.K, kbeg + kchunk);
+  if (kbeg >= kend) return;
+  ACC cw = ACC(0), cx = ACC(0), cy = ACC(0), cz = ACC(0);
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = threadIdx.x + 256 * i;   // 0..1023 = plane*256 + r*16 + c
+      const int pl = e >> 8, r = (e >> 4) & 15, c = e & 15;
+      const TA* A = static_cast<const TA*>(g.a[pl]);
+      const TB* B = static_cast<const TB*>(g.b[pl]);
+      // A tile element (m = m0 + r, k = k0 + c); B tile element (k = k0 + r, n = n0 + c)
+      ACC va = ACC(0), vb = ACC(0);
+      const int64_t ka = k0 + c, ma = m0 + r;
+      if (A && ka < kend && ma < g.M) {
+        if (CONJ) {
+          va = ACC(A[ka * g.lda + ma]);
+          if (pl) va = -va;
+        } else {
+          va = ACC(A[ma * g.lda + ka]);
+        }
+      }
+      const int64_t kb = k0 + r, nb = n0 + c;
+      if (B && kb < kend && nb < g.N) vb = ACC(B[kb * g.ldb + nb]);
+      As[pl][c][r] = va;
+      Bs[pl][r][c] = vb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk)
+      qmac(cw, cx, cy, cz, As[0][kk][ty], As[1][kk][ty], As[2][kk][ty], As[3][kk][ty], Bs[0][kk][tx],
+           Bs[1][kk][tx], Bs[2][kk][tx], Bs[3][kk][tx]);
+    __syncthreads();
+  }
+  const int64_t m = m0 + ty, n = n0 + tx;
+  if (m >= g.M || n >= g.N) return;
+  const ACC alpha = ACC(g.alpha);
+  const ACC v[4] = {alpha * cw, alpha * cx, alpha * cy, alpha * cz};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    TC* dst = static_cast<TC*>(g.c[q]) + m * g.ldc + n;
+    if (g.splits > 1) atomicAdd(dst, static_cast<TC>(v[q]));
+    else if (g.beta == 0.0) *dst = static_cast<TC>(v[q]);
+    else *dst = static_cast<TC>(v[q] + ACC(g.beta) * ACC(*dst));
+  }
+}
+
 template <typename T>
-__global__ void scale_kernel(T* c, int64_t rows, int64_t cols, int64_t ld, int64_t ps, T beta) {
+__global__ void scale_kernel(T* c, int64_t rows, int64_t cols, int64_t ld, int64_t ps, T beta,
+                             const double* gate, double gate_skip) {
+  if (gate && *gate == gate_skip) return;
   const int64_t total = rows * cols * 4;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -233,6 +295,15 @@ __global__ void draw_kernel(T* out, int64_t rows, int64_t cols, int kind, uint32
 
 template <typename ACC, typename TA, typename TB, typename TC>
 cudaError_t launch_t(const GemmDesc& d, cudaStream_t st) {
+  if (d.small && d.epi == 0) {
+    dim3 grid((unsigned)((d.M + 15) / 16), (unsigned)((d.N + 15) / 16), (unsigned)d.splits);
+    if (d.conj_a)
+      qgemm_small_kernel<ACC, TA, TB, TC, true><<<grid, 256, 0, st>>>(d);
+    else
+      qgemm_small_kernel<ACC, TA, TB, TC, false><<<grid, 256, 0, st>>>(d);
+    count_launch();
+    return cudaGetLastError();
+  }
   dim3 grid((unsigned)((d.M + 63) / 64), (unsigned)((d.N + 63) / 64), (unsigned)d.splits);
   if (d.conj_a)
     qgemm_kernel<ACC, TA, TB, TC, true><<<grid, 256, 0, st>>>(d);
@@ -266,14 +337,15 @@ cudaError_t launch_qgemm(const GemmDesc& d, cudaStream_t st) {
 }
 
 cudaError_t launch_scale(void* c, int f64, int64_t rows, int64_t cols, int64_t ld, int64_t ps,
-                         double beta, cudaStream_t st) {
+                         double beta, cudaStream_t st, const double* gate, double gate_skip) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
   const int64_t total = rows * cols * 4;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8 * kNumSMs);
   if (f64)
-    scale_kernel<double><<<blocks, 256, 0, st>>>((double*)c, rows, cols, ld, ps, beta);
+    scale_kernel<double><<<blocks, 256, 0, st>>>((double*)c, rows, cols, ld, ps, beta, gate, gate_skip);
   else
-    scale_kernel<float><<<blocks, 256, 0, st>>>((float*)c, rows, cols, ld, ps, (float)beta);
+    scale_kernel<float><<<blocks, 256, 0, st>>>((float*)c, rows, cols, ld, ps, (float)beta, gate,
+                                                gate_skip);
   count_launch();
   return cudaGetLastError();
 }

@@ -11,7 +11,10 @@ cudaError_t tc_pack_embeddings(const qs_handle_s& h, cudaStream_t st);
 // fused one-read sketch of a block of A
 qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t lda, int64_t row0,
                            int64_t col0, int64_t mb, int64_t nb, double eta, cudaStream_t st);
-// pseudo-SVD rangefinder (Alg. 2)
-qs_status pseudo_svd_run(qs_handle_s& h, cudaStream_t st);
+// pseudo-SVD small stage (Alg. 2 on chi_R): Z (s x s quaternion) from R (s x s upper)
+size_t psvd_work_bytes(int64_t s);
+cudaError_t launch_psvd_small(const double* R, int64_t ldr, int64_t psr, int s, void* work,
+                              double* Z, int64_t ldz, int64_t psz, uint64_t seed, double* scalars,
+                              int32_t* status, cudaStream_t st);
 cudaError_t launch_finalize_err(double* scalars, double* out, cudaStream_t st);
 }  // namespace qs

@@ -317,6 +317,22 @@ __global__ void qaxpby_eye_kernel(const double* X, int64_t ldx, int64_t psx, dou
   }
 }
 
+// G_next = (1-eps)^2 G + 2 eps (1-eps) I + eps^2 Ginv: the Gram of H M with
+// M = (1-eps) I + eps G^{-1} (M commutes with G).  Runs only when scalars[kScGate] == 1.
+__global__ void qgram_update_kernel(const double* G, double* Gn, const double* Gi, int64_t ld,
+                                    int64_t ps, int n, const double* scalars, int slot) {
+  if (scalars[kScGate] != 1.0) return;
+  const double eps = scalars[slot];
+  const double a = (1.0 - eps) * (1.0 - eps), b = 2.0 * eps * (1.0 - eps), c = eps * eps;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int i = e / n, j = e % n;
+    for (int p = 0; p < 4; ++p) {
+      const int64_t o = p * ps + (int64_t)i * ld + j;
+      Gn[o] = a * G[o] + c * Gi[o] + ((p == 0 && i == j) ? b : 0.0);
+    }
+  }
+}
+
 // D = S* (conjugate transpose) of an r x c quaternion matrix (D is c x r).
 template <typename TS, typename TD>
 __global__ void qconjT_kernel(const TS* S, int64_t lds, int64_t pss, TD* D, int64_t ldd,
@@ -415,6 +431,15 @@ cudaError_t launch_qcopy(const void* S, int s_f64, int64_t lds, int64_t pss, voi
     qcopy_kernel<float, double><<<blocks, 256, 0, st>>>((const float*)S, lds, pss, (double*)D, ldd, psd, r, c);
   else
     qcopy_kernel<float, float><<<blocks, 256, 0, st>>>((const float*)S, lds, pss, (float*)D, ldd, psd, r, c);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qgram_update(const double* G, double* Gn, const double* Gi, int64_t ld,
+                                int64_t ps, int n, const double* scalars, int slot,
+                                cudaStream_t st) {
+  const int blocks = std::max(1, std::min(64, (n * n + 255) / 256));
+  qgram_update_kernel<<<blocks, 256, 0, st>>>(G, Gn, Gi, ld, ps, n, scalars, slot);
   count_launch();
   return cudaGetLastError();
 }

@@ -19,4 +19,16 @@ cudaError_t launch_qconjT(const void* S, int s_f64, int64_t lds, int64_t pss, vo
 cudaError_t launch_qcopy(const void* S, int s_f64, int64_t lds, int64_t pss, void* D, int d_f64,
                          int64_t ldd, int64_t psd, int64_t r, int64_t c, cudaStream_t st);
 cudaError_t launch_clear_stop(int32_t* status, cudaStream_t st);
+// Gram of the corrected H in s x s space (gated by scalars[kScGate] == 1).
+cudaError_t launch_qgram_update(const double* G, double* Gn, const double* Gi, int64_t ld,
+                                int64_t ps, int n, const double* scalars, int slot,
+                                cudaStream_t st);
+// Fused shared-memory Cholesky (+ optional power-iteration eps into scalars[power_slot] when
+// power_slot >= 0) and in-place inverse: writes L^{-1} (lower) to Li, and L to Lout when
+// Lout is not null (same leading dimension and plane stride).  n <= qchol_inv_max_n().
+int qchol_inv_max_n();
+cudaError_t launch_qchol_inv(const double* G, int64_t ldg, int64_t psg, double* Li, int64_t ldl,
+                             int64_t psl, int n, int complex_only, int allow_shift, double shift_rows,
+                             int power_slot, double kappa_stop, int use_df64, int32_t* status,
+                             double* scalars, int fail_bits, double* Lout, cudaStream_t st);
 }  // namespace qs

@@ -4,7 +4,8 @@ Tolerances (derived from the arithmetic):
   * FP64 steps: 1e-12 relative Frobenius for the sketches (u * sqrt(K) ~ 1e-15 at these K);
     HX and the projector of H carry the intrinsic sensitivity of the range of Y to rounding,
     measured on c1 with the oracle itself (1-ulp input perturbations move the 3-correction
-    HX by up to 3.6e-11), so HX is compared at 1e-9 and the final error at 1e-6 relative.
+    HX by up to 3.6e-11), so HX is compared at 1e-9; the final error (3e-6 of ||A|| on c1)
+    then agrees to 1e-9/3e-6 = 3e-4 relative.
   * FP32 SIMT sketch: 1e-5 relative Frobenius.
   * final relative error: within 1% of the oracle's.
 """
@@ -154,7 +155,9 @@ def test_c1_fp64_pipeline(pkg):
     X = qs.get("X").cpu().numpy()
     HX_ref = O.qmatmul(ref["H"], ref["X"])
     assert rel(O.qmatmul(H, X), HX_ref) < 1e-9
-    assert abs(err - ref["err"]) <= 1e-6 * ref["err"]
+    # the error is 3e-6 of ||A||; HX agrees to 1e-9 of ||A||, so err may move by up to
+    # 1e-9/3e-6 = 3e-4 relative (a perturbation aligned with the residual)
+    assert abs(err - ref["err"]) <= 3e-4 * ref["err"]
     # the rangefinder's own properties: range of Y and kappa(H) < 10 after 3 corrections
     sv = np.linalg.svd(O.chi(H), compute_uv=False)
     assert sv[0] / sv[-1] < 10
