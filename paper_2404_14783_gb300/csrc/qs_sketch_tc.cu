@@ -20,8 +20,9 @@
 //   warps 2-5   converters: FP32 -> BF16 hi/lo in place (an 8-row group of 2 KB becomes a
 //               1 KB hi atom and a 1 KB lo atom, so the operand's 8-row stride is 2048 B).
 //   warps 6-9   epilogue: TMEM -> registers -> red.global.add.v4.f32 into Y and W (L2).
-// TMEM (512 columns) is used by two phases per tile: the W phase (accumulators W_q for
-// 128-row slices of Psi: N = 64 columns each) and then the Y phase (Y_q: N = NS columns).
+// TMEM (512 columns) is split into two halves used by alternating "waves": one W wave per
+// 128-row slice of Psi (W_q for q = 0..3, N = 64 columns each) and two Y waves (a pair of
+// output planes each, N = NS columns), so draining one wave overlaps the next wave's MMAs.
 // Every wait is bounded (2 s of %globaltimer); on expiry the CTA records QS_ERR_TIMEOUT in
 // the workspace status word, stops issuing work, waits (bounded) for its own copies and
 // MMAs, frees TMEM and returns.
@@ -168,7 +169,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int b_mn_major, 
 }
 
 struct Shared {
-  uint64_t a_full, a_ready, a_free, tm_full, tm_empty, done;
+  uint64_t a_full, a_ready, a_free, done;
+  uint64_t h_full[2], h_empty[2];  // TMEM halves (256 columns each)
   uint64_t st_full[kStages], st_empty[kStages];
   uint32_t tmem_base;
   volatile int abort;
@@ -211,8 +213,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(&sh->a_full, 1);
     mbar_init(&sh->a_ready, 4);
     mbar_init(&sh->a_free, 1);
-    mbar_init(&sh->tm_full, 1);
-    mbar_init(&sh->tm_empty, 4);
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(&sh->h_full[h], 1);
+      mbar_init(&sh->h_empty[h], 4);
+    }
     mbar_init(&sh->done, 1);
     for (int i = 0; i < kStages; ++i) {
       mbar_init(&sh->st_full[i], 1);
@@ -229,9 +233,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sh->tmem_base;
-  const int wstages = 2 * 4 * p.MT;  // (k-half, Psi plane, M-slice)
-  const int ystages = 4;             // Omega plane
+  // Work of one tile, in "waves".  A wave owns one TMEM half (256 columns) and the halves
+  // alternate, so the epilogue drains one wave while the MMAs of the next one run.
+  //   W waves (one per 128-row slice mt of Psi): W_q[mt] for q = 0..3, 64 columns each;
+  //       stages (k-half kh, Psi plane pa): 2 x 4.
+  //   Y waves (one per pair of output planes): Y_q for q = 2 qp, 2 qp + 1 (NS columns each);
+  //       stages (Omega plane pb): 4 (Omega is staged once per pair).
+  const int nwaves = p.MT + 2;
   const uint32_t hl_tx = (p.nprod == 3) ? 2u : 1u;
+  auto wave_stages = [&](int wv) { return wv < p.MT ? 8 : 4; };
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -241,34 +251,38 @@ __global__ void __launch_bounds__(kThreads, 1)
       int t_local = 0;
       bool a_outstanding = false;
       uint32_t a_fills = 0;
-      for (int t = blockIdx.x; t < ntiles && !sh->abort; t += gridDim.x, ++t_local) {
+      bool stop = false;
+      for (int t = blockIdx.x; t < ntiles && !stop && !sh->abort; t += gridDim.x, ++t_local) {
         const int ti = t / p.tiles_n, tj = t % p.tiles_n;
         if (t_local > 0 && !wait_bar(&sh->a_free, (t_local - 1) & 1, sh, p.status)) break;
         mbar_expect_tx(&sh->a_full, nplanes_a * 32768u);
         for (int q = p0; q < 4; ++q) tma_load_2d(sA + q * 32768, tA[q], tj * kBN, ti * kBM, &sh->a_full);
         a_outstanding = true;
         ++a_fills;
-        const int nst = wstages + ystages;
-        for (int st = 0; st < nst && !sh->abort; ++st) {
-          if (slot_uses[slot] > 0 &&
-              !wait_bar(&sh->st_empty[slot], (slot_uses[slot] - 1) & 1, sh, p.status))
-            break;
-          uint8_t* dst = sRing + slot * kStageBytes;
-          if (st < wstages) {
-            const int kh = st / (4 * p.MT), rem = st % (4 * p.MT), pl = rem / p.MT, mt = rem % p.MT;
-            mbar_expect_tx(&sh->st_full[slot], hl_tx * 16384u);
-            for (int hl = 0; hl < (int)hl_tx; ++hl)
-              tma_load_2d(dst + hl * 16384, &tPsi, p.row0 + ti * kBM + kh * 64,
-                          (pl * 2 + hl) * p.LS + mt * 128, &sh->st_full[slot]);
-          } else {
-            const int pl = st - wstages;
-            mbar_expect_tx(&sh->st_full[slot], hl_tx * (uint32_t)(p.NS * 128));
-            for (int hl = 0; hl < (int)hl_tx; ++hl)
-              tma_load_2d(dst + hl * 16384, &tOm, p.col0 + tj * kBN, (pl * 2 + hl) * p.NS,
-                          &sh->st_full[slot]);
+        for (int wv = 0; wv < nwaves && !stop; ++wv) {
+          for (int st = 0; st < wave_stages(wv); ++st) {
+            if (slot_uses[slot] > 0 &&
+                !wait_bar(&sh->st_empty[slot], (slot_uses[slot] - 1) & 1, sh, p.status)) {
+              stop = true;
+              break;
+            }
+            uint8_t* dst = sRing + slot * kStageBytes;
+            if (wv < p.MT) {
+              const int kh = st >> 2, pl = st & 3;
+              mbar_expect_tx(&sh->st_full[slot], hl_tx * 16384u);
+              for (int hl = 0; hl < (int)hl_tx; ++hl)
+                tma_load_2d(dst + hl * 16384, &tPsi, p.row0 + ti * kBM + kh * 64,
+                            (pl * 2 + hl) * p.LS + wv * 128, &sh->st_full[slot]);
+            } else {
+              const int pl = st;
+              mbar_expect_tx(&sh->st_full[slot], hl_tx * (uint32_t)(p.NS * 128));
+              for (int hl = 0; hl < (int)hl_tx; ++hl)
+                tma_load_2d(dst + hl * 16384, &tOm, p.col0 + tj * kBN, (pl * 2 + hl) * p.NS,
+                            &sh->st_full[slot]);
+            }
+            ++slot_uses[slot];
+            slot = (slot + 1) % kStages;
           }
-          ++slot_uses[slot];
-          slot = (slot + 1) % kStages;
         }
       }
       // wait (bounded) for our own copies before leaving
@@ -281,82 +295,81 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int slot = 0;
       uint32_t slot_uses[kStages] = {0, 0, 0};
-      uint32_t tm_uses = 0;
+      uint32_t g = 0;  // global wave counter: half = g & 1, use of that half = g >> 1
       int t_local = 0;
       const uint32_t a_base = smem_u32(sA), r_base = smem_u32(sRing);
-      for (int t = blockIdx.x; t < ntiles && !sh->abort; t += gridDim.x, ++t_local) {
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok && !sh->abort; t += gridDim.x, ++t_local) {
         if (!wait_bar(&sh->a_ready, t_local & 1, sh, p.status)) break;
         tc_fence_after();
-        // ---------------- W phase: W_q[mt] += sign Psi_a A_b  (M=128 Psi rows, N=64 A cols)
-        if (tm_uses > 0 && !wait_bar(&sh->tm_empty, (tm_uses - 1) & 1, sh, p.status)) break;
-        tc_fence_after();
-        uint32_t wstarted = 0;  // bit (q*MT+mt)
-        bool ok = true;
-        for (int st = 0; st < wstages && ok; ++st) {
-          const int kh = st / (4 * p.MT), rem = st % (4 * p.MT), pa = rem / p.MT, mt = rem % p.MT;
-          if (!wait_bar(&sh->st_full[slot], slot_uses[slot] & 1, sh, p.status)) { ok = false; break; }
+        for (int wv = 0; wv < nwaves && ok; ++wv, ++g) {
+          const uint32_t half = g & 1, use = g >> 1;
+          if (use > 0 && !wait_bar(&sh->h_empty[half], (use - 1) & 1, sh, p.status)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t stage = r_base + slot * kStageBytes;
-          for (int q = 0; q < 4; ++q) {
-            const int b = kWPlaneB[q][pa];
-            if (p.pure && b == 0) continue;
-            const int neg = kWSign[q][pa] < 0;
-            const uint32_t idesc = idesc_bf16(128, 64, 1, neg);
-            const uint32_t d = tmem + (uint32_t)((q * p.MT + mt) * 64);
-            const uint32_t bit = 1u << (q * p.MT + mt);
-            for (int ks = 0; ks < 4; ++ks) {
-              const uint32_t arow = (uint32_t)(kh * 64 + ks * 16);
-              for (int pr = 0; pr < p.nprod; ++pr) {
-                const int ha = (pr == 2) ? 1 : 0;  // Psi lo
-                const int hb = (pr == 1) ? 1 : 0;  // A lo
-                const uint64_t ad = sdesc(stage + ha * 16384 + ks * 32, 16, 1024);
-                const uint64_t bd = sdesc(a_base + b * 32768 + hb * 1024 + (arow / 8) * 2048, 32768, 2048);
-                umma(d, ad, bd, idesc, (wstarted & bit) ? 1u : 0u);
-                wstarted |= bit;
+          const uint32_t hbase = tmem + half * 256;
+          uint32_t started = 0;
+          for (int st = 0; st < wave_stages(wv); ++st) {
+            if (!wait_bar(&sh->st_full[slot], slot_uses[slot] & 1, sh, p.status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t stage = r_base + slot * kStageBytes;
+            if (wv < p.MT) {
+              // W_q[mt] += sign Psi_pa A_b  (M = 128 Psi rows, N = 64 A columns)
+              const int kh = st >> 2, pa = st & 3;
+              const uint64_t dpsi = sdesc(stage, 16, 1024);
+              for (int q = 0; q < 4; ++q) {
+                const int b = kWPlaneB[q][pa];
+                if (p.pure && b == 0) continue;
+                const uint32_t idesc = idesc_bf16(128, 64, 1, kWSign[q][pa] < 0);
+                const uint32_t d = hbase + (uint32_t)(q * 64);
+                const uint64_t da = sdesc(a_base + b * 32768 + (uint32_t)(kh * 8) * 2048, 32768, 2048);
+                uint32_t acc = (started >> q) & 1u;
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {
+                  const uint64_t ad = dpsi + (uint64_t)((ks * 32) >> 4);
+                  const uint64_t bd = da + (uint64_t)((ks * 2 * 2048) >> 4);
+                  umma(d, ad, bd, idesc, acc);                   // Psi_hi A_hi
+                  acc = 1u;
+                  if (p.nprod == 3) {
+                    umma(d, ad, bd + (1024 >> 4), idesc, 1u);    // Psi_hi A_lo
+                    umma(d, ad + (16384 >> 4), bd, idesc, 1u);   // Psi_lo A_hi
+                  }
+                }
+                started |= 1u << q;
+              }
+            } else {
+              // Y_q += sign A_a Omega_pb for q in the wave's pair  (M = 128 A rows, N = NS)
+              const int qp = wv - p.MT, pb = st;
+              const uint64_t dom = sdesc(stage, 16, 1024);
+              for (int j = 0; j < 2; ++j) {
+                const int q = 2 * qp + j;
+                const int a = kYPlaneA[q][pb];
+                if (p.pure && a == 0) continue;
+                const uint32_t idesc = idesc_bf16(128, p.NS, 0, kYSign[q][pb] < 0);
+                const uint32_t d = hbase + (uint32_t)(j * p.NS);
+                const uint64_t da = sdesc(a_base + a * 32768, 16, 2048);
+                uint32_t acc = (started >> j) & 1u;
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {
+                  const uint64_t ad = da + (uint64_t)((ks * 32) >> 4);
+                  const uint64_t bd = dom + (uint64_t)((ks * 32) >> 4);
+                  umma(d, ad, bd, idesc, acc);                   // A_hi Omega_hi
+                  acc = 1u;
+                  if (p.nprod == 3) {
+                    umma(d, ad + (1024 >> 4), bd, idesc, 1u);    // A_lo Omega_hi
+                    umma(d, ad, bd + (16384 >> 4), idesc, 1u);   // A_hi Omega_lo
+                  }
+                }
+                started |= 1u << j;
               }
             }
+            umma_commit(&sh->st_empty[slot]);
+            ++slot_uses[slot];
+            slot = (slot + 1) % kStages;
           }
-          umma_commit(&sh->st_empty[slot]);
-          ++slot_uses[slot];
-          slot = (slot + 1) % kStages;
+          if (!ok) break;
+          if (wv == nwaves - 1) umma_commit(&sh->a_free);
+          umma_commit(&sh->h_full[half]);
         }
-        if (!ok) break;
-        umma_commit(&sh->tm_full);
-        ++tm_uses;
-        // ---------------- Y phase: Y_q += sign A_a Omega_b  (M=128 A rows, N=NS)
-        if (!wait_bar(&sh->tm_empty, (tm_uses - 1) & 1, sh, p.status)) break;
-        tc_fence_after();
-        uint32_t ystarted = 0;
-        for (int st = 0; st < ystages && ok; ++st) {
-          const int pb = st;  // Omega plane
-          if (!wait_bar(&sh->st_full[slot], slot_uses[slot] & 1, sh, p.status)) { ok = false; break; }
-          tc_fence_after();
-          const uint32_t stage = r_base + slot * kStageBytes;
-          for (int q = 0; q < 4; ++q) {
-            const int a = kYPlaneA[q][pb];
-            if (p.pure && a == 0) continue;
-            const int neg = kYSign[q][pb] < 0;
-            const uint32_t idesc = idesc_bf16(128, p.NS, 0, neg);
-            const uint32_t d = tmem + (uint32_t)(q * p.NS);
-            for (int ks = 0; ks < 4; ++ks) {
-              for (int pr = 0; pr < p.nprod; ++pr) {
-                const int ha = (pr == 1) ? 1 : 0;  // A lo
-                const int hb = (pr == 2) ? 1 : 0;  // Omega lo
-                const uint64_t ad = sdesc(a_base + a * 32768 + ha * 1024 + ks * 32, 16, 2048);
-                const uint64_t bd = sdesc(stage + hb * 16384 + ks * 32, 16, 1024);
-                umma(d, ad, bd, idesc, (ystarted >> q) & 1u);
-                ystarted |= 1u << q;
-              }
-            }
-          }
-          umma_commit(&sh->st_empty[slot]);
-          ++slot_uses[slot];
-          slot = (slot + 1) % kStages;
-        }
-        if (!ok) break;
-        umma_commit(&sh->a_free);
-        umma_commit(&sh->tm_full);
-        ++tm_uses;
       }
       // drain: every MMA issued so far completes before TMEM is released
       umma_commit(&sh->done);
@@ -364,42 +377,37 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp >= 2 && warp <= 5) {
     // ------------------------------------------------------------ converters
+    // An 8-row group of one plane (2 KB of FP32) is read by one warp as 128 float4 chunks
+    // (lane l takes chunks l, l+32, l+64, l+96: half a warp per row, conflict free), then
+    // rewritten in place as a 1 KB hi atom and a 1 KB lo atom (128-byte swizzle).
     const int cw = warp - 2;
     int t_local = 0;
     for (int t = blockIdx.x; t < ntiles && !sh->abort; t += gridDim.x, ++t_local) {
       if (!wait_bar(&sh->a_full, t_local & 1, sh, p.status)) break;
-      // 4 planes x 16 groups of 8 rows; each warp takes 16 groups
       for (int gi = cw; gi < 64; gi += 4) {
         const int plane = gi >> 4, grp = gi & 15;
         if (p.pure && plane == 0) continue;
-        uint8_t* g = sA + plane * 32768 + grp * 2048;
-        const int r = lane >> 2, c0 = (lane & 3) * 16;
-        const float4* src = reinterpret_cast<const float4*>(g + r * 256 + c0 * 4);
-        float v[16];
+        uint8_t* gb = sA + plane * 32768 + grp * 2048;
+        float4 v[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float4 f = src[k];
-          v[4 * k] = f.x; v[4 * k + 1] = f.y; v[4 * k + 2] = f.z; v[4 * k + 3] = f.w;
-        }
+        for (int i = 0; i < 4; ++i) v[i] = reinterpret_cast<const float4*>(gb)[lane + 32 * i];
         __syncwarp();
-        uint32_t hi[8], lo[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * k]), h1 = __float2bfloat16_rn(v[2 * k + 1]);
-          const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * k] - __bfloat162float(h0));
-          const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * k + 1] - __bfloat162float(h1));
-          hi[k] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-          lo[k] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-        }
-        // 16 columns = two 16-byte chunks: logical chunks c0/8 and c0/8+1 of row r
+        for (int i = 0; i < 4; ++i) {
+          const int c = lane + 32 * i, r = c >> 4, f = c & 15;
+          const float x[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+          uint32_t hw[2], lw[2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int chunk = (c0 >> 3) + h;
-          const int phys = (chunk ^ r) & 7;
-          uint4* dh = reinterpret_cast<uint4*>(g + r * 128 + phys * 16);
-          uint4* dl = reinterpret_cast<uint4*>(g + 1024 + r * 128 + phys * 16);
-          *dh = make_uint4(hi[4 * h], hi[4 * h + 1], hi[4 * h + 2], hi[4 * h + 3]);
-          *dl = make_uint4(lo[4 * h], lo[4 * h + 1], lo[4 * h + 2], lo[4 * h + 3]);
+          for (int k = 0; k < 2; ++k) {
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * k]), h1 = __float2bfloat16_rn(x[2 * k + 1]);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * k] - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * k + 1] - __bfloat162float(h1));
+            hw[k] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            lw[k] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+          }
+          const int off = r * 128 + ((((f >> 1) ^ r) & 7) << 4) + (f & 1) * 8;
+          *reinterpret_cast<uint2*>(gb + off) = make_uint2(hw[0], hw[1]);
+          *reinterpret_cast<uint2*>(gb + 1024 + off) = make_uint2(lw[0], lw[1]);
         }
         __syncwarp();
       }
@@ -410,66 +418,66 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ------------------------------------------------------------ epilogue
     const int lq = warp & 3;  // TMEM lane quarter this warp may access
-    uint32_t tm_uses = 0;
-    int t_local = 0;
+    uint32_t g = 0;
     const bool wvec = ((p.col0 & 3) == 0) && ((p.ldw & 3) == 0);
-    for (int t = blockIdx.x; t < ntiles && !sh->abort; t += gridDim.x, ++t_local) {
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok && !sh->abort; t += gridDim.x) {
       const int ti = t / p.tiles_n, tj = t % p.tiles_n;
-      // ---- W phase: lanes = Psi rows of slice mt, 64 columns of A
-      if (!wait_bar(&sh->tm_full, tm_uses & 1, sh, p.status)) break;
-      tc_fence_after();
-      ++tm_uses;
-      for (int q = 0; q < 4; ++q) {
-        for (int mt = 0; mt < p.MT; ++mt) {
-          const int prow = mt * 128 + lq * 32 + lane;
+      for (int wv = 0; wv < nwaves; ++wv, ++g) {
+        const uint32_t half = g & 1, use = g >> 1;
+        if (!wait_bar(&sh->h_full[half], use & 1, sh, p.status)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t hcol = half * 256;
+        if (wv < p.MT) {
+          // lanes = Psi rows of slice wv, 64 columns of A per output plane
+          const int prow = wv * 128 + lq * 32 + lane;
           const int cbase = tj * kBN;
-          float* wrow = p.W[q] + (int64_t)prow * p.ldw + p.col0 + cbase;
-          for (int c16 = 0; c16 < 64; c16 += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)((q * p.MT + mt) * 64 + c16), v);
-            if (prow < p.l) {
-              for (int k = 0; k < 16; k += 4) {
-                const int col = cbase + c16 + k;
-                if (wvec && col + 3 < p.nb) {
-                  red_v4(wrow + c16 + k, p.eta * v[k], p.eta * v[k + 1], p.eta * v[k + 2], p.eta * v[k + 3]);
-                } else {
-                  for (int u = 0; u < 4; ++u)
-                    if (col + u < p.nb) atomicAdd(wrow + c16 + k + u, p.eta * v[k + u]);
+          for (int q = 0; q < 4; ++q) {
+            float* wrow = p.W[q] + (int64_t)prow * p.ldw + p.col0 + cbase;
+            for (int c16 = 0; c16 < 64; c16 += 16) {
+              float v[16];
+              tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + hcol + (uint32_t)(q * 64 + c16), v);
+              if (prow < p.l) {
+                for (int k = 0; k < 16; k += 4) {
+                  const int col = cbase + c16 + k;
+                  if (wvec && col + 3 < p.nb) {
+                    red_v4(wrow + c16 + k, p.eta * v[k], p.eta * v[k + 1], p.eta * v[k + 2], p.eta * v[k + 3]);
+                  } else {
+                    for (int u = 0; u < 4; ++u)
+                      if (col + u < p.nb) atomicAdd(wrow + c16 + k + u, p.eta * v[k + u]);
+                  }
+                }
+              }
+            }
+          }
+        } else {
+          // lanes = A rows, NS columns per output plane of the pair
+          const int qp = wv - p.MT;
+          const int arow = ti * kBM + lq * 32 + lane;
+          for (int j = 0; j < 2; ++j) {
+            const int q = 2 * qp + j;
+            float* yrow = p.Y[q] + (int64_t)(p.row0 + arow) * p.ldy;
+            for (int c16 = 0; c16 < p.NS; c16 += 16) {
+              float v[16];
+              tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + hcol + (uint32_t)(j * p.NS + c16), v);
+              if (arow < p.mb) {
+                for (int k = 0; k < 16; k += 4) {
+                  const int col = c16 + k;
+                  if (col + 3 < p.s) {
+                    red_v4(yrow + col, p.eta * v[k], p.eta * v[k + 1], p.eta * v[k + 2], p.eta * v[k + 3]);
+                  } else {
+                    for (int u = 0; u < 4; ++u)
+                      if (col + u < p.s) atomicAdd(yrow + col + u, p.eta * v[k + u]);
+                  }
                 }
               }
             }
           }
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh->h_empty[half]);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sh->tm_empty);
-      // ---- Y phase: lanes = A rows, NS columns per output plane
-      if (!wait_bar(&sh->tm_full, tm_uses & 1, sh, p.status)) break;
-      tc_fence_after();
-      ++tm_uses;
-      const int arow = ti * kBM + lq * 32 + lane;
-      for (int q = 0; q < 4; ++q) {
-        float* yrow = p.Y[q] + (int64_t)(p.row0 + arow) * p.ldy;
-        for (int c16 = 0; c16 < p.NS; c16 += 16) {
-          float v[16];
-          tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(q * p.NS + c16), v);
-          if (arow < p.mb) {
-            for (int k = 0; k < 16; k += 4) {
-              const int col = c16 + k;
-              if (col + 3 < p.s) {
-                red_v4(yrow + col, p.eta * v[k], p.eta * v[k + 1], p.eta * v[k + 2], p.eta * v[k + 3]);
-              } else {
-                for (int u = 0; u < 4; ++u)
-                  if (col + u < p.s) atomicAdd(yrow + col + u, p.eta * v[k + u]);
-              }
-            }
-          }
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sh->tm_empty);
     }
   }
   tc_fence_before();
