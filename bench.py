@@ -42,6 +42,18 @@ def load_peaks():
     return d
 
 
+def max_over_ranks(value, world):
+    """Largest value over all ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload(name):
     import workloads as WL
     w = dict(WL.WORKLOADS[name])
@@ -180,11 +192,7 @@ def run_ours(args, rank, world, local_rank):
     for ev in per_step_events:
         for i, k in enumerate(stage_ms):
             stage_ms[k] += ev[i].elapsed_time(ev[i + 1]) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world)
     final_err = float(err_out.item())
     status = qs.device_status()
 

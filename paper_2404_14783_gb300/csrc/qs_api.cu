@@ -139,7 +139,7 @@ int pick_splits(int64_t M, int64_t N, int64_t K) {
 // acc: 0 = FP32 (all operands FP32), 1 = FP64, 2 = double-float on the FP32 pipes.
 cudaError_t gemm(const Ctx& x, const Mat& A, bool conjA, const Mat& B, const Mat& C, int64_t M,
                  int64_t N, int64_t K, double alpha, double beta, int acc, bool allow_split,
-                 const double* gate = nullptr, double gate_skip = 0.0) {
+                 const double* gate = nullptr, double gate_skip = 0.0, int herm = 0) {
   GemmDesc d{};
   d.M = M; d.N = N; d.K = K;
   A.cplanes(d.a); d.lda = A.ld; d.a_f64 = A.f64; d.conj_a = conjA;
@@ -149,7 +149,7 @@ cudaError_t gemm(const Ctx& x, const Mat& A, bool conjA, const Mat& B, const Mat
   d.small = is_small(M, N);
   d.splits = (allow_split || d.small) ? pick_splits(M, N, K) : 1;
   d.epi = 0; d.err = nullptr;
-  d.gate = gate; d.gate_skip = gate_skip;
+  d.gate = gate; d.gate_skip = gate_skip; d.herm = herm;
   if (d.splits > 1 && beta != 1.0) {
     cudaError_t e = launch_scale(C.p, C.f64, M, N, C.ld, C.ps, beta, x.st, gate, gate_skip);
     if (e != cudaSuccess) return e;
@@ -157,10 +157,29 @@ cudaError_t gemm(const Ctx& x, const Mat& A, bool conjA, const Mat& B, const Mat
   return launch_qgemm(d, x.st);
 }
 
+// C = A B with a complex B (planes y, z of B are zero and not read).
+cudaError_t gemm_bcplx(const Ctx& x, const Mat& A, const Mat& B, const Mat& C, int64_t M, int64_t N,
+                       int64_t K, int acc) {
+  GemmDesc d{};
+  d.M = M; d.N = N; d.K = K;
+  A.cplanes(d.a); d.lda = A.ld; d.a_f64 = A.f64; d.conj_a = 0;
+  B.cplanes(d.b); d.b[2] = nullptr; d.b[3] = nullptr; d.ldb = B.ld; d.b_f64 = B.f64;
+  C.planes(d.c); d.ldc = C.ld; d.c_f64 = C.f64;
+  d.alpha = 1.0; d.beta = 0.0; d.acc_f64 = acc; d.splits = 1;
+  d.small = is_small(M, N);
+  return launch_qgemm(d, x.st);
+}
+
 // Gram G = A* A of a tall m x s matrix (FP64 result).
 cudaError_t gram(const Ctx& x, const Mat& A, int64_t rows, int64_t cols, const Mat& G,
                const double* gate = nullptr, double gate_skip = 0.0) {
-  return gemm(x, A, true, A, G, cols, cols, rows, 1.0, 0.0, x.acc_hi(), true, gate, gate_skip);
+  if (!is_small(cols, cols))
+    return gemm(x, A, true, A, G, cols, cols, rows, 1.0, 0.0, x.acc_hi(), true, gate, gate_skip);
+  // Hermitian: tiles on and above the diagonal, then the mirror
+  cudaError_t e = gemm(x, A, true, A, G, cols, cols, rows, 1.0, 0.0, x.acc_hi(), true, gate,
+                       gate_skip, /*herm=*/1);
+  if (e != cudaSuccess) return e;
+  return launch_qmirror((double*)G.p, G.ld, G.ps, (int)cols, x.st, gate, gate_skip);
 }
 
 // Li = L^{-1} for G = L L* (and eps into scalars[slot] when slot >= 0).  Small s uses the
@@ -196,8 +215,9 @@ qs_status pseudo_qr(const Ctx& x, int ncorr) {
   QS_CU(gram(x, Y, x.m, s, G));
   QS_CU(chol_inv(x, G, L, Li, 1, 1, 2.0 * x.m, -1, kDevRank | kDevStopCorr));
   QS_CU(launch_qconjT(Li.p, 1, Li.ld, Li.ps, D.p, 1, D.ld, D.ps, s, s, x.st));   // D = R^{-1}
-  // second Cholesky-QR pass on T = Y R^{-1} restores orthogonality of the Q factor
-  QS_CU(gemm(x, Y, false, D, T, x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
+  // second Cholesky-QR pass on T = Y R^{-1} restores orthogonality of the Q factor; R^{-1}
+  // is complex (the y, z planes of D are zero), which the product exploits
+  QS_CU(gemm_bcplx(x, Y, D, T, x.m, s, s, x.acc_hi()));
   QS_CU(gram(x, T, x.m, s, G));
   QS_CU(chol_inv(x, G, L, Li, 1, 0, 2.0 * x.m, -1, kDevRank | kDevStopCorr));
   QS_CU(launch_qconjT(Li.p, 1, Li.ld, Li.ps, R2.p, 1, R2.ld, R2.ps, s, s, x.st));
@@ -231,6 +251,8 @@ qs_status pseudo_qr(const Ctx& x, int ncorr) {
       Gk = G;
     }
   }
+  // H = Y D in the FP64 class: D carries the correction factors, whose norm times ||Y||
+  // is far above 1/u32, so an FP32 product would tilt the range of H away from that of Y
   QS_CU(gemm(x, Y, false, Dcur, x.H(), x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
   return QS_OK;
 }
@@ -243,10 +265,14 @@ qs_status core_solve(const Ctx& x) {
             R2 = x.small(5), S = x.small(6);
   int32_t* st = x.status();
   double* sc = x.scalars();
-  // (Alg. 3 step 2) P = Psi H.  FP32 modes: the inputs carry FP32-level error and
-  // kappa(P) is small, so the product runs in FP32 and is widened for the small solve.
+  // (Alg. 3 step 2) P = Psi H.  FP32 modes: after corrections (or pseudo-SVD) kappa(P) is
+  // small and an FP32 product, widened for the small solve, loses nothing; an uncorrected
+  // pseudo-QR H has kappa(Y), which would amplify the FP32 rounding of P into X, so that
+  // product accumulates in double-float.
   if (x.f64) {
     QS_CU(gemm(x, x.psi(), false, x.H(), P, l, s, x.m, 1.0, 0.0, 1, true));
+  } else if (!x.h->h_well_conditioned) {
+    QS_CU(gemm(x, x.psi(), false, x.H(), P, l, s, x.m, 1.0, 0.0, 2, true));
   } else {
     const Mat P32{x.core(0).p, s, l * s, 0};
     QS_CU(gemm(x, x.psi(), false, x.H(), P32, l, s, x.m, 1.0, 0.0, 0, true));
@@ -263,11 +289,15 @@ qs_status core_solve(const Ctx& x) {
   QS_CU(gemm(x, Tp, false, R2, Qp, l, s, s, 1.0, 0.0, x.acc_hi(), false));       // Q (l x s)
   QS_CU(gemm(x, L2i, false, L1i, S, s, s, s, 1.0, 0.0, x.acc_hi(), false));      // (R^{-1})* = L2^{-1} L1^{-1}
   QS_CU(gemm(x, Qp, false, S, ZT, l, s, s, 1.0, 0.0, x.acc_hi(), false));        // (P^dagger)* = Q R^{-*}
-  // P^dagger (s x l), in the working precision of W
-  const Mat Zw{Z.p, Z.ld, Z.ps, x.f64 ? 1 : 0};
+  // P^dagger (s x l), in the working precision of W; with an uncorrected H the norm of
+  // P^dagger is kappa(H) times that of P, so it stays FP64 and X accumulates in double-float
+  const bool wide = x.f64 || !x.h->h_well_conditioned;
+  const Mat Zw{Z.p, Z.ld, Z.ps, wide ? 1 : 0};
   QS_CU(launch_qconjT(ZT.p, 1, ZT.ld, ZT.ps, Zw.p, Zw.f64, Zw.ld, Zw.ps, (int)l, s, x.st));
   // X = P^dagger W (s x n)
-  QS_CU(gemm(x, Zw, false, x.W(), x.X(), s, x.n, l, 1.0, 0.0, x.f64 ? 1 : 0, true));
+  // (split-K partial sums would meet in an FP32 output, so the double-float case runs unsplit)
+  QS_CU(gemm(x, Zw, false, x.W(), x.X(), s, x.n, l, 1.0, 0.0, x.f64 ? 1 : (wide ? 2 : 0),
+             x.f64 || !wide));
   return QS_OK;
 }
 
@@ -412,6 +442,7 @@ qs_status qrangefinder(qs_handle_t h, int32_t kind, int32_t n_correction, void* 
   QS_CU(launch_clear_stop(x.status(), st));
   QS_CU(cudaMemsetAsync(x.scalars() + kScKappa, 0, sizeof(double) * 6, st));
   QS_CU(cudaMemsetAsync(x.scalars() + kScGate, 0, sizeof(double), st));
+  h->h_well_conditioned = kind == QS_RF_PSEUDO_SVD || n_correction > 0;
   if (kind == QS_RF_PSEUDO_QR) return pseudo_qr(x, n_correction);
   return pseudo_svd(x);
 }

@@ -85,6 +85,9 @@ struct qs_handle_s {
   size_t off_status, off_scalars, off_omega, off_psi, off_y, off_w, off_h, off_x;
   size_t off_gram, off_small, off_p, off_core, off_pack, off_psvd, off_tail;
   size_t small_bytes, core_bytes, pack_bytes;
+  // 0 after a pseudo-QR without corrections (H inherits kappa(Y)); the core solve then
+  // forms Psi H in the FP64 class in the FP32 modes
+  int h_well_conditioned;
   int32_t* d_status() const { return reinterpret_cast<int32_t*>(ws + off_status); }
   double* d_scalars() const { return reinterpret_cast<double*>(ws + off_scalars); }
 };
@@ -110,6 +113,8 @@ struct GemmDesc {
   // device-side gate: the launch does nothing when gate != null and *gate == gate_skip
   const double* gate;
   double gate_skip;
+  int herm;      // C = A* A is Hermitian: the small kernel computes only tiles on/above the
+                 // diagonal (the caller mirrors the rest)
 };
 // Plane pointers of a matrix with uniform plane stride.
 inline void planes_of(const void* base, int64_t ps, int esize, int64_t offset_elems,
@@ -125,6 +130,8 @@ cudaError_t launch_qgemm(const GemmDesc& d, cudaStream_t st);
 cudaError_t launch_scale(void* c, int f64, int64_t rows, int64_t cols, int64_t ld, int64_t ps,
                          double beta, cudaStream_t st, const double* gate = nullptr,
                          double gate_skip = 0.0);
+cudaError_t launch_qmirror(double* G, int64_t ld, int64_t ps, int n, cudaStream_t st,
+                           const double* gate = nullptr, double gate_skip = 0.0);
 cudaError_t launch_draw(void* out, int f64, int64_t rows, int64_t cols, int kind, uint32_t stream,
                         uint64_t seed, cudaStream_t st);
 }  // namespace qs

@@ -24,8 +24,9 @@ __device__ __forceinline__ T ld_elem(const void* base, int64_t idx) {
   return static_cast<const T*>(base)[idx];
 }
 
-template <typename ACC, typename TA, typename TB, typename TC, bool CONJ>
-__global__ void __launch_bounds__(256) qgemm_kernel(GemmDesc g) {
+// BCPLX: B has only its w and x planes (a complex matrix); the y and z products are skipped.
+template <typename ACC, typename TA, typename TB, typename TC, bool CONJ, bool BCPLX = false>
+__global__ void __launch_bounds__(256, sizeof(ACC) == 4 ? 2 : 1) qgemm_kernel(GemmDesc g) {
   constexpr int BM = 64, BN = 64;
   constexpr int BK = sizeof(ACC) == 8 ? 4 : 8;
   __shared__ __align__(16) ACC As[2][4][BK][BM];
@@ -107,9 +108,22 @@ __global__ void __launch_bounds__(256) qgemm_kernel(GemmDesc g) {
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          qmac(acc[0][i][j], acc[1][i][j], acc[2][i][j], acc[3][i][j], a[0][i], a[1][i], a[2][i],
-               a[3][i], b[0][j], b[1][j], b[2][j], b[3][j]);
+        for (int j = 0; j < 4; ++j) {
+          if (BCPLX) {  // b = b_w + b_x i: (a b)_w = a_w b_w - a_x b_x, (a b)_x = a_w b_x + a_x b_w,
+                        // (a b)_y = a_y b_w + a_z b_x, (a b)_z = a_z b_w - a_y b_x
+            acc[0][i][j] = fma(a[0][i], b[0][j], acc[0][i][j]);
+            acc[0][i][j] = fma(-a[1][i], b[1][j], acc[0][i][j]);
+            acc[1][i][j] = fma(a[0][i], b[1][j], acc[1][i][j]);
+            acc[1][i][j] = fma(a[1][i], b[0][j], acc[1][i][j]);
+            acc[2][i][j] = fma(a[2][i], b[0][j], acc[2][i][j]);
+            acc[2][i][j] = fma(a[3][i], b[1][j], acc[2][i][j]);
+            acc[3][i][j] = fma(a[3][i], b[0][j], acc[3][i][j]);
+            acc[3][i][j] = fma(-a[2][i], b[1][j], acc[3][i][j]);
+          } else {
+            qmac(acc[0][i][j], acc[1][i][j], acc[2][i][j], acc[3][i][j], a[0][i], a[1][i], a[2][i],
+                 a[3][i], b[0][j], b[1][j], b[2][j], b[3][j]);
+          }
+        }
     }
     if (has_next) {
       store_regs(buf ^ 1);
@@ -188,6 +202,7 @@ __global__ void __launch_bounds__(256) qgemm_small_kernel(GemmDesc g) {
   __shared__ ACC As[4][BK][T + 1];
   __shared__ ACC Bs[4][BK][T + 1];
   if (g.gate && *g.gate == g.gate_skip) return;
+  if (g.herm && blockIdx.y < blockIdx.x) return;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t m0 = (int64_t)blockIdx.x * T, n0 = (int64_t)blockIdx.y * T;
   int64_t kchunk = (g.K + g.splits - 1) / g.splits;
@@ -236,6 +251,21 @@ __global__ void __launch_bounds__(256) qgemm_small_kernel(GemmDesc g) {
     if (g.splits > 1) atomicAdd(dst, static_cast<TC>(v[q]));
     else if (g.beta == 0.0) *dst = static_cast<TC>(v[q]);
     else *dst = static_cast<TC>(v[q] + ACC(g.beta) * ACC(*dst));
+  }
+}
+
+// Lower triangle of a Hermitian quaternion matrix from its upper triangle: G_ji = conj(G_ij).
+__global__ void qmirror_kernel(double* G, int64_t ld, int64_t ps, int n, const double* gate,
+                               double gate_skip) {
+  if (gate && *gate == gate_skip) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int i = e / n, j = e % n;
+    if (j >= i) continue;  // (i, j) strictly lower: take from (j, i)
+    const int64_t dst = (int64_t)i * ld + j, src = (int64_t)j * ld + i;
+    G[dst] = G[src];
+    G[ps + dst] = -G[ps + src];
+    G[2 * ps + dst] = -G[2 * ps + src];
+    G[3 * ps + dst] = -G[3 * ps + src];
   }
 }
 
@@ -305,8 +335,11 @@ cudaError_t launch_t(const GemmDesc& d, cudaStream_t st) {
     return cudaGetLastError();
   }
   dim3 grid((unsigned)((d.M + 63) / 64), (unsigned)((d.N + 63) / 64), (unsigned)d.splits);
+  const bool bcplx = !d.b[2] && !d.b[3] && d.b[0] && d.b[1];
   if (d.conj_a)
     qgemm_kernel<ACC, TA, TB, TC, true><<<grid, 256, 0, st>>>(d);
+  else if (bcplx && sizeof(ACC) == 8)
+    qgemm_kernel<ACC, TA, TB, TC, false, true><<<grid, 256, 0, st>>>(d);
   else
     qgemm_kernel<ACC, TA, TB, TC, false><<<grid, 256, 0, st>>>(d);
   count_launch();
@@ -346,6 +379,14 @@ cudaError_t launch_scale(void* c, int f64, int64_t rows, int64_t cols, int64_t l
   else
     scale_kernel<float><<<blocks, 256, 0, st>>>((float*)c, rows, cols, ld, ps, (float)beta, gate,
                                                 gate_skip);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qmirror(double* G, int64_t ld, int64_t ps, int n, cudaStream_t st,
+                           const double* gate, double gate_skip) {
+  const int blocks = std::max(1, std::min(64, (n * n + 255) / 256));
+  qmirror_kernel<<<blocks, 256, 0, st>>>(G, ld, ps, n, gate, gate_skip);
   count_launch();
   return cudaGetLastError();
 }

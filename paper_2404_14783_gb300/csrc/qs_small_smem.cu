@@ -92,6 +92,21 @@ __device__ __forceinline__ QT<R> wsum4(QT<R> v) {
 
 __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
+// Quaternion array in shared memory stored component-wise (structure of arrays): lanes that
+// touch consecutive entries touch consecutive 8-byte words, free of bank conflicts.
+template <typename R>
+struct QA {
+  R* c0;
+  R* c1;
+  R* c2;
+  R* c3;
+  __device__ __forceinline__ QT<R> operator[](int i) const { return QT<R>{c0[i], c1[i], c2[i], c3[i]}; }
+  __device__ __forceinline__ void set(int i, const QT<R>& v) const {
+    c0[i] = v.w; c1[i] = v.x; c2[i] = v.y; c3[i] = v.z;
+  }
+  __device__ static QA make(R* base, int cap) { return QA{base, base + cap, base + 2 * cap, base + 3 * cap}; }
+};
+
 template <typename R>
 __global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_t ldg, int64_t psg,
                                                          double* Li, int64_t ldl, int64_t psl, int n,
@@ -101,9 +116,11 @@ __global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_
                                                          double* scalars, int fail_bits,
                                                          double* Lout) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  QT<R>* L = reinterpret_cast<QT<R>*>(smem_raw);      // packed lower triangle
-  QT<R>* row = L + n * (n + 1) / 2;                    // scratch row
-  QT<R>* vec = row + n;                                // 4 vectors of n for the power iterates
+  const int ntri = n * (n + 1) / 2;
+  R* sbase = reinterpret_cast<R*>(smem_raw);
+  const QA<R> L = QA<R>::make(sbase, ntri);                 // packed lower triangle
+  const QA<R> row = QA<R>::make(sbase + 4 * ntri, n);       // scratch row
+  const QA<R> vec = QA<R>::make(sbase + 4 * ntri + 4 * n, 4 * n);  // 4 vectors for the power iterates
   __shared__ int fail;
   __shared__ double shift, inv_d;
   __shared__ double red[32];
@@ -131,7 +148,7 @@ __global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_
       double w = gget(i, j, 0), x = gget(i, j, 1), y = gget(i, j, 2), z = gget(i, j, 3);
       if (complex_only) { y = 0.0; z = 0.0; }
       if (i == j) { x = y = z = 0.0; w += shift; }
-      L[e] = QT<R>{from_d<R>(w), from_d<R>(x), from_d<R>(y), from_d<R>(z)};
+      L.set(e, QT<R>{from_d<R>(w), from_d<R>(x), from_d<R>(y), from_d<R>(z)});
     }
     if (tid == 0) fail = 0;
     __syncthreads();
@@ -142,19 +159,19 @@ __global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_
           fail = 1;
         } else {
           const double r = sqrt(d);
-          L[tri(j, j)] = QT<R>{from_d<R>(r), R(0), R(0), R(0)};
+          L.set(tri(j, j), QT<R>{from_d<R>(r), R(0), R(0), R(0)});
           inv_d = 1.0 / r;
         }
       }
       __syncthreads();
       if (fail) break;
       const R inv = from_d<R>(inv_d);
-      for (int i = j + 1 + tid; i < n; i += nt) L[tri(i, j)] = qt_scale(L[tri(i, j)], inv);
+      for (int i = j + 1 + tid; i < n; i += nt) L.set(tri(i, j), qt_scale(L[tri(i, j)], inv));
       __syncthreads();
       for (int i = j + 1 + warp; i < n; i += nw) {
         const QT<R> lij = L[tri(i, j)];
         for (int k = j + 1 + lane; k <= i; k += 32)
-          L[tri(i, k)] = qt_sub_mul_conj(L[tri(i, k)], lij, L[tri(k, j)]);
+          L.set(tri(i, k), qt_sub_mul_conj(L[tri(i, k)], lij, L[tri(k, j)]));
       }
       __syncthreads();
     }
@@ -200,36 +217,39 @@ __global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_
   if (power_slot >= 0) {
     __shared__ double res[2];
     if (warp < 2) {
-      QT<R>* v = vec + warp * n;        // current vector
-      QT<R>* x = vec + (2 + warp) * n;  // copy / work
+      const int vo = warp * n, xo = (2 + warp) * n;  // current vector / work vector offsets
+      auto V = [&](int i) { return vec[vo + i]; };
+      auto X = [&](int i) { return vec[xo + i]; };
+      auto setV = [&](int i, const QT<R>& q) { vec.set(vo + i, q); };
+      auto setX = [&](int i, const QT<R>& q) { vec.set(xo + i, q); };
       const double c = 1.0 / sqrt(2.0 * n);
-      for (int i = lane; i < n; i += 32) x[i] = QT<R>{from_d<R>(c), R(0), from_d<R>(-c), R(0)};
+      for (int i = lane; i < n; i += 32) setX(i, QT<R>{from_d<R>(c), R(0), from_d<R>(-c), R(0)});
       __syncwarp();
       double est = 0.0;
       for (int it = 0; it < 3; ++it) {
         if (warp == 0) {
           // v = G^{-1} x: L y = x, then L* v = y
-          for (int i = lane; i < n; i += 32) v[i] = x[i];
+          for (int i = lane; i < n; i += 32) setV(i, X(i));
           __syncwarp();
           for (int i = 0; i < n; ++i) {
             QT<R> acc{R(0), R(0), R(0), R(0)};
-            for (int k = lane; k < i; k += 32) acc = qt_mac(acc, L[tri(i, k)], v[k]);
+            for (int k = lane; k < i; k += 32) acc = qt_mac(acc, L[tri(i, k)], V(k));
             acc = wsum4(acc);
             if (lane == 0) {
               const R inv = from_d<R>(1.0 / to_d(L[tri(i, i)].w));
-              const QT<R> b = v[i];
-              v[i] = qt_scale(QT<R>{b.w - acc.w, b.x - acc.x, b.y - acc.y, b.z - acc.z}, inv);
+              const QT<R> b = V(i);
+              setV(i, qt_scale(QT<R>{b.w - acc.w, b.x - acc.x, b.y - acc.y, b.z - acc.z}, inv));
             }
             __syncwarp();
           }
           for (int i = n - 1; i >= 0; --i) {
             QT<R> acc{R(0), R(0), R(0), R(0)};
-            for (int k = i + 1 + lane; k < n; k += 32) acc = qt_mac_conj_a(acc, L[tri(k, i)], v[k]);
+            for (int k = i + 1 + lane; k < n; k += 32) acc = qt_mac_conj_a(acc, L[tri(k, i)], V(k));
             acc = wsum4(acc);
             if (lane == 0) {
               const R inv = from_d<R>(1.0 / to_d(L[tri(i, i)].w));
-              const QT<R> b = v[i];
-              v[i] = qt_scale(QT<R>{b.w - acc.w, b.x - acc.x, b.y - acc.y, b.z - acc.z}, inv);
+              const QT<R> b = V(i);
+              setV(i, qt_scale(QT<R>{b.w - acc.w, b.x - acc.x, b.y - acc.y, b.z - acc.z}, inv));
             }
             __syncwarp();
           }
@@ -237,32 +257,32 @@ __global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_
           // t = L* x (kept in v), then w = L t (into x)
           for (int i = lane; i < n; i += 32) {
             QT<R> acc{R(0), R(0), R(0), R(0)};
-            for (int k = i; k < n; ++k) acc = qt_mac_conj_a(acc, L[tri(k, i)], x[k]);
-            v[i] = acc;
+            for (int k = i; k < n; ++k) acc = qt_mac_conj_a(acc, L[tri(k, i)], X(k));
+            setV(i, acc);
           }
           __syncwarp();
         }
         double dot = 0.0, nrm = 0.0;
         if (warp == 0) {
           for (int i = lane; i < n; i += 32) {
-            const QT<R> a = x[i], b = v[i];
+            const QT<R> a = X(i), b = V(i);
             dot += to_d(a.w) * to_d(b.w) + to_d(a.x) * to_d(b.x) + to_d(a.y) * to_d(b.y) + to_d(a.z) * to_d(b.z);
             nrm += to_d(b.w) * to_d(b.w) + to_d(b.x) * to_d(b.x) + to_d(b.y) * to_d(b.y) + to_d(b.z) * to_d(b.z);
           }
         } else {
           for (int i = lane; i < n; i += 32) {
-            const QT<R> t = v[i];
+            const QT<R> t = V(i);
             dot += to_d(t.w) * to_d(t.w) + to_d(t.x) * to_d(t.x) + to_d(t.y) * to_d(t.y) + to_d(t.z) * to_d(t.z);
           }
           for (int i = lane; i < n; i += 32) {
             QT<R> acc{R(0), R(0), R(0), R(0)};
-            for (int k = 0; k <= i; ++k) acc = qt_mac(acc, L[tri(i, k)], v[k]);
+            for (int k = 0; k <= i; ++k) acc = qt_mac(acc, L[tri(i, k)], V(k));
             nrm += to_d(acc.w) * to_d(acc.w) + to_d(acc.x) * to_d(acc.x) + to_d(acc.y) * to_d(acc.y) +
                    to_d(acc.z) * to_d(acc.z);
-            row[i] = acc;  // row[] is free until the inverse; warp 1 owns it here
+            row.set(i, acc);  // row[] is free until the inverse; warp 1 owns it here
           }
           __syncwarp();
-          for (int i = lane; i < n; i += 32) v[i] = row[i];
+          for (int i = lane; i < n; i += 32) setV(i, row[i]);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -272,7 +292,7 @@ __global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_
         est = dot;
         const R inv = from_d<R>(nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0);
         __syncwarp();
-        for (int i = lane; i < n; i += 32) x[i] = qt_scale(v[i], inv);
+        for (int i = lane; i < n; i += 32) setX(i, qt_scale(V(i), inv));
         __syncwarp();
       }
       if (lane == 0) res[warp] = est;
@@ -328,11 +348,11 @@ __global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_
       }
       if (active && part == 0) {
         const R one = (i == j) ? R(1) : R(0);
-        row[j] = qt_scale(QT<R>{one - acc.w, -acc.x, -acc.y, -acc.z}, inv);
+        row.set(j, qt_scale(QT<R>{one - acc.w, -acc.x, -acc.y, -acc.z}, inv));
       }
     }
     __syncthreads();
-    for (int j = tid; j <= i; j += nt) L[tri(i, j)] = row[j];
+    for (int j = tid; j <= i; j += nt) L.set(tri(i, j), row[j]);
     __syncthreads();
   }
   for (int e = tid; e < n * n; e += nt) {

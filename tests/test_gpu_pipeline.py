@@ -172,3 +172,56 @@ def test_fp32_pipeline_error_within_one_percent(pkg):
     Om, Psi = _emb(n, s, l, m, "gaussian", 3)
     ref = O.onepass(Ad.double().cpu().numpy(), Om, Psi, "pseudo_qr", 3)
     assert abs(err - ref["err"]) <= 0.01 * ref["err"], (err, ref["err"])
+
+
+_C2_SHAPED = {}
+
+
+def _c2_shaped_reference():
+    """sigma_i = i^-2 spectrum (rank cap 1024), s = 101, l = 203 at 2048 x 2048; the oracle's
+    one-pass result on the same FP32 input values."""
+    if not _C2_SHAPED:
+        m = n = 2048
+        s, l = 101, 203
+        A = WL.make_decay(m, n, seed=0, rank_cap=1024, dtype=np.float32)
+        Om, Psi = _emb(n, s, l, m, "gaussian", 0)
+        A64 = A.astype(np.float64)
+        ref = {}
+        for nc in (0, 3):
+            info = {}
+            r = O.onepass(A64, Om, Psi, "pseudo_qr", nc)
+            O.pseudo_qr(r["Y"], nc, info=info)
+            ref[nc] = (r["err"], info.get("eps", []))
+        _C2_SHAPED.update(A=A, A64=A64, Psi=Psi, s=s, l=l, ref=ref)
+    return _C2_SHAPED
+
+
+@pytest.mark.parametrize("ncorr", [3, 0])
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+def test_c2_shaped_pipeline(pkg, prec, ncorr):
+    """The bench workload's shape class at 2048 x 2048 in the FP32 modes.
+
+    * R(H) = R(Y) (Alg. 1): the distance of the GPU's own Y from the range of its H is at
+      FP32-rounding level (1e-6 bar; an FP32 product H = Y D with the correction factors
+      in D measured 2e-4 here).
+    * Final error against the oracle's: the sketches carry relative error <= 5e-6, whose
+      effect on HX is statistically independent of the residual A - HX and moves the error
+      by far less than 1e-4 relative (measured 4e-6); a bar of 1e-3 fails a range tilt
+      (1.4%) or an ill-conditioned core formed in FP32 (0.3% at kappa(H) = 7e3).
+    * After 3 corrections kappa(H) < 10 and the correction parameters follow the oracle's.
+    """
+    c = _c2_shaped_reference()
+    s, l = c["s"], c["l"]
+    qs, err, status, Ad = _run(pkg, c["A"], s, l, prec, ncorr=ncorr, seed=0)
+    ref_err, ref_eps = c["ref"][ncorr]
+    H = qs.get("H").cpu().double().numpy()
+    Y = qs.get("Y").cpu().double().numpy()
+    CH, CY = O.chi(H), O.chi(Y)
+    Qh, _ = np.linalg.qr(CH)
+    assert np.linalg.norm(CY - Qh @ (Qh.conj().T @ CY)) / np.linalg.norm(CY) < 1e-6
+    assert status == 0
+    assert abs(err - ref_err) <= 1e-3 * ref_err, (err, ref_err)
+    if ncorr == 3:
+        sv = np.linalg.svd(CH, compute_uv=False)
+        assert sv[0] / sv[-1] < 10
+        np.testing.assert_allclose(qs.get("scalars").cpu().numpy()[2:5], ref_eps, rtol=1e-3)
