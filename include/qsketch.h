@@ -152,6 +152,38 @@ QS_API qs_status qonepass_core(qs_handle_t h, void* stream);
 QS_API qs_status qreconstruct_error(qs_handle_t h, const void* const A_planes[4], int64_t lda,
                              double* rel_err_dev, void* stream);
 
+/* Allocation-free relative error (a service entry point; the paper has no counterpart).
+ * Computes ||A - H X||_F / ||A||_F, the error measure of Sec. 5, for factors the caller
+ * holds itself, with no handle and no workspace: for callers that did not build the
+ * factors through a handle (stored factors, another library) and cannot allocate one,
+ * since a device allocation synchronises the device and fails once the process's memory
+ * is fully reserved.
+ *   m, n, s   : A is m x n, H is m x s, X is s x n (quaternion), all >= 1.
+ *   dtype     : QS_DT_F64 (all planes FP64, FP64 accumulation) or QS_DT_F32 (all planes
+ *               FP32, FP32 accumulation of H X, FP64 sums of squares).
+ *   *_planes  : four device planes each, row-major with leading dimensions lda >= n,
+ *               ldh >= s, ldx >= n.  A_planes[0] may be NULL (pure quaternion A); H and X
+ *               planes may not.  Read only.
+ *   rel_err_dev: device pointer to one double, written on `stream`.
+ * Scratch: a library-owned static device array of 2 doubles per 64 x 64 tile of A, at
+ * most QS_STATIC_ERR_MAX_TILES tiles (1 MiB); nothing in it has to start at zero, every
+ * slot read is written earlier by the same call.  The sums are reduced in a fixed order,
+ * so the result is deterministic.
+ * Returns QS_ERR_INVALID for bad sizes, dtypes or pointers, QS_ERR_UNSUPPORTED when
+ * ceil(m/64) * ceil(n/64) > QS_STATIC_ERR_MAX_TILES (both before any CUDA call), and
+ * QS_ERR_CUDA when the scratch lookup or a launch fails.
+ * The first call on a device looks up the scratch address on the current device (once per
+ * device, cached); a caller that captures streams into graphs makes that first call before
+ * any capture.  The scratch is shared by every call on a device: two calls whose work may
+ * overlap in time (different streams without ordering, or several host threads) race on
+ * it; order them (one stream, or events). */
+#define QS_STATIC_ERR_MAX_TILES 65536
+QS_API qs_status qs_reconstruct_error_static(int64_t m, int64_t n, int64_t s, int32_t dtype,
+                                             const void* const A_planes[4], int64_t lda,
+                                             const void* const H_planes[4], int64_t ldh,
+                                             const void* const X_planes[4], int64_t ldx,
+                                             double* rel_err_dev, void* stream);
+
 /* Device pointer, leading dimension (elements), plane stride (elements) and element type
  * of an object in the workspace.  Views stay valid until qsketch_destroy. */
 QS_API qs_status qsketch_get(qs_handle_t h, int32_t which, void** dev_ptr, int64_t* ld,

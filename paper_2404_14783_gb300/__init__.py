@@ -10,7 +10,8 @@ package is its thin Python binding.  See ``QSketch`` for the calls:
     qs.error(A)                  # ||A - HX||_F / ||A||_F   (Sec. 5)
 """
 from .qsketch import (QSketch, QSError, QSConfig, load_library, ABI_SYMBOLS, LIB_PATH,
-                      PRECISIONS, EMBEDDINGS, RANGEFINDERS, launch_count)
+                      PRECISIONS, EMBEDDINGS, RANGEFINDERS, launch_count,
+                      reconstruct_error_static)
 
 __all__ = ["QSketch", "QSError", "QSConfig", "load_library", "ABI_SYMBOLS", "LIB_PATH",
-           "PRECISIONS", "EMBEDDINGS", "RANGEFINDERS", "launch_count"]
+           "PRECISIONS", "EMBEDDINGS", "RANGEFINDERS", "launch_count", "reconstruct_error_static"]

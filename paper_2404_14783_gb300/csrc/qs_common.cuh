@@ -130,6 +130,12 @@ cudaError_t launch_qgemm(const GemmDesc& d, cudaStream_t st);
 cudaError_t launch_scale(void* c, int f64, int64_t rows, int64_t cols, int64_t ld, int64_t ps,
                          double beta, cudaStream_t st, const double* gate = nullptr,
                          double gate_skip = 0.0);
+// Error pass of d (d.epi semantics: C holds A; sums of |A - HX|^2 and |A|^2) with the
+// per-tile sums stored at partials[2t], partials[2t+1] for t < ceil(M/64) ceil(N/64), then
+// reduced in a fixed order into *out = sqrt(num / den).  All of A, H, X FP64 or all FP32;
+// accumulation in their type.  Every partial read is written first by the same call.
+cudaError_t launch_qgemm_err_partials(const GemmDesc& d, double* partials, double* out,
+                                      cudaStream_t st);
 cudaError_t launch_qmirror(double* G, int64_t ld, int64_t ps, int n, cudaStream_t st,
                            const double* gate = nullptr, double gate_skip = 0.0);
 cudaError_t launch_draw(void* out, int f64, int64_t rows, int64_t cols, int kind, uint32_t stream,

@@ -25,7 +25,10 @@ __device__ __forceinline__ T ld_elem(const void* base, int64_t idx) {
 }
 
 // BCPLX: B has only its w and x planes (a complex matrix); the y and z products are skipped.
-template <typename ACC, typename TA, typename TB, typename TC, bool CONJ, bool BCPLX = false>
+// PARTIAL (error epilogue only): each CTA stores its two tile sums at err[2t], err[2t+1]
+// (t = its linear tile index) instead of adding them atomically into err[0], err[1].
+template <typename ACC, typename TA, typename TB, typename TC, bool CONJ, bool BCPLX = false,
+          bool PARTIAL = false>
 __global__ void __launch_bounds__(256, sizeof(ACC) == 4 ? 2 : 1) qgemm_kernel(GemmDesc g) {
   constexpr int BM = 64, BN = 64;
   constexpr int BK = sizeof(ACC) == 8 ? 4 : 8;
@@ -165,8 +168,14 @@ __global__ void __launch_bounds__(256, sizeof(ACC) == 4 ? 2 : 1) qgemm_kernel(Ge
     if (tid == 0) {
       double a0 = 0.0, a1 = 0.0;
       for (int w = 0; w < 8; ++w) { a0 += red[0][w]; a1 += red[1][w]; }
-      atomicAdd(g.err, a0);
-      atomicAdd(g.err + 1, a1);
+      if (PARTIAL) {
+        const int64_t t = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+        g.err[2 * t] = a0;
+        g.err[2 * t + 1] = a1;
+      } else {
+        atomicAdd(g.err, a0);
+        atomicAdd(g.err + 1, a1);
+      }
     }
     return;
   }
@@ -252,6 +261,29 @@ __global__ void __launch_bounds__(256) qgemm_small_kernel(GemmDesc g) {
     else if (g.beta == 0.0) *dst = static_cast<TC>(v[q]);
     else *dst = static_cast<TC>(v[q] + ACC(g.beta) * ACC(*dst));
   }
+}
+
+// Sum of the per-tile error partials in a fixed order (one CTA of 256 threads): thread i
+// adds tiles i, i + 256, ... in turn, then a fixed pairwise tree; out = sqrt(num / den).
+__global__ void __launch_bounds__(256) err_partials_reduce_kernel(const double* part,
+                                                                  int64_t tiles, double* out) {
+  __shared__ double sn[256], sd[256];
+  double num = 0.0, den = 0.0;
+  for (int64_t t = threadIdx.x; t < tiles; t += 256) {
+    num += part[2 * t];
+    den += part[2 * t + 1];
+  }
+  sn[threadIdx.x] = num;
+  sd[threadIdx.x] = den;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      sn[threadIdx.x] += sn[threadIdx.x + w];
+      sd[threadIdx.x] += sd[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sd[0] > 0.0 ? sqrt(sn[0] / sd[0]) : 0.0;
 }
 
 // Lower triangle of a Hermitian quaternion matrix from its upper triangle: G_ji = conj(G_ij).
@@ -367,6 +399,25 @@ cudaError_t launch_qgemm(const GemmDesc& d, cudaStream_t st) {
   if (d.acc_f64 == 2)
     return d.a_f64 ? launch_b<df64, double>(d, st) : launch_b<df64, float>(d, st);
   return d.a_f64 ? launch_b<double, double>(d, st) : launch_b<double, float>(d, st);
+}
+
+cudaError_t launch_qgemm_err_partials(const GemmDesc& d, double* partials, double* out,
+                                      cudaStream_t st) {
+  if (d.M <= 0 || d.N <= 0 || d.K <= 0 || !partials || !out) return cudaErrorInvalidValue;
+  if (d.a_f64 != d.b_f64 || d.a_f64 != d.c_f64 || d.conj_a) return cudaErrorInvalidValue;
+  GemmDesc g = d;
+  g.epi = 1; g.err = partials; g.splits = 1; g.small = 0; g.gate = nullptr; g.herm = 0;
+  const dim3 grid((unsigned)((d.M + 63) / 64), (unsigned)((d.N + 63) / 64), 1);
+  if (d.a_f64)
+    qgemm_kernel<double, double, double, double, false, false, true><<<grid, 256, 0, st>>>(g);
+  else
+    qgemm_kernel<float, float, float, float, false, false, true><<<grid, 256, 0, st>>>(g);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  err_partials_reduce_kernel<<<1, 256, 0, st>>>(partials, (int64_t)grid.x * grid.y, out);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_scale(void* c, int f64, int64_t rows, int64_t cols, int64_t ld, int64_t ps,

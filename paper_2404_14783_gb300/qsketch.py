@@ -28,7 +28,8 @@ RANGEFINDERS = {"pseudo_qr": QS_RF_PSEUDO_QR, "pseudo_svd": QS_RF_PSEUDO_SVD}
 
 ABI_SYMBOLS = ("qsketch_workspace_bytes", "qsketch_create", "qsketch_update", "qrangefinder",
                "qonepass_core", "qreconstruct_error", "qsketch_get", "qs_last_device_error",
-               "qsketch_destroy", "qs_status_string", "qs_launch_count", "qs_version")
+               "qsketch_destroy", "qs_status_string", "qs_launch_count", "qs_version",
+               "qs_reconstruct_error_static")
 
 
 class QSConfig(ctypes.Structure):
@@ -70,8 +71,11 @@ def load_library(path=LIB_PATH):
     lib.qs_status_string.restype = ctypes.c_char_p
     lib.qs_version.restype = I32
     lib.qs_launch_count.restype = I64
+    lib.qs_reconstruct_error_static.argtypes = [I64, I64, I64, I32, planes, I64, planes, I64,
+                                                planes, I64, VP, VP]
     for name in ("qsketch_create", "qsketch_update", "qrangefinder", "qonepass_core",
-                 "qreconstruct_error", "qsketch_get", "qs_last_device_error", "qsketch_destroy"):
+                 "qreconstruct_error", "qsketch_get", "qs_last_device_error", "qsketch_destroy",
+                 "qs_reconstruct_error_static"):
         getattr(lib, name).restype = I32
     _lib = lib
     return lib
@@ -80,6 +84,38 @@ def load_library(path=LIB_PATH):
 def launch_count():
     """Kernel launches the library has enqueued in this process."""
     return int(load_library().qs_launch_count())
+
+
+def reconstruct_error_static(A, H, X, out, stream=None):
+    """||A - H X||_F / ||A||_F through qs_reconstruct_error_static (no handle, no workspace).
+
+    A (m x n), H (m x s), X (s x n): (4, rows, cols) CUDA tensors or lists of four planes
+    (A's first plane may be None), all float64 or all float32, row-major planes.  `out` is a
+    1-element CUDA float64 tensor the result is written to on `stream`; the caller provides
+    it so that the call itself allocates nothing."""
+    lib = load_library()
+    f64 = out.dtype == torch.float64 and _dtype_of(H) == torch.float64
+    a_ptrs, lda = _planes(A, f64)
+    h_ptrs, ldh = _planes(H, f64)
+    x_ptrs, ldx = _planes(X, f64)
+    m, s = _shape_of(H)
+    n = _shape_of(X)[1]
+    _check(lib.qs_reconstruct_error_static(m, n, s, QS_DT_F64 if f64 else QS_DT_F32, a_ptrs, lda,
+                                           h_ptrs, ldh, x_ptrs, ldx,
+                                           ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+           "qs_reconstruct_error_static")
+    return out
+
+
+def _dtype_of(M):
+    return M.dtype if isinstance(M, torch.Tensor) else next(t for t in M if t is not None).dtype
+
+
+def _shape_of(M):
+    if isinstance(M, torch.Tensor):
+        return int(M.shape[1]), int(M.shape[2])
+    ref = next(t for t in M if t is not None)
+    return int(ref.shape[0]), int(ref.shape[1])
 
 
 def _status_string(code):
