@@ -11,6 +11,7 @@
 
 #include "qs_common.cuh"
 #include "qs_small.cuh"
+#include "qs_err_tc.cuh"
 #include "qs_sketch_tc.cuh"
 
 using namespace qs;
@@ -66,12 +67,13 @@ size_t plan(const qs_config& c, qs_handle_s* h) {
   const size_t pack_bytes = tc_pack_bytes(c);
   size_t o_pack = take(pack_bytes);
   size_t o_psvd = take(psvd_work_bytes(c.s));
+  size_t o_epack = take(tc_mode(c.prec) ? err_tc_pack_bytes(c.m, c.n, c.s) : 0);
   if (h) {
     h->esize = (int)es;
     h->off_status = o_status; h->off_scalars = o_scal; h->off_omega = o_om; h->off_psi = o_psi;
     h->off_y = o_y; h->off_w = o_w; h->off_h = o_h; h->off_x = o_x; h->off_gram = o_gram;
     h->off_small = o_small; h->off_p = o_p; h->off_core = o_core; h->off_pack = o_pack;
-    h->off_psvd = o_psvd;
+    h->off_psvd = o_psvd; h->off_epack = o_epack;
     h->off_tail = off; h->small_bytes = small_bytes; h->core_bytes = core_bytes;
     h->pack_bytes = pack_bytes;
   }
@@ -464,6 +466,15 @@ qs_status qreconstruct_error(qs_handle_t h, const void* const A_planes[4], int64
   Ctx x{h, st, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64};
   double* sc = x.scalars();
   QS_CU(cudaMemsetAsync(sc + kScErrNum, 0, 2 * sizeof(double), st));
+  const void* Ap[4] = {A_planes[0], A_planes[1], A_planes[2], A_planes[3]};
+  if (c.pure) Ap[0] = nullptr;
+  if (tc_mode(c.prec) && err_tc_supported(Ap, lda)) {
+    // tensor-core modes: H X on the tensor cores (split BF16), residual in FP32
+    QS_CU(launch_err_tc(Ap, lda, static_cast<const float*>(x.H().p), static_cast<const float*>(x.X().p),
+                        c.m, c.n, c.s, h->ws + h->off_epack, sc + kScErrNum, x.status(), st));
+    QS_CU(launch_finalize_err(sc, rel_err_dev, st));
+    return QS_OK;
+  }
   GemmDesc d{};
   d.M = c.m; d.N = c.n; d.K = c.s;
   x.H().cplanes(d.a); d.lda = c.s; d.a_f64 = x.f64;

@@ -1,11 +1,14 @@
 """The allocation-free error entry point (qs_reconstruct_error_static) against the handle's
 error pass (qreconstruct_error), through the C ABI.
 
-Both run the same per-tile arithmetic of the SIMT product's error epilogue; only the order
-in which the tile sums are added differs (atomics versus a fixed-order reduction), so the
-two agree to FP64 summation rounding: 1e-12 relative.  The static path is deterministic,
-so two calls in a row return the same bits; the second call also shows that no state left
-in the static scratch by the first one leaks into the result.
+In the FP64 and FP32 modes both run the same per-tile arithmetic of the SIMT product's error
+epilogue; only the order in which the tile sums are added differs (atomics versus a
+fixed-order reduction), so the two agree to FP64 summation rounding: 1e-12 relative.  In the
+split-BF16 mode the handle's pass runs on the tensor cores (H X from BF16 hi/lo pairs), which
+moves the error by at most 2^-15 ||M||_F / ||A||_F, M = |H| |X| over the Hamilton terms.
+The static path is deterministic, so two calls in a row return the same bits; the second
+call also shows that no state left in the static scratch by the first one leaks into the
+result.
 """
 import ctypes
 
@@ -44,6 +47,18 @@ def _pipeline(pkg, m, n, s, l, prec, pure=False, seed=5):
     return qs, planes, ref
 
 
+_PLANE = [[0, 1, 2, 3], [1, 0, 3, 2], [2, 3, 0, 1], [3, 2, 1, 0]]
+
+
+def _split_bf16_bound(planes, H, X):
+    Hn = H.double().cpu().numpy()
+    Xn = X.double().cpu().numpy()
+    An = np.stack([np.zeros(Hn.shape[1:2] + Xn.shape[2:]) if p is None else p.double().cpu().numpy()
+                   for p in planes])
+    M = np.stack([sum(np.abs(Hn[_PLANE[q][b]]) @ np.abs(Xn[b]) for b in range(4)) for q in range(4)])
+    return 2.0 ** -15 * np.linalg.norm(M) / np.linalg.norm(An)
+
+
 def _static_twice(pkg, planes, H, X):
     out = torch.empty(1, dtype=torch.float64, device="cuda")
     r1 = float(pkg.reconstruct_error_static(planes, H, X, out).item())
@@ -58,7 +73,10 @@ def test_static_error_matches_handle_error(pkg, m, n, s, l, prec):
     qs, planes, ref = _pipeline(pkg, m, n, s, l, prec)
     r1, r2 = _static_twice(pkg, planes, qs.get("H"), qs.get("X"))
     assert ref > 0
-    assert abs(r1 - ref) <= 1e-12 * ref, (r1, ref)
+    tol = 1e-12 * ref
+    if prec == "bf16x3":
+        tol += _split_bf16_bound(planes, qs.get("H"), qs.get("X"))
+    assert abs(r1 - ref) <= tol, (r1, ref, tol)
     assert r2 == r1
 
 
