@@ -39,6 +39,16 @@ __device__ __forceinline__ df64 df_fast_two_sum(float a, float b) {
   return df64(s, e);
 }
 
+// Renormalised copy (|lo| <= ulp(hi) / 2) by TwoSum: the compensated fma() below leaves lo
+// unnormalised, so hi alone may even have the wrong sign; anything that starts from an FP32
+// estimate of hi (reciprocal, square root) renormalises first.
+__device__ __forceinline__ df64 df_norm(df64 a) {
+  const float s = __fadd_rn(a.hi, a.lo);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(a.lo, bb));
+  return df64(s, e);
+}
+
 __device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
 
 __device__ __forceinline__ df64 operator+(df64 a, df64 b) {

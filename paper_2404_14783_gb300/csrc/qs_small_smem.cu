@@ -107,23 +107,121 @@ struct QA {
   __device__ static QA make(R* base, int cap) { return QA{base, base + cap, base + 2 * cap, base + 3 * cap}; }
 };
 
+
+// Complex-aware variants: with C (complex_only) the y and z components are identically zero
+// and are neither stored nor computed.
+template <typename R, bool C>
+__device__ __forceinline__ QT<R> qsub_mul_conj(QT<R> c, const QT<R>& a, const QT<R>& b) {
+  if constexpr (C) {  // complex: c - a conj(b)
+    c.w = fma(-a.w, b.w, fma(-a.x, b.x, c.w));
+    c.x = fma(a.w, b.x, fma(-a.x, b.w, c.x));
+    return c;
+  } else {
+    return qt_sub_mul_conj(c, a, b);
+  }
+}
+template <typename R, bool C>
+__device__ __forceinline__ QT<R> qmac(QT<R> c, const QT<R>& a, const QT<R>& b) {
+  if constexpr (C) {
+    c.w = fma(a.w, b.w, fma(-a.x, b.x, c.w));
+    c.x = fma(a.w, b.x, fma(a.x, b.w, c.x));
+    return c;
+  } else {
+    return qt_mac(c, a, b);
+  }
+}
+template <typename R, bool C>
+__device__ __forceinline__ QT<R> qscale(const QT<R>& a, R s) {
+  if constexpr (C) return QT<R>{a.w * s, a.x * s, R(0), R(0)};
+  else return qt_scale(a, s);
+}
+
+__device__ __forceinline__ double nrm_(double v) { return v; }
+__device__ __forceinline__ df64 nrm_(df64 v) { return df_norm(v); }
+
+// Quaternion array in shared memory stored component-wise (structure of arrays); with C only
+// the w and x components exist.  Double-float values are renormalised when stored, so every
+// value read back has |lo| <= ulp(hi) / 2.
+template <typename R, bool C>
+struct QS {
+  R* c0;
+  R* c1;
+  R* c2;
+  R* c3;
+  __device__ __forceinline__ QT<R> operator[](int i) const {
+    if constexpr (C) return QT<R>{c0[i], c1[i], R(0), R(0)};
+    else return QT<R>{c0[i], c1[i], c2[i], c3[i]};
+  }
+  __device__ __forceinline__ void set(int i, const QT<R>& v) const {
+    c0[i] = nrm_(v.w); c1[i] = nrm_(v.x);
+    if constexpr (!C) { c2[i] = nrm_(v.y); c3[i] = nrm_(v.z); }
+  }
+  __device__ static QS make(R* base, int cap) {
+    return C ? QS{base, base + cap, nullptr, nullptr}
+             : QS{base, base + cap, base + 2 * cap, base + 3 * cap};
+  }
+};
+
+// Reciprocal and square root in the working type (double-float: renormalise, FP32 estimate
+// plus one Newton step, about 46 correct bits).
+__device__ __forceinline__ double rcp_(double d) { return 1.0 / d; }
+__device__ __forceinline__ double sqrt_(double d) { return sqrt(d); }
+__device__ __forceinline__ df64 rcp_(df64 d) {
+  d = df_norm(d);
+  const float r0 = __frcp_rn(d.hi);
+  const df64 e = df64(1.f, 0.f) - d * df64(r0, 0.f);          // 1 - d r0
+  return df64(r0, 0.f) + df64(r0, 0.f) * e;
+}
+__device__ __forceinline__ df64 sqrt_(df64 d) {
+  d = df_norm(d);
+  const float s0 = __fsqrt_rn(d.hi);
+  const df64 sq = df64(s0, 0.f) * df64(s0, 0.f);
+  const float corr = __fdiv_rn((d - sq).hi, 2.f * s0);
+  return df_fast_two_sum(s0, corr);
+}
+
+// Row (ii) and column (kk) of entry f of a packed lower triangle (0 <= kk <= ii).
+__device__ __forceinline__ void tri_rc(int f, int& ii, int& kk) {
+  int i = (int)((sqrtf(8.0f * (float)f + 1.0f) - 1.0f) * 0.5f);
+  while (tri(i + 1, 0) <= f) ++i;
+  while (tri(i, 0) > f) --i;
+  ii = i;
+  kk = f - tri(i, 0);
+}
+
+// Sum over the 8 lanes of an aligned lane group (partial sums of one output).
 template <typename R>
+__device__ __forceinline__ R gsum8(R v) {
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    if constexpr (std::is_same<R, double>::value) {
+      v = v + __shfl_xor_sync(0xffffffffu, v, o);
+    } else {
+      v = v + df64(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+    }
+  }
+  return v;
+}
+template <typename R>
+__device__ __forceinline__ QT<R> gsum8q(QT<R> v) {
+  return QT<R>{gsum8(v.w), gsum8(v.x), gsum8(v.y), gsum8(v.z)};
+}
+
+template <typename R, bool C>
 __global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_t ldg, int64_t psg,
                                                          double* Li, int64_t ldl, int64_t psl, int n,
-                                                         int complex_only, int allow_shift,
-                                                         double shift_rows, int power_slot,
-                                                         double kappa_stop, int32_t* status,
-                                                         double* scalars, int fail_bits,
-                                                         double* Lout) {
+                                                         int allow_shift, double shift_rows,
+                                                         int power_slot, double kappa_stop,
+                                                         int32_t* status, double* scalars,
+                                                         int fail_bits, double* Lout) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
+  constexpr int NC = C ? 2 : 4;
   const int ntri = n * (n + 1) / 2;
   R* sbase = reinterpret_cast<R*>(smem_raw);
-  const QA<R> L = QA<R>::make(sbase, ntri);                 // packed lower triangle
-  const QA<R> row = QA<R>::make(sbase + 4 * ntri, n);       // scratch row
-  const QA<R> vec = QA<R>::make(sbase + 4 * ntri + 4 * n, 4 * n);  // 4 vectors for the power iterates
-  __shared__ int fail;
-  __shared__ double shift, inv_d;
-  __shared__ double red[32];
+  const QS<R, C> L = QS<R, C>::make(sbase, ntri);                 // packed lower triangle
+  const QS<R, false> row = QS<R, false>::make(sbase + NC * ntri, n);      // scratch row
+  const QS<R, false> vec = QS<R, false>::make(sbase + NC * ntri + 4 * n, 4 * n);  // power vectors
+  __shared__ double red[2][32];
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
   auto gget = [&](int i, int j, int p) { return G[p * psg + (int64_t)i * ldg + j]; };
   auto write_identity = [&]() {
@@ -137,57 +235,67 @@ __global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_
     write_identity();
     return;
   }
-  if (tid == 0) shift = 0.0;
-  __syncthreads();
+  // ---------------------------------------------------------------- Cholesky G (+ shift) = L L*
+  // Right-looking, one barrier per column: in the pass of column j every thread reads the
+  // pivot d_j, and the threads share, flat, the trailing update L_ik -= L_ij conj(L_kj) / d_j
+  // (j < k <= i) together with the scaling of column j - 1 by 1/sqrt(d_{j-1}), which no
+  // thread of this pass reads.
+  double shift = 0.0;
+  bool fail = false;
   for (int attempt = 0; attempt < 2; ++attempt) {
-    for (int e = tid; e < n * (n + 1) / 2; e += nt) {
-      int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-      while (tri(i + 1, 0) <= e) ++i;
-      while (tri(i, 0) > e) --i;
-      const int j = e - tri(i, 0);
-      double w = gget(i, j, 0), x = gget(i, j, 1), y = gget(i, j, 2), z = gget(i, j, 3);
-      if (complex_only) { y = 0.0; z = 0.0; }
+    for (int e = tid; e < ntri; e += nt) {
+      int i, j;
+      tri_rc(e, i, j);
+      double w = gget(i, j, 0), x = gget(i, j, 1), y = 0.0, z = 0.0;
+      if (!C) { y = gget(i, j, 2); z = gget(i, j, 3); }
       if (i == j) { x = y = z = 0.0; w += shift; }
       L.set(e, QT<R>{from_d<R>(w), from_d<R>(x), from_d<R>(y), from_d<R>(z)});
     }
-    if (tid == 0) fail = 0;
     __syncthreads();
-    for (int j = 0; j < n; ++j) {
-      if (tid == 0) {
-        const double d = to_d(L[tri(j, j)].w);
-        if (!(d > 0.0) || !isfinite(d)) {
-          fail = 1;
+    fail = false;
+    R dprev = R(0);
+    for (int j = 0; j <= n; ++j) {
+      R inv_d = R(0), dj = R(0);
+      if (j < n) {
+        dj = L[tri(j, j)].w;
+        const double dd = to_d(dj);
+        if (!(dd > 0.0) || !isfinite(dd)) { fail = true; break; }   // same value in every thread
+        inv_d = rcp_(dj);
+      }
+      const int c = j - 1;
+      const int S = c >= 0 ? n - c : 0;
+      const int T = j < n ? (n - j - 1) * (n - j) / 2 : 0;
+      R r = R(0), inv_r = R(0);
+      if (S > 0) { r = sqrt_(dprev); inv_r = rcp_(r); }
+      for (int e = tid; e < S + T; e += nt) {
+        if (e < S) {
+          const int i = c + e;
+          if (e == 0) L.set(tri(c, c), QT<R>{r, R(0), R(0), R(0)});
+          else L.set(tri(i, c), qscale<R, C>(L[tri(i, c)], inv_r));
         } else {
-          const double r = sqrt(d);
-          L.set(tri(j, j), QT<R>{from_d<R>(r), R(0), R(0), R(0)});
-          inv_d = 1.0 / r;
+          int ii, kk;
+          tri_rc(e - S, ii, kk);
+          const int i = j + 1 + ii, k = j + 1 + kk;
+          const QT<R> a = qscale<R, C>(L[tri(i, j)], inv_d);
+          L.set(tri(i, k), qsub_mul_conj<R, C>(L[tri(i, k)], a, L[tri(k, j)]));
         }
       }
-      __syncthreads();
-      if (fail) break;
-      const R inv = from_d<R>(inv_d);
-      for (int i = j + 1 + tid; i < n; i += nt) L.set(tri(i, j), qt_scale(L[tri(i, j)], inv));
-      __syncthreads();
-      for (int i = j + 1 + warp; i < n; i += nw) {
-        const QT<R> lij = L[tri(i, j)];
-        for (int k = j + 1 + lane; k <= i; k += 32)
-          L.set(tri(i, k), qt_sub_mul_conj(L[tri(i, k)], lij, L[tri(k, j)]));
-      }
+      dprev = dj;
       __syncthreads();
     }
-    __syncthreads();
     if (!fail) break;
     if (attempt == 0 && allow_shift) {
+      // shifted Cholesky-QR: shift = 11 (rows s + s (s + 1)) u trace(G)
       double tr = 0.0;
       for (int i = tid; i < n; i += nt) tr += gget(i, i, 0);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-      if (lane == 0) red[warp] = tr;
+      if (lane == 0) red[0][warp] = tr;
       __syncthreads();
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += red[0][w];
+      shift = 11.0 * (shift_rows * n + (double)n * (n + 1)) * 1.1102230246251565e-16 * t;
       if (tid == 0) {
-        double t = 0.0;
-        for (int w = 0; w < nw; ++w) t += red[w];
-        shift = 11.0 * (shift_rows * n + (double)n * (n + 1)) * 1.1102230246251565e-16 * t;
         scalars[kScShift] = shift;
         atomicOr(status, kDevRank);
       }
@@ -213,93 +321,118 @@ __global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_
       Lout[3 * psl + (int64_t)i * ldl + j] = to_d(v.z);
     }
   }
-  // ---------------------------------------------------------------- power iterates
-  if (power_slot >= 0) {
-    __shared__ double res[2];
-    if (warp < 2) {
-      const int vo = warp * n, xo = (2 + warp) * n;  // current vector / work vector offsets
-      auto V = [&](int i) { return vec[vo + i]; };
-      auto X = [&](int i) { return vec[xo + i]; };
-      auto setV = [&](int i, const QT<R>& q) { vec.set(vo + i, q); };
-      auto setX = [&](int i, const QT<R>& q) { vec.set(xo + i, q); };
-      const double c = 1.0 / sqrt(2.0 * n);
-      for (int i = lane; i < n; i += 32) setX(i, QT<R>{from_d<R>(c), R(0), from_d<R>(-c), R(0)});
-      __syncwarp();
-      double est = 0.0;
-      for (int it = 0; it < 3; ++it) {
-        if (warp == 0) {
-          // v = G^{-1} x: L y = x, then L* v = y
-          for (int i = lane; i < n; i += 32) setV(i, X(i));
-          __syncwarp();
-          for (int i = 0; i < n; ++i) {
-            QT<R> acc{R(0), R(0), R(0), R(0)};
-            for (int k = lane; k < i; k += 32) acc = qt_mac(acc, L[tri(i, k)], V(k));
-            acc = wsum4(acc);
-            if (lane == 0) {
-              const R inv = from_d<R>(1.0 / to_d(L[tri(i, i)].w));
-              const QT<R> b = V(i);
-              setV(i, qt_scale(QT<R>{b.w - acc.w, b.x - acc.x, b.y - acc.y, b.z - acc.z}, inv));
-            }
-            __syncwarp();
+  // ---------------------------------------------------------------- L^{-1} in place
+  // row i of X = L^{-1}: X_ij = (delta_ij - sum_{j<=k<i} L_ik X_kj) / L_ii, rows k < i already X;
+  // 8 lanes share each output
+  constexpr int P = 8;
+  for (int i = 0; i < n; ++i) {
+    const R inv = rcp_(L[tri(i, i)].w);
+    const int work = (i + 1) * P, work_r = (work + 31) & ~31;
+    for (int t = tid; t < work_r; t += nt) {
+      const int j = t / P, part = t % P;
+      const bool active = t < work;
+      QT<R> acc{R(0), R(0), R(0), R(0)};
+      if (active)
+        for (int k = j + part; k < i; k += P) acc = qmac<R, C>(acc, L[tri(i, k)], L[tri(k, j)]);
+      acc.w = gsum8(acc.w);
+      acc.x = gsum8(acc.x);
+      if (!C) {
+        acc.y = gsum8(acc.y);
+        acc.z = gsum8(acc.z);
+      }
+      if (active && part == 0) {
+        const R one = (i == j) ? R(1) : R(0);
+        row.set(j, qscale<R, C>(QT<R>{one - acc.w, -acc.x, -acc.y, -acc.z}, inv));
+      }
+    }
+    __syncthreads();
+    for (int j = tid; j <= i; j += nt) L.set(tri(i, j), row[j]);
+    __syncthreads();
+  }
+  // ---------------------------------------------------------------- power iterates (Sec. 3.1)
+  // eps: rho = x* G^{-1} x = ||L^{-1} x||^2 on the iterates x <- G^{-1} x / |G^{-1} x| from
+  // (c, 0, -c, 0), eps = 1 / sqrt(rho); lambda_max(G) from iterates z <- G z / |G z| on G
+  // itself; kappa(H) = sqrt(lambda_max(G) rho).  Each output of a matrix-vector product is a
+  // dot product shared by 8 lanes.
+  if (power_slot >= 0 && !C) {
+    const int X0 = 0, Y0 = n, Z0 = 2 * n, U0 = 3 * n;   // x, y = L^{-1} x, z, u = G z in vec
+    const double c0 = 1.0 / sqrt(2.0 * n);
+    for (int i = tid; i < n; i += nt) {
+      vec.set(X0 + i, QT<R>{from_d<R>(c0), R(0), from_d<R>(-c0), R(0)});
+      vec.set(Z0 + i, QT<R>{from_d<R>(c0), R(0), from_d<R>(-c0), R(0)});
+    }
+    __syncthreads();
+    double rho = 0.0, lam = 0.0;
+    const int grp = tid / P, part = tid % P, ngrp = nt / P;
+    for (int it = 0; it < 3; ++it) {
+      // y = L^{-1} x (lower) and u = G z
+      for (int ob = 0; ob < 2 * n; ob += ngrp) {   // trip count uniform over the block
+        const int o = ob + grp;
+        QT<R> acc{R(0), R(0), R(0), R(0)};
+        if (o < n) {
+          for (int k = part; k <= o; k += P) acc = qt_mac(acc, L[tri(o, k)], vec[X0 + k]);
+        } else if (o < 2 * n) {
+          const int i = o - n;
+          for (int k = part; k < n; k += P) {
+            const QT<R> g{from_d<R>(gget(i, k, 0)), from_d<R>(gget(i, k, 1)), from_d<R>(gget(i, k, 2)),
+                          from_d<R>(gget(i, k, 3))};
+            acc = qt_mac(acc, g, vec[Z0 + k]);
           }
-          for (int i = n - 1; i >= 0; --i) {
-            QT<R> acc{R(0), R(0), R(0), R(0)};
-            for (int k = i + 1 + lane; k < n; k += 32) acc = qt_mac_conj_a(acc, L[tri(k, i)], V(k));
-            acc = wsum4(acc);
-            if (lane == 0) {
-              const R inv = from_d<R>(1.0 / to_d(L[tri(i, i)].w));
-              const QT<R> b = V(i);
-              setV(i, qt_scale(QT<R>{b.w - acc.w, b.x - acc.x, b.y - acc.y, b.z - acc.z}, inv));
-            }
-            __syncwarp();
-          }
-        } else {
-          // t = L* x (kept in v), then w = L t (into x)
-          for (int i = lane; i < n; i += 32) {
-            QT<R> acc{R(0), R(0), R(0), R(0)};
-            for (int k = i; k < n; ++k) acc = qt_mac_conj_a(acc, L[tri(k, i)], X(k));
-            setV(i, acc);
-          }
-          __syncwarp();
         }
-        double dot = 0.0, nrm = 0.0;
-        if (warp == 0) {
-          for (int i = lane; i < n; i += 32) {
-            const QT<R> a = X(i), b = V(i);
-            dot += to_d(a.w) * to_d(b.w) + to_d(a.x) * to_d(b.x) + to_d(a.y) * to_d(b.y) + to_d(a.z) * to_d(b.z);
-            nrm += to_d(b.w) * to_d(b.w) + to_d(b.x) * to_d(b.x) + to_d(b.y) * to_d(b.y) + to_d(b.z) * to_d(b.z);
-          }
-        } else {
-          for (int i = lane; i < n; i += 32) {
-            const QT<R> t = V(i);
-            dot += to_d(t.w) * to_d(t.w) + to_d(t.x) * to_d(t.x) + to_d(t.y) * to_d(t.y) + to_d(t.z) * to_d(t.z);
-          }
-          for (int i = lane; i < n; i += 32) {
-            QT<R> acc{R(0), R(0), R(0), R(0)};
-            for (int k = 0; k <= i; ++k) acc = qt_mac(acc, L[tri(i, k)], V(k));
-            nrm += to_d(acc.w) * to_d(acc.w) + to_d(acc.x) * to_d(acc.x) + to_d(acc.y) * to_d(acc.y) +
-                   to_d(acc.z) * to_d(acc.z);
-            row.set(i, acc);  // row[] is free until the inverse; warp 1 owns it here
-          }
-          __syncwarp();
-          for (int i = lane; i < n; i += 32) setV(i, row[i]);
+        acc = gsum8q(acc);
+        if (part == 0 && o < 2 * n) vec.set((o < n ? Y0 : U0 - n) + o, acc);
+      }
+      __syncthreads();
+      // x <- L^{-*} y normalised (into the row scratch first), z <- u / |u|
+      for (int kb = 0; kb < n; kb += ngrp) {
+        const int k = kb + grp;
+        QT<R> acc{R(0), R(0), R(0), R(0)};
+        if (k < n)
+          for (int i = k + part; i < n; i += P) acc = qt_mac_conj_a(acc, L[tri(i, k)], vec[Y0 + i]);
+        acc = gsum8q(acc);
+        if (part == 0 && k < n) row.set(k, acc);
+      }
+      if (warp == nw - 1) {  // |y|^2 = rho, z* u = lambda, |u|^2
+        double sy = 0.0, zu = 0.0, su = 0.0;
+        for (int i = lane; i < n; i += 32) {
+          const QT<R> yv = vec[Y0 + i], zv = vec[Z0 + i], uv = vec[U0 + i];
+          sy += to_d(yv.w) * to_d(yv.w) + to_d(yv.x) * to_d(yv.x) + to_d(yv.y) * to_d(yv.y) + to_d(yv.z) * to_d(yv.z);
+          zu += to_d(zv.w) * to_d(uv.w) + to_d(zv.x) * to_d(uv.x) + to_d(zv.y) * to_d(uv.y) + to_d(zv.z) * to_d(uv.z);
+          su += to_d(uv.w) * to_d(uv.w) + to_d(uv.x) * to_d(uv.x) + to_d(uv.y) * to_d(uv.y) + to_d(uv.z) * to_d(uv.z);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          dot += __shfl_xor_sync(0xffffffffu, dot, o);
-          nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+          sy += __shfl_xor_sync(0xffffffffu, sy, o);
+          zu += __shfl_xor_sync(0xffffffffu, zu, o);
+          su += __shfl_xor_sync(0xffffffffu, su, o);
         }
-        est = dot;
-        const R inv = from_d<R>(nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0);
-        __syncwarp();
-        for (int i = lane; i < n; i += 32) setX(i, qt_scale(V(i), inv));
-        __syncwarp();
+        if (lane == 0) { red[0][0] = sy; red[0][1] = zu; red[0][2] = su; }
       }
-      if (lane == 0) res[warp] = est;
+      __syncthreads();
+      rho = red[0][0];
+      lam = red[0][1];
+      const double su = red[0][2];
+      if (warp == 0) {  // |L^{-*} y|^2
+        double sv = 0.0;
+        for (int i = lane; i < n; i += 32) {
+          const QT<R> v = row[i];
+          sv += to_d(v.w) * to_d(v.w) + to_d(v.x) * to_d(v.x) + to_d(v.y) * to_d(v.y) + to_d(v.z) * to_d(v.z);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+        if (lane == 0) red[1][0] = sv;
+      }
+      __syncthreads();
+      const R inv_v = from_d<R>(red[1][0] > 0.0 ? 1.0 / sqrt(red[1][0]) : 0.0);
+      const R inv_u = from_d<R>(su > 0.0 ? 1.0 / sqrt(su) : 0.0);
+      for (int i = tid; i < n; i += nt) {
+        vec.set(X0 + i, qt_scale(row[i], inv_v));
+        vec.set(Z0 + i, qt_scale(vec[U0 + i], inv_u));
+      }
+      __syncthreads();
     }
-    __syncthreads();
     if (tid == 0) {
-      const double r = res[0], lm = res[1];
+      const double r = rho, lm = lam;
       if (!(r > 0.0) || !isfinite(r)) {
         scalars[power_slot] = 0.0;
         atomicOr(status, kDevRank | kDevStopCorr);
@@ -318,42 +451,6 @@ __global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_
         scalars[kScGate] = (u * kap * kap * kap < 0.04) ? 1.0 : 0.0;
       }
     }
-    __syncthreads();
-  }
-  // ---------------------------------------------------------------- L^{-1} in place
-  // row i of X = L^{-1}: X_ij = (delta_ij - sum_{j<=k<i} L_ik X_kj) / L_ii, rows k < i already X
-  constexpr int P = 8;
-  for (int i = 0; i < n; ++i) {
-    const R inv = from_d<R>(1.0 / to_d(L[tri(i, i)].w));
-    const int work = (i + 1) * P, work_r = (work + 31) & ~31;
-    for (int t = tid; t < work_r; t += nt) {
-      const int j = t / P, part = t % P;
-      const bool active = t < work;
-      QT<R> acc{R(0), R(0), R(0), R(0)};
-      if (active)
-        for (int k = j + part; k < i; k += P) acc = qt_mac(acc, L[tri(i, k)], L[tri(k, j)]);
-#pragma unroll
-      for (int o = P / 2; o > 0; o >>= 1) {
-        if constexpr (std::is_same<R, double>::value) {
-          acc.w = acc.w + __shfl_xor_sync(0xffffffffu, acc.w, o);
-          acc.x = acc.x + __shfl_xor_sync(0xffffffffu, acc.x, o);
-          acc.y = acc.y + __shfl_xor_sync(0xffffffffu, acc.y, o);
-          acc.z = acc.z + __shfl_xor_sync(0xffffffffu, acc.z, o);
-        } else {
-          acc.w = acc.w + df64(__shfl_xor_sync(0xffffffffu, acc.w.hi, o), __shfl_xor_sync(0xffffffffu, acc.w.lo, o));
-          acc.x = acc.x + df64(__shfl_xor_sync(0xffffffffu, acc.x.hi, o), __shfl_xor_sync(0xffffffffu, acc.x.lo, o));
-          acc.y = acc.y + df64(__shfl_xor_sync(0xffffffffu, acc.y.hi, o), __shfl_xor_sync(0xffffffffu, acc.y.lo, o));
-          acc.z = acc.z + df64(__shfl_xor_sync(0xffffffffu, acc.z.hi, o), __shfl_xor_sync(0xffffffffu, acc.z.lo, o));
-        }
-      }
-      if (active && part == 0) {
-        const R one = (i == j) ? R(1) : R(0);
-        row.set(j, qt_scale(QT<R>{one - acc.w, -acc.x, -acc.y, -acc.z}, inv));
-      }
-    }
-    __syncthreads();
-    for (int j = tid; j <= i; j += nt) L.set(tri(i, j), row[j]);
-    __syncthreads();
   }
   for (int e = tid; e < n * n; e += nt) {
     const int i = e / n, j = e % n;
@@ -367,15 +464,30 @@ __global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_
 }
 
 template <typename R>
-size_t smem_need(int n) {
-  return sizeof(QT<R>) * ((size_t)n * (n + 1) / 2 + 5 * (size_t)n) + 64;
+size_t smem_need(int n, bool cplx) {
+  return sizeof(R) * ((cplx ? 2 : 4) * (size_t)n * (n + 1) / 2 + 4 * 5 * (size_t)n) + 64;
+}
+
+template <typename R, bool C>
+cudaError_t launch_one(const double* G, int64_t ldg, int64_t psg, double* Li, int64_t ldl,
+                       int64_t psl, int n, int allow_shift, double shift_rows, int power_slot,
+                       double kappa_stop, int32_t* status, double* scalars, int fail_bits,
+                       double* Lout, cudaStream_t st) {
+  const size_t sm = smem_need<R>(n, C);
+  cudaError_t e = cudaFuncSetAttribute(qchol_inv_kernel<R, C>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  qchol_inv_kernel<R, C><<<1, 1024, sm, st>>>(G, ldg, psg, Li, ldl, psl, n, allow_shift, shift_rows,
+                                              power_slot, kappa_stop, status, scalars, fail_bits,
+                                              Lout);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 int qchol_inv_max_n() {
   int n = 1;
-  while (smem_need<double>(n + 1) <= 225 * 1024) ++n;
+  while (smem_need<double>(n + 1, false) <= 225 * 1024) ++n;
   return n;
 }
 
@@ -384,25 +496,22 @@ cudaError_t launch_qchol_inv(const double* G, int64_t ldg, int64_t psg, double* 
                              int power_slot, double kappa_stop, int use_df64, int32_t* status,
                              double* scalars, int fail_bits, double* Lout, cudaStream_t st) {
   if (n > qchol_inv_max_n()) return cudaErrorInvalidValue;
-  if (use_df64) {
-    const size_t sm = smem_need<df64>(n);
-    cudaError_t e = cudaFuncSetAttribute(qchol_inv_kernel<df64>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    qchol_inv_kernel<df64><<<1, 1024, sm, st>>>(G, ldg, psg, Li, ldl, psl, n, complex_only,
-                                                allow_shift, shift_rows, power_slot, kappa_stop,
-                                                status, scalars, fail_bits, Lout);
-  } else {
-    const size_t sm = smem_need<double>(n);
-    cudaError_t e = cudaFuncSetAttribute(qchol_inv_kernel<double>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    qchol_inv_kernel<double><<<1, 1024, sm, st>>>(G, ldg, psg, Li, ldl, psl, n, complex_only,
-                                                  allow_shift, shift_rows, power_slot, kappa_stop,
-                                                  status, scalars, fail_bits, Lout);
-  }
+  // the complex specialisation has no power iterates (they act on quaternion vectors)
+  if (complex_only && power_slot >= 0) return cudaErrorInvalidValue;
+  const bool cplx = complex_only != 0;
+  cudaError_t e;
+  if (use_df64)
+    e = cplx ? launch_one<df64, true>(G, ldg, psg, Li, ldl, psl, n, allow_shift, shift_rows, power_slot,
+                                      kappa_stop, status, scalars, fail_bits, Lout, st)
+             : launch_one<df64, false>(G, ldg, psg, Li, ldl, psl, n, allow_shift, shift_rows,
+                                       power_slot, kappa_stop, status, scalars, fail_bits, Lout, st);
+  else
+    e = cplx ? launch_one<double, true>(G, ldg, psg, Li, ldl, psl, n, allow_shift, shift_rows,
+                                        power_slot, kappa_stop, status, scalars, fail_bits, Lout, st)
+             : launch_one<double, false>(G, ldg, psg, Li, ldl, psl, n, allow_shift, shift_rows,
+                                         power_slot, kappa_stop, status, scalars, fail_bits, Lout, st);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace qs
