@@ -132,7 +132,9 @@ inline bool is_small(int64_t M, int64_t N) { return M <= 512 && N <= 512; }
 int pick_splits(int64_t M, int64_t N, int64_t K) {
   const int tile = is_small(M, N) ? 16 : 64;
   const int64_t tiles = ((M + tile - 1) / tile) * ((N + tile - 1) / tile);
-  int64_t sp = (2 * kNumSMs + tiles - 1) / tiles;
+  // the one-output-per-thread small kernel needs several CTAs per SM to hide its latency
+  const int64_t target = (is_small(M, N) ? 8 : 2) * kNumSMs;
+  int64_t sp = (target + tiles - 1) / tiles;
   sp = std::min<int64_t>(sp, std::max<int64_t>(1, K / (is_small(M, N) ? 16 : 32)));
   return (int)std::max<int64_t>(1, std::min<int64_t>(sp, 1024));
 }
@@ -141,7 +143,8 @@ int pick_splits(int64_t M, int64_t N, int64_t K) {
 // acc: 0 = FP32 (all operands FP32), 1 = FP64, 2 = double-float on the FP32 pipes.
 cudaError_t gemm(const Ctx& x, const Mat& A, bool conjA, const Mat& B, const Mat& C, int64_t M,
                  int64_t N, int64_t K, double alpha, double beta, int acc, bool allow_split,
-                 const double* gate = nullptr, double gate_skip = 0.0, int herm = 0) {
+                 const double* gate = nullptr, double gate_skip = 0.0, int herm = 0,
+                 int cplx_out = 0) {
   GemmDesc d{};
   d.M = M; d.N = N; d.K = K;
   A.cplanes(d.a); d.lda = A.ld; d.a_f64 = A.f64; d.conj_a = conjA;
@@ -151,7 +154,7 @@ cudaError_t gemm(const Ctx& x, const Mat& A, bool conjA, const Mat& B, const Mat
   d.small = is_small(M, N);
   d.splits = (allow_split || d.small) ? pick_splits(M, N, K) : 1;
   d.epi = 0; d.err = nullptr;
-  d.gate = gate; d.gate_skip = gate_skip; d.herm = herm;
+  d.gate = gate; d.gate_skip = gate_skip; d.herm = herm; d.cplx_out = cplx_out;
   if (d.splits > 1 && beta != 1.0) {
     cudaError_t e = launch_scale(C.p, C.f64, M, N, C.ld, C.ps, beta, x.st, gate, gate_skip);
     if (e != cudaSuccess) return e;
@@ -172,14 +175,16 @@ cudaError_t gemm_bcplx(const Ctx& x, const Mat& A, const Mat& B, const Mat& C, i
   return launch_qgemm(d, x.st);
 }
 
-// Gram G = A* A of a tall m x s matrix (FP64 result).
+// Gram G = A* A of a tall m x s matrix (FP64 result).  complex_part: only the complex part
+// (planes w, x) is formed, the y, z planes are zero -- what a Cholesky-QR of the compact
+// complex form A_c needs (A_c* A_c is the complex part of A* A).
 cudaError_t gram(const Ctx& x, const Mat& A, int64_t rows, int64_t cols, const Mat& G,
-               const double* gate = nullptr, double gate_skip = 0.0) {
+                 const double* gate = nullptr, double gate_skip = 0.0, bool complex_part = false) {
   if (!is_small(cols, cols))
     return gemm(x, A, true, A, G, cols, cols, rows, 1.0, 0.0, x.acc_hi(), true, gate, gate_skip);
   // Hermitian: tiles on and above the diagonal, then the mirror
   cudaError_t e = gemm(x, A, true, A, G, cols, cols, rows, 1.0, 0.0, x.acc_hi(), true, gate,
-                       gate_skip, /*herm=*/1);
+                       gate_skip, /*herm=*/1, complex_part ? 1 : 0);
   if (e != cudaSuccess) return e;
   return launch_qmirror((double*)G.p, G.ld, G.ps, (int)cols, x.st, gate, gate_skip);
 }
@@ -214,7 +219,7 @@ qs_status pseudo_qr(const Ctx& x, int ncorr) {
   int32_t* st = x.status();
   double* sc = x.scalars();
   // (Alg. 1 step 2) thin complex QR of Y_c by Cholesky-QR: Y_c* Y_c = L L*, R = L*.
-  QS_CU(gram(x, Y, x.m, s, G));
+  QS_CU(gram(x, Y, x.m, s, G, nullptr, 0.0, /*complex_part=*/true));
   QS_CU(chol_inv(x, G, L, Li, 1, 1, 2.0 * x.m, -1, kDevRank | kDevStopCorr));
   QS_CU(launch_qconjT(Li.p, 1, Li.ld, Li.ps, D.p, 1, D.ld, D.ps, s, s, x.st));   // D = R^{-1}
   // second Cholesky-QR pass on T = Y R^{-1} restores orthogonality of the Q factor; R^{-1}

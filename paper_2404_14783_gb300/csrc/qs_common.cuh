@@ -115,6 +115,7 @@ struct GemmDesc {
   double gate_skip;
   int herm;      // C = A* A is Hermitian: the small kernel computes only tiles on/above the
                  // diagonal (the caller mirrors the rest)
+  int cplx_out;  // small kernel with conj_a: form only the complex part (planes w, x) of C
 };
 // Plane pointers of a matrix with uniform plane stride.
 inline void planes_of(const void* base, int64_t ps, int esize, int64_t offset_elems,

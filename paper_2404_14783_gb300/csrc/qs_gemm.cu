@@ -205,7 +205,8 @@ __global__ void __launch_bounds__(256, sizeof(ACC) == 4 ? 2 : 1) qgemm_kernel(Ge
 
 // Small products (M, N <= 512, e.g. the s x s factors of the rangefinders): one quaternion
 // output per thread, 16 x 16 outputs per CTA, K staged 16 deep, split-K over grid z.
-template <typename ACC, typename TA, typename TB, typename TC, bool CONJ>
+// COUT: only the complex part (planes w, x) of C is formed; planes y, z are left zero.
+template <typename ACC, typename TA, typename TB, typename TC, bool CONJ, bool COUT = false>
 __global__ void __launch_bounds__(256) qgemm_small_kernel(GemmDesc g) {
   constexpr int T = 16, BK = 16;
   __shared__ ACC As[4][BK][T + 1];
@@ -245,9 +246,17 @@ __global__ void __launch_bounds__(256) qgemm_small_kernel(GemmDesc g) {
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < BK; ++kk)
-      qmac(cw, cx, cy, cz, As[0][kk][ty], As[1][kk][ty], As[2][kk][ty], As[3][kk][ty], Bs[0][kk][tx],
-           Bs[1][kk][tx], Bs[2][kk][tx], Bs[3][kk][tx]);
+    for (int kk = 0; kk < BK; ++kk) {
+      if (COUT) {  // (a b)_w and (a b)_x of the Hamilton product
+        const ACC aw = As[0][kk][ty], ax = As[1][kk][ty], ay = As[2][kk][ty], az = As[3][kk][ty];
+        const ACC bw = Bs[0][kk][tx], bx = Bs[1][kk][tx], by = Bs[2][kk][tx], bz = Bs[3][kk][tx];
+        cw = fma(aw, bw, fma(-ax, bx, fma(-ay, by, fma(-az, bz, cw))));
+        cx = fma(aw, bx, fma(ax, bw, fma(ay, bz, fma(-az, by, cx))));
+      } else {
+        qmac(cw, cx, cy, cz, As[0][kk][ty], As[1][kk][ty], As[2][kk][ty], As[3][kk][ty],
+             Bs[0][kk][tx], Bs[1][kk][tx], Bs[2][kk][tx], Bs[3][kk][tx]);
+      }
+    }
     __syncthreads();
   }
   const int64_t m = m0 + ty, n = n0 + tx;
@@ -257,6 +266,10 @@ __global__ void __launch_bounds__(256) qgemm_small_kernel(GemmDesc g) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     TC* dst = static_cast<TC*>(g.c[q]) + m * g.ldc + n;
+    if (COUT && q >= 2) {
+      if (g.splits == 1) *dst = TC(0);   // split-K: C was zeroed by the pre-scale
+      continue;
+    }
     if (g.splits > 1) atomicAdd(dst, static_cast<TC>(v[q]));
     else if (g.beta == 0.0) *dst = static_cast<TC>(v[q]);
     else *dst = static_cast<TC>(v[q] + ACC(g.beta) * ACC(*dst));
@@ -359,7 +372,9 @@ template <typename ACC, typename TA, typename TB, typename TC>
 cudaError_t launch_t(const GemmDesc& d, cudaStream_t st) {
   if (d.small && d.epi == 0) {
     dim3 grid((unsigned)((d.M + 15) / 16), (unsigned)((d.N + 15) / 16), (unsigned)d.splits);
-    if (d.conj_a)
+    if (d.conj_a && d.cplx_out)
+      qgemm_small_kernel<ACC, TA, TB, TC, true, true><<<grid, 256, 0, st>>>(d);
+    else if (d.conj_a)
       qgemm_small_kernel<ACC, TA, TB, TC, true><<<grid, 256, 0, st>>>(d);
     else
       qgemm_small_kernel<ACC, TA, TB, TC, false><<<grid, 256, 0, st>>>(d);
