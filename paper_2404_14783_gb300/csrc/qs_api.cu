@@ -201,7 +201,7 @@ cudaError_t chol_inv(const Ctx& x, const Mat& G, const Mat& L, const Mat& Li, in
   if (s <= qchol_inv_max_n())
     return launch_qchol_inv((const double*)G.p, G.ld, G.ps, (double*)Li.p, Li.ld, Li.ps, s,
                             complex_only, allow_shift, shift_rows, slot, kKappaStop, !x.f64, st, sc,
-                            fail_bits, want_L ? (double*)L.p : nullptr, x.st);
+                            fail_bits, (double*)L.p, x.st);
   cudaError_t e = launch_qchol((const double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s,
                                complex_only, allow_shift, shift_rows, st, sc, fail_bits, x.st);
   if (e == cudaSuccess && slot >= 0)

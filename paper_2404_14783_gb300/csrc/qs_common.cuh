@@ -29,6 +29,7 @@ enum {
   kScErrNum = 8,    // accumulator: ||A - HX||_F^2
   kScErrDen = 9,    // accumulator: ||A||_F^2
   kScGate = 10,     // 1: next Gram of the corrections by the s x s update, 0: explicit pass
+  kScCholOk = 11,   // internal: 1 when the last shared-memory Cholesky succeeded
   kScCount = 16
 };
 

@@ -23,12 +23,13 @@ cudaError_t launch_clear_stop(int32_t* status, cudaStream_t st);
 cudaError_t launch_qgram_update(const double* G, double* Gn, const double* Gi, int64_t ld,
                                 int64_t ps, int n, const double* scalars, int slot,
                                 cudaStream_t st);
-// Fused shared-memory Cholesky (+ optional power-iteration eps into scalars[power_slot] when
-// power_slot >= 0) and in-place inverse: writes L^{-1} (lower) to Li, and L to Lout when
-// Lout is not null (same leading dimension and plane stride).  n <= qchol_inv_max_n().
+// Shared-memory Cholesky G = L L* (writes L, lower, to Lg), L^{-1} to Li (several CTAs, one
+// warp per column) and, when power_slot >= 0, the power-iteration eps into
+// scalars[power_slot] (same leading dimension and plane stride for Lg and Li).
+// n <= qchol_inv_max_n().
 int qchol_inv_max_n();
 cudaError_t launch_qchol_inv(const double* G, int64_t ldg, int64_t psg, double* Li, int64_t ldl,
                              int64_t psl, int n, int complex_only, int allow_shift, double shift_rows,
                              int power_slot, double kappa_stop, int use_df64, int32_t* status,
-                             double* scalars, int fail_bits, double* Lout, cudaStream_t st);
+                             double* scalars, int fail_bits, double* Lg, cudaStream_t st);
 }  // namespace qs

@@ -1,15 +1,17 @@
 // Small factorisations held entirely in shared memory (s <= ~110 quaternion rows).
 //
-// qchol_inv: for a Hermitian positive definite quaternion G (s x s, FP64 in global memory)
+// qchol_inv (three launches: Cholesky, inverse by columns, power iterates): for a Hermitian
+// positive definite quaternion G (s x s, FP64 in global memory)
 //   1. G (+ shift on retry) = L L*, right-looking Cholesky in the quaternion (or, with
 //      complex_only, the complex) algebra; real positive diagonal.  This realises the thin
 //      complex QR of Alg. 1 step 2 through Cholesky-QR (R = L*), and the solves with
 //      chi_{H*H} of the correction step (Alg. 1 step 4).  On breakdown one retry with the
 //      shifted Cholesky-QR shift 11 (rows*s + s(s+1)) u trace(G) (Fukaya et al. 2020).
-//   2. optionally the correction parameter eps ~ sigma_s(H) from three power iterates on
+//   2. L^{-1} column by column (one warp per column, several CTAs), written to global memory
+//      as a full s x s matrix.
+//   3. optionally the correction parameter eps ~ sigma_s(H) from three power iterates on
 //      G^{-1} = L^{-*} L^{-1} (Sec. 3.1), and a kappa(H) estimate; kappa beyond the range of
 //      use of the correction (1e8) stops the corrections (rank warning).
-//   3. L^{-1} in place (row by row), written to global memory as a full s x s matrix.
 // Arithmetic type R: double (FP64 mode) or df64 (double-float on the FP32 pipes).
 #include <algorithm>
 #include <cmath>
@@ -207,39 +209,44 @@ __device__ __forceinline__ QT<R> gsum8q(QT<R> v) {
   return QT<R>{gsum8(v.w), gsum8(v.x), gsum8(v.y), gsum8(v.z)};
 }
 
+// ---------------------------------------------------------------- K1: Cholesky
+// G (+ shift on retry) = L L*, right-looking with one barrier per column: in the pass of
+// column j every thread reads the pivot d_j, and the threads share, flat, the trailing update
+// L_ik -= L_ij conj(L_kj) / d_j (j < k <= i) together with the scaling of column j - 1 by
+// 1/sqrt(d_{j-1}), which no thread of this pass reads.  Writes L (lower, zero above) and
+// scalars[kScCholOk] = 1; on breakdown (or when the corrections are already stopped) writes
+// Li = I, scalars[power_slot] = 0 and scalars[kScCholOk] = 0, which the inverse and power
+// kernels of the same factorisation read as "skip".
 template <typename R, bool C>
-__global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_t ldg, int64_t psg,
-                                                         double* Li, int64_t ldl, int64_t psl, int n,
-                                                         int allow_shift, double shift_rows,
-                                                         int power_slot, double kappa_stop,
-                                                         int32_t* status, double* scalars,
-                                                         int fail_bits, double* Lout) {
+__global__ void __launch_bounds__(1024) qchol_kernel(const double* G, int64_t ldg, int64_t psg,
+                                                     double* Lg, double* Li, int64_t ldl, int64_t psl,
+                                                     int n, int allow_shift, double shift_rows,
+                                                     int power_slot, int32_t* status, double* scalars,
+                                                     int fail_bits) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  constexpr int NC = C ? 2 : 4;
   const int ntri = n * (n + 1) / 2;
-  R* sbase = reinterpret_cast<R*>(smem_raw);
-  const QS<R, C> L = QS<R, C>::make(sbase, ntri);                 // packed lower triangle
-  const QS<R, false> row = QS<R, false>::make(sbase + NC * ntri, n);      // scratch row
-  const QS<R, false> vec = QS<R, false>::make(sbase + NC * ntri + 4 * n, 4 * n);  // power vectors
-  __shared__ double red[2][32];
+  const QS<R, C> L = QS<R, C>::make(reinterpret_cast<R*>(smem_raw), ntri);   // packed lower triangle
+  __shared__ double red[32];
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
   auto gget = [&](int i, int j, int p) { return G[p * psg + (int64_t)i * ldg + j]; };
-  auto write_identity = [&]() {
+  auto give_up = [&]() {   // L = L^{-1} = I
     for (int e = tid; e < n * n; e += nt) {
       const int i = e / n, j = e % n;
-      for (int p = 0; p < 4; ++p) Li[p * psl + (int64_t)i * ldl + j] = (p == 0 && i == j) ? 1.0 : 0.0;
+      for (int p = 0; p < 4; ++p) {
+        const double v = (p == 0 && i == j) ? 1.0 : 0.0;
+        Li[p * psl + (int64_t)i * ldl + j] = v;
+        Lg[p * psl + (int64_t)i * ldl + j] = v;
+      }
     }
-    if (tid == 0 && power_slot >= 0) scalars[power_slot] = 0.0;
+    if (tid == 0) {
+      if (power_slot >= 0) scalars[power_slot] = 0.0;
+      scalars[kScCholOk] = 0.0;
+    }
   };
   if (status[0] & kDevStopCorr) {
-    write_identity();
+    give_up();
     return;
   }
-  // ---------------------------------------------------------------- Cholesky G (+ shift) = L L*
-  // Right-looking, one barrier per column: in the pass of column j every thread reads the
-  // pivot d_j, and the threads share, flat, the trailing update L_ik -= L_ij conj(L_kj) / d_j
-  // (j < k <= i) together with the scaling of column j - 1 by 1/sqrt(d_{j-1}), which no
-  // thread of this pass reads.
   double shift = 0.0;
   bool fail = false;
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -290,10 +297,10 @@ __global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_
       for (int i = tid; i < n; i += nt) tr += gget(i, i, 0);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-      if (lane == 0) red[0][warp] = tr;
+      if (lane == 0) red[warp] = tr;
       __syncthreads();
       double t = 0.0;
-      for (int w = 0; w < nw; ++w) t += red[0][w];
+      for (int w = 0; w < nw; ++w) t += red[w];
       shift = 11.0 * (shift_rows * n + (double)n * (n + 1)) * 1.1102230246251565e-16 * t;
       if (tid == 0) {
         scalars[kScShift] = shift;
@@ -306,212 +313,278 @@ __global__ void __launch_bounds__(1024) qchol_inv_kernel(const double* G, int64_
   }
   if (fail) {
     if (tid == 0) atomicOr(status, fail_bits);
-    __syncthreads();
-    write_identity();
+    give_up();
     return;
-  }
-  if (Lout) {  // the factor itself (lower, zero above the diagonal), same layout as Li
-    for (int e = tid; e < n * n; e += nt) {
-      const int i = e / n, j = e % n;
-      QT<R> v{R(0), R(0), R(0), R(0)};
-      if (j <= i) v = L[tri(i, j)];
-      Lout[0 * psl + (int64_t)i * ldl + j] = to_d(v.w);
-      Lout[1 * psl + (int64_t)i * ldl + j] = to_d(v.x);
-      Lout[2 * psl + (int64_t)i * ldl + j] = to_d(v.y);
-      Lout[3 * psl + (int64_t)i * ldl + j] = to_d(v.z);
-    }
-  }
-  // ---------------------------------------------------------------- L^{-1} in place
-  // row i of X = L^{-1}: X_ij = (delta_ij - sum_{j<=k<i} L_ik X_kj) / L_ii, rows k < i already X;
-  // 8 lanes share each output
-  constexpr int P = 8;
-  for (int i = 0; i < n; ++i) {
-    const R inv = rcp_(L[tri(i, i)].w);
-    const int work = (i + 1) * P, work_r = (work + 31) & ~31;
-    for (int t = tid; t < work_r; t += nt) {
-      const int j = t / P, part = t % P;
-      const bool active = t < work;
-      QT<R> acc{R(0), R(0), R(0), R(0)};
-      if (active)
-        for (int k = j + part; k < i; k += P) acc = qmac<R, C>(acc, L[tri(i, k)], L[tri(k, j)]);
-      acc.w = gsum8(acc.w);
-      acc.x = gsum8(acc.x);
-      if (!C) {
-        acc.y = gsum8(acc.y);
-        acc.z = gsum8(acc.z);
-      }
-      if (active && part == 0) {
-        const R one = (i == j) ? R(1) : R(0);
-        row.set(j, qscale<R, C>(QT<R>{one - acc.w, -acc.x, -acc.y, -acc.z}, inv));
-      }
-    }
-    __syncthreads();
-    for (int j = tid; j <= i; j += nt) L.set(tri(i, j), row[j]);
-    __syncthreads();
-  }
-  // ---------------------------------------------------------------- power iterates (Sec. 3.1)
-  // eps: rho = x* G^{-1} x = ||L^{-1} x||^2 on the iterates x <- G^{-1} x / |G^{-1} x| from
-  // (c, 0, -c, 0), eps = 1 / sqrt(rho); lambda_max(G) from iterates z <- G z / |G z| on G
-  // itself; kappa(H) = sqrt(lambda_max(G) rho).  Each output of a matrix-vector product is a
-  // dot product shared by 8 lanes.
-  if (power_slot >= 0 && !C) {
-    const int X0 = 0, Y0 = n, Z0 = 2 * n, U0 = 3 * n;   // x, y = L^{-1} x, z, u = G z in vec
-    const double c0 = 1.0 / sqrt(2.0 * n);
-    for (int i = tid; i < n; i += nt) {
-      vec.set(X0 + i, QT<R>{from_d<R>(c0), R(0), from_d<R>(-c0), R(0)});
-      vec.set(Z0 + i, QT<R>{from_d<R>(c0), R(0), from_d<R>(-c0), R(0)});
-    }
-    __syncthreads();
-    double rho = 0.0, lam = 0.0;
-    const int grp = tid / P, part = tid % P, ngrp = nt / P;
-    for (int it = 0; it < 3; ++it) {
-      // y = L^{-1} x (lower) and u = G z
-      for (int ob = 0; ob < 2 * n; ob += ngrp) {   // trip count uniform over the block
-        const int o = ob + grp;
-        QT<R> acc{R(0), R(0), R(0), R(0)};
-        if (o < n) {
-          for (int k = part; k <= o; k += P) acc = qt_mac(acc, L[tri(o, k)], vec[X0 + k]);
-        } else if (o < 2 * n) {
-          const int i = o - n;
-          for (int k = part; k < n; k += P) {
-            const QT<R> g{from_d<R>(gget(i, k, 0)), from_d<R>(gget(i, k, 1)), from_d<R>(gget(i, k, 2)),
-                          from_d<R>(gget(i, k, 3))};
-            acc = qt_mac(acc, g, vec[Z0 + k]);
-          }
-        }
-        acc = gsum8q(acc);
-        if (part == 0 && o < 2 * n) vec.set((o < n ? Y0 : U0 - n) + o, acc);
-      }
-      __syncthreads();
-      // x <- L^{-*} y normalised (into the row scratch first), z <- u / |u|
-      for (int kb = 0; kb < n; kb += ngrp) {
-        const int k = kb + grp;
-        QT<R> acc{R(0), R(0), R(0), R(0)};
-        if (k < n)
-          for (int i = k + part; i < n; i += P) acc = qt_mac_conj_a(acc, L[tri(i, k)], vec[Y0 + i]);
-        acc = gsum8q(acc);
-        if (part == 0 && k < n) row.set(k, acc);
-      }
-      if (warp == nw - 1) {  // |y|^2 = rho, z* u = lambda, |u|^2
-        double sy = 0.0, zu = 0.0, su = 0.0;
-        for (int i = lane; i < n; i += 32) {
-          const QT<R> yv = vec[Y0 + i], zv = vec[Z0 + i], uv = vec[U0 + i];
-          sy += to_d(yv.w) * to_d(yv.w) + to_d(yv.x) * to_d(yv.x) + to_d(yv.y) * to_d(yv.y) + to_d(yv.z) * to_d(yv.z);
-          zu += to_d(zv.w) * to_d(uv.w) + to_d(zv.x) * to_d(uv.x) + to_d(zv.y) * to_d(uv.y) + to_d(zv.z) * to_d(uv.z);
-          su += to_d(uv.w) * to_d(uv.w) + to_d(uv.x) * to_d(uv.x) + to_d(uv.y) * to_d(uv.y) + to_d(uv.z) * to_d(uv.z);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          sy += __shfl_xor_sync(0xffffffffu, sy, o);
-          zu += __shfl_xor_sync(0xffffffffu, zu, o);
-          su += __shfl_xor_sync(0xffffffffu, su, o);
-        }
-        if (lane == 0) { red[0][0] = sy; red[0][1] = zu; red[0][2] = su; }
-      }
-      __syncthreads();
-      rho = red[0][0];
-      lam = red[0][1];
-      const double su = red[0][2];
-      if (warp == 0) {  // |L^{-*} y|^2
-        double sv = 0.0;
-        for (int i = lane; i < n; i += 32) {
-          const QT<R> v = row[i];
-          sv += to_d(v.w) * to_d(v.w) + to_d(v.x) * to_d(v.x) + to_d(v.y) * to_d(v.y) + to_d(v.z) * to_d(v.z);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-        if (lane == 0) red[1][0] = sv;
-      }
-      __syncthreads();
-      const R inv_v = from_d<R>(red[1][0] > 0.0 ? 1.0 / sqrt(red[1][0]) : 0.0);
-      const R inv_u = from_d<R>(su > 0.0 ? 1.0 / sqrt(su) : 0.0);
-      for (int i = tid; i < n; i += nt) {
-        vec.set(X0 + i, qt_scale(row[i], inv_v));
-        vec.set(Z0 + i, qt_scale(vec[U0 + i], inv_u));
-      }
-      __syncthreads();
-    }
-    if (tid == 0) {
-      const double r = rho, lm = lam;
-      if (!(r > 0.0) || !isfinite(r)) {
-        scalars[power_slot] = 0.0;
-        atomicOr(status, kDevRank | kDevStopCorr);
-      } else {
-        const double kap = sqrt(fmax(lm, 0.0) * r);
-        scalars[kScKappa] = kap;
-        if (kap > kappa_stop) {
-          scalars[power_slot] = 0.0;
-          atomicOr(status, kDevRank | kDevStopCorr);
-        } else {
-          scalars[power_slot] = 1.0 / sqrt(r);
-        }
-        // The next Gram H_{k+1}* H_{k+1} may be formed in s x s space when its rounding error
-        // (u kappa^2 relative) stays far below its smallest eigenvalue (~4/kappa): u kappa^3 < 0.04.
-        const double u = std::is_same<R, double>::value ? 1.1102230246251565e-16 : 3.552713678800501e-15;
-        scalars[kScGate] = (u * kap * kap * kap < 0.04) ? 1.0 : 0.0;
-      }
-    }
   }
   for (int e = tid; e < n * n; e += nt) {
     const int i = e / n, j = e % n;
     QT<R> v{R(0), R(0), R(0), R(0)};
     if (j <= i) v = L[tri(i, j)];
-    Li[0 * psl + (int64_t)i * ldl + j] = to_d(v.w);
-    Li[1 * psl + (int64_t)i * ldl + j] = to_d(v.x);
-    Li[2 * psl + (int64_t)i * ldl + j] = to_d(v.y);
-    Li[3 * psl + (int64_t)i * ldl + j] = to_d(v.z);
+    Lg[0 * psl + (int64_t)i * ldl + j] = to_d(v.w);
+    Lg[1 * psl + (int64_t)i * ldl + j] = to_d(v.x);
+    Lg[2 * psl + (int64_t)i * ldl + j] = to_d(v.y);
+    Lg[3 * psl + (int64_t)i * ldl + j] = to_d(v.z);
+  }
+  if (tid == 0) scalars[kScCholOk] = 1.0;
+}
+
+// ---------------------------------------------------------------- K2: L^{-1} by columns
+// Column c of X = L^{-1} solves L x = e_c by forward substitution,
+//     X_ic = (delta_ic - sum_{c<=k<i} L_ik X_kc) / L_ii,
+// independently of the other columns: one warp per column, kCB columns per CTA.  The CTA
+// stages the trailing triangle of L it needs (rows and columns >= its first column) in
+// shared memory; a warp keeps its column of X in registers (lane t holds rows c0 + t + 32 u)
+// and needs no barrier with the other warps.  n <= 128.
+constexpr int kCB = 8;
+template <typename R, bool C>
+__global__ void __launch_bounds__(32 * kCB) qtrinv_cols_kernel(const double* Lg, double* Li, int64_t ldl,
+                                                                int64_t psl, int n,
+                                                                const double* scalars) {
+  if (scalars[kScCholOk] != 1.0) return;
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int c0 = blockIdx.x * kCB, nn = n - c0;
+  const int ntri = nn * (nn + 1) / 2;
+  const QS<R, C> L = QS<R, C>::make(reinterpret_cast<R*>(smem_raw), ntri);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  auto lget = [&](int i, int k, int p) { return Lg[p * psl + (int64_t)i * ldl + k]; };
+  for (int e = tid; e < ntri; e += blockDim.x) {
+    int ii, kk;
+    tri_rc(e, ii, kk);
+    const int i = c0 + ii, k = c0 + kk;
+    L.set(e, QT<R>{from_d<R>(lget(i, k, 0)), from_d<R>(lget(i, k, 1)),
+                   C ? R(0) : from_d<R>(lget(i, k, 2)), C ? R(0) : from_d<R>(lget(i, k, 3))});
+  }
+  __syncthreads();
+  const int c = c0 + warp;
+  if (c >= n) return;
+  QT<R> xs[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) xs[u] = QT<R>{R(0), R(0), R(0), R(0)};
+  for (int i = c; i < n; ++i) {
+    const int li = i - c0;
+    QT<R> acc{R(0), R(0), R(0), R(0)};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int lk = lane + 32 * u, k = c0 + lk;
+      if (k >= c && k < i) acc = qmac<R, C>(acc, L[tri(li, lk)], xs[u]);
+    }
+    acc.w = wsum(acc.w);
+    acc.x = wsum(acc.x);
+    if (!C) {
+      acc.y = wsum(acc.y);
+      acc.z = wsum(acc.z);
+    }
+    const R inv = rcp_(L[tri(li, li)].w);
+    const R one = (i == c) ? R(1) : R(0);
+    const QT<R> xi = qscale<R, C>(QT<R>{one - acc.w, -acc.x, -acc.y, -acc.z}, inv);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (lane + 32 * u == li) xs[u] = QT<R>{nrm_(xi.w), nrm_(xi.x), nrm_(xi.y), nrm_(xi.z)};
+  }
+  // column c of Li: rows < c are zero
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = c0 + lane + 32 * u;
+    if (i < n) {
+      const QT<R> v = i >= c ? xs[u] : QT<R>{R(0), R(0), R(0), R(0)};
+      Li[0 * psl + (int64_t)i * ldl + c] = to_d(v.w);
+      Li[1 * psl + (int64_t)i * ldl + c] = to_d(v.x);
+      Li[2 * psl + (int64_t)i * ldl + c] = to_d(v.y);
+      Li[3 * psl + (int64_t)i * ldl + c] = to_d(v.z);
+    }
+  }
+  for (int i = lane; i < c0; i += 32) {   // rows above the CTA's first column
+    for (int p = 0; p < 4; ++p) Li[p * psl + (int64_t)i * ldl + c] = 0.0;
   }
 }
 
+// ---------------------------------------------------------------- K3: power iterates (Sec. 3.1)
+// eps: rho = x* G^{-1} x = ||L^{-1} x||^2 on the iterates x <- G^{-1} x / |G^{-1} x| from
+// (c, 0, -c, 0), eps = 1 / sqrt(rho); lambda_max(G) from iterates z <- G z / |G z| on G
+// itself; kappa(H) = sqrt(lambda_max(G) rho).  Each output of a matrix-vector product is a
+// dot product shared by 8 lanes.
 template <typename R>
-size_t smem_need(int n, bool cplx) {
-  return sizeof(R) * ((cplx ? 2 : 4) * (size_t)n * (n + 1) / 2 + 4 * 5 * (size_t)n) + 64;
+__global__ void __launch_bounds__(1024) qpower_kernel(const double* G, int64_t ldg, int64_t psg,
+                                                      const double* Li, int64_t ldl, int64_t psl,
+                                                      int n, int power_slot, double kappa_stop,
+                                                      int32_t* status, double* scalars) {
+  if (scalars[kScCholOk] != 1.0) return;
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int ntri = n * (n + 1) / 2;
+  R* sbase = reinterpret_cast<R*>(smem_raw);
+  const QS<R, false> L = QS<R, false>::make(sbase, ntri);                   // L^{-1}, lower
+  const QS<R, false> row = QS<R, false>::make(sbase + 4 * ntri, n);
+  const QS<R, false> vec = QS<R, false>::make(sbase + 4 * ntri + 4 * n, 4 * n);
+  __shared__ double red[2][4];
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  auto gget = [&](int i, int j, int p) { return G[p * psg + (int64_t)i * ldg + j]; };
+  for (int e = tid; e < ntri; e += nt) {
+    int i, j;
+    tri_rc(e, i, j);
+    L.set(e, QT<R>{from_d<R>(Li[(int64_t)i * ldl + j]), from_d<R>(Li[psl + (int64_t)i * ldl + j]),
+                   from_d<R>(Li[2 * psl + (int64_t)i * ldl + j]), from_d<R>(Li[3 * psl + (int64_t)i * ldl + j])});
+  }
+  constexpr int P = 8;
+  const int X0 = 0, Y0 = n, Z0 = 2 * n, U0 = 3 * n;   // x, y = L^{-1} x, z, u = G z in vec
+  const double c0 = 1.0 / sqrt(2.0 * n);
+  for (int i = tid; i < n; i += nt) {
+    vec.set(X0 + i, QT<R>{from_d<R>(c0), R(0), from_d<R>(-c0), R(0)});
+    vec.set(Z0 + i, QT<R>{from_d<R>(c0), R(0), from_d<R>(-c0), R(0)});
+  }
+  __syncthreads();
+  double rho = 0.0, lam = 0.0;
+  const int grp = tid / P, part = tid % P, ngrp = nt / P;
+  for (int it = 0; it < 3; ++it) {
+    // y = L^{-1} x (lower) and u = G z
+    for (int ob = 0; ob < 2 * n; ob += ngrp) {   // trip count uniform over the block
+      const int o = ob + grp;
+      QT<R> acc{R(0), R(0), R(0), R(0)};
+      if (o < n) {
+        for (int k = part; k <= o; k += P) acc = qt_mac(acc, L[tri(o, k)], vec[X0 + k]);
+      } else if (o < 2 * n) {
+        const int i = o - n;
+        for (int k = part; k < n; k += P) {
+          const QT<R> g{from_d<R>(gget(i, k, 0)), from_d<R>(gget(i, k, 1)), from_d<R>(gget(i, k, 2)),
+                        from_d<R>(gget(i, k, 3))};
+          acc = qt_mac(acc, g, vec[Z0 + k]);
+        }
+      }
+      acc = gsum8q(acc);
+      if (part == 0 && o < 2 * n) vec.set((o < n ? Y0 : U0 - n) + o, acc);
+    }
+    __syncthreads();
+    // x <- L^{-*} y (into the row scratch first); |y|^2 = rho, z* u = lambda, |u|^2
+    for (int kb = 0; kb < n; kb += ngrp) {
+      const int k = kb + grp;
+      QT<R> acc{R(0), R(0), R(0), R(0)};
+      if (k < n)
+        for (int i = k + part; i < n; i += P) acc = qt_mac_conj_a(acc, L[tri(i, k)], vec[Y0 + i]);
+      acc = gsum8q(acc);
+      if (part == 0 && k < n) row.set(k, acc);
+    }
+    if (warp == nw - 1) {
+      double sy = 0.0, zu = 0.0, su = 0.0;
+      for (int i = lane; i < n; i += 32) {
+        const QT<R> yv = vec[Y0 + i], zv = vec[Z0 + i], uv = vec[U0 + i];
+        sy += to_d(yv.w) * to_d(yv.w) + to_d(yv.x) * to_d(yv.x) + to_d(yv.y) * to_d(yv.y) + to_d(yv.z) * to_d(yv.z);
+        zu += to_d(zv.w) * to_d(uv.w) + to_d(zv.x) * to_d(uv.x) + to_d(zv.y) * to_d(uv.y) + to_d(zv.z) * to_d(uv.z);
+        su += to_d(uv.w) * to_d(uv.w) + to_d(uv.x) * to_d(uv.x) + to_d(uv.y) * to_d(uv.y) + to_d(uv.z) * to_d(uv.z);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        zu += __shfl_xor_sync(0xffffffffu, zu, o);
+        su += __shfl_xor_sync(0xffffffffu, su, o);
+      }
+      if (lane == 0) { red[0][0] = sy; red[0][1] = zu; red[0][2] = su; }
+    }
+    __syncthreads();
+    rho = red[0][0];
+    lam = red[0][1];
+    const double su = red[0][2];
+    if (warp == 0) {  // |L^{-*} y|^2
+      double sv = 0.0;
+      for (int i = lane; i < n; i += 32) {
+        const QT<R> v = row[i];
+        sv += to_d(v.w) * to_d(v.w) + to_d(v.x) * to_d(v.x) + to_d(v.y) * to_d(v.y) + to_d(v.z) * to_d(v.z);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+      if (lane == 0) red[1][0] = sv;
+    }
+    __syncthreads();
+    const R inv_v = from_d<R>(red[1][0] > 0.0 ? 1.0 / sqrt(red[1][0]) : 0.0);
+    const R inv_u = from_d<R>(su > 0.0 ? 1.0 / sqrt(su) : 0.0);
+    for (int i = tid; i < n; i += nt) {
+      vec.set(X0 + i, qt_scale(row[i], inv_v));
+      vec.set(Z0 + i, qt_scale(vec[U0 + i], inv_u));
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double r = rho, lm = lam;
+    if (!(r > 0.0) || !isfinite(r)) {
+      scalars[power_slot] = 0.0;
+      atomicOr(status, kDevRank | kDevStopCorr);
+    } else {
+      const double kap = sqrt(fmax(lm, 0.0) * r);
+      scalars[kScKappa] = kap;
+      if (kap > kappa_stop) {
+        scalars[power_slot] = 0.0;
+        atomicOr(status, kDevRank | kDevStopCorr);
+      } else {
+        scalars[power_slot] = 1.0 / sqrt(r);
+      }
+      // The next Gram H_{k+1}* H_{k+1} may be formed in s x s space when its rounding error
+      // (u kappa^2 relative) stays far below its smallest eigenvalue (~4/kappa): u kappa^3 < 0.04.
+      const double u = std::is_same<R, double>::value ? 1.1102230246251565e-16 : 3.552713678800501e-15;
+      scalars[kScGate] = (u * kap * kap * kap < 0.04) ? 1.0 : 0.0;
+    }
+  }
+}
+
+size_t smem_chol(int n, size_t rsize, bool cplx) {
+  return rsize * (cplx ? 2 : 4) * ((size_t)n * (n + 1) / 2) + 64;
+}
+size_t smem_power(int n, size_t rsize) {
+  return rsize * (4 * ((size_t)n * (n + 1) / 2) + 20 * (size_t)n) + 64;
 }
 
 template <typename R, bool C>
-cudaError_t launch_one(const double* G, int64_t ldg, int64_t psg, double* Li, int64_t ldl,
+cudaError_t launch_all(const double* G, int64_t ldg, int64_t psg, double* Lg, double* Li, int64_t ldl,
                        int64_t psl, int n, int allow_shift, double shift_rows, int power_slot,
                        double kappa_stop, int32_t* status, double* scalars, int fail_bits,
-                       double* Lout, cudaStream_t st) {
-  const size_t sm = smem_need<R>(n, C);
-  cudaError_t e = cudaFuncSetAttribute(qchol_inv_kernel<R, C>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                       cudaStream_t st) {
+  const size_t s1 = smem_chol(n, sizeof(R), C);
+  cudaError_t e = cudaFuncSetAttribute(qchol_kernel<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
   if (e != cudaSuccess) return e;
-  qchol_inv_kernel<R, C><<<1, 1024, sm, st>>>(G, ldg, psg, Li, ldl, psl, n, allow_shift, shift_rows,
-                                              power_slot, kappa_stop, status, scalars, fail_bits,
-                                              Lout);
-  return cudaGetLastError();
+  qchol_kernel<R, C><<<1, 1024, s1, st>>>(G, ldg, psg, Lg, Li, ldl, psl, n, allow_shift, shift_rows,
+                                          power_slot, status, scalars, fail_bits);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t s2 = smem_chol(n, sizeof(R), C);
+  e = cudaFuncSetAttribute(qtrinv_cols_kernel<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
+  if (e != cudaSuccess) return e;
+  qtrinv_cols_kernel<R, C><<<(n + kCB - 1) / kCB, 32 * kCB, s2, st>>>(Lg, Li, ldl, psl, n, scalars);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (power_slot >= 0 && !C) {
+    const size_t s3 = smem_power(n, sizeof(R));
+    e = cudaFuncSetAttribute(qpower_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3);
+    if (e != cudaSuccess) return e;
+    qpower_kernel<R><<<1, 1024, s3, st>>>(G, ldg, psg, Li, ldl, psl, n, power_slot, kappa_stop,
+                                         status, scalars);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace
 
 int qchol_inv_max_n() {
   int n = 1;
-  while (smem_need<double>(n + 1, false) <= 225 * 1024) ++n;
+  while (n + 1 <= 128 && smem_power(n + 1, sizeof(double)) <= 225 * 1024) ++n;
   return n;
 }
 
 cudaError_t launch_qchol_inv(const double* G, int64_t ldg, int64_t psg, double* Li, int64_t ldl,
                              int64_t psl, int n, int complex_only, int allow_shift, double shift_rows,
                              int power_slot, double kappa_stop, int use_df64, int32_t* status,
-                             double* scalars, int fail_bits, double* Lout, cudaStream_t st) {
-  if (n > qchol_inv_max_n()) return cudaErrorInvalidValue;
-  // the complex specialisation has no power iterates (they act on quaternion vectors)
+                             double* scalars, int fail_bits, double* Lg, cudaStream_t st) {
+  if (n > qchol_inv_max_n() || !Lg) return cudaErrorInvalidValue;
   if (complex_only && power_slot >= 0) return cudaErrorInvalidValue;
-  const bool cplx = complex_only != 0;
-  cudaError_t e;
   if (use_df64)
-    e = cplx ? launch_one<df64, true>(G, ldg, psg, Li, ldl, psl, n, allow_shift, shift_rows, power_slot,
-                                      kappa_stop, status, scalars, fail_bits, Lout, st)
-             : launch_one<df64, false>(G, ldg, psg, Li, ldl, psl, n, allow_shift, shift_rows,
-                                       power_slot, kappa_stop, status, scalars, fail_bits, Lout, st);
-  else
-    e = cplx ? launch_one<double, true>(G, ldg, psg, Li, ldl, psl, n, allow_shift, shift_rows,
-                                        power_slot, kappa_stop, status, scalars, fail_bits, Lout, st)
-             : launch_one<double, false>(G, ldg, psg, Li, ldl, psl, n, allow_shift, shift_rows,
-                                         power_slot, kappa_stop, status, scalars, fail_bits, Lout, st);
-  count_launch();
-  return e;
+    return complex_only
+               ? launch_all<df64, true>(G, ldg, psg, Lg, Li, ldl, psl, n, allow_shift, shift_rows,
+                                        power_slot, kappa_stop, status, scalars, fail_bits, st)
+               : launch_all<df64, false>(G, ldg, psg, Lg, Li, ldl, psl, n, allow_shift, shift_rows,
+                                         power_slot, kappa_stop, status, scalars, fail_bits, st);
+  return complex_only
+             ? launch_all<double, true>(G, ldg, psg, Lg, Li, ldl, psl, n, allow_shift, shift_rows,
+                                        power_slot, kappa_stop, status, scalars, fail_bits, st)
+             : launch_all<double, false>(G, ldg, psg, Lg, Li, ldl, psl, n, allow_shift, shift_rows,
+                                         power_slot, kappa_stop, status, scalars, fail_bits, st);
 }
 
 }  // namespace qs
