@@ -30,6 +30,7 @@ enum {
   kScErrDen = 9,    // accumulator: ||A||_F^2
   kScGate = 10,     // 1: next Gram of the corrections by the s x s update, 0: explicit pass
   kScCholOk = 11,   // internal: 1 when the last shared-memory Cholesky succeeded
+  kScLamMax = 12,   // internal: lambda_max(G) estimate of the last factorised Gram
   kScCount = 16
 };
 

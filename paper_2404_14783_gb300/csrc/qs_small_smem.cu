@@ -326,16 +326,82 @@ __global__ void __launch_bounds__(1024) qchol_kernel(const double* G, int64_t ld
     Lg[3 * psl + (int64_t)i * ldl + j] = to_d(v.z);
   }
   if (tid == 0) scalars[kScCholOk] = 1.0;
+  if constexpr (!C) {
+    if (power_slot >= 0) {
+      // lambda_max(G) for the kappa estimate: iterates z <- L (L* z) / |.| from (c, 0, -c, 0),
+      // lambda = z* G z = |L* z|^2 at the last iterate
+      const QS<R, false> z = QS<R, false>::make(reinterpret_cast<R*>(smem_raw) + 4 * ntri, n);
+      const QS<R, false> t = QS<R, false>::make(reinterpret_cast<R*>(smem_raw) + 4 * ntri + 4 * n, n);
+      const QS<R, false> u = QS<R, false>::make(reinterpret_cast<R*>(smem_raw) + 4 * ntri + 8 * n, n);
+      const double c0 = 1.0 / sqrt(2.0 * n);
+      for (int i = tid; i < n; i += nt) z.set(i, QT<R>{from_d<R>(c0), R(0), from_d<R>(-c0), R(0)});
+      __syncthreads();
+      constexpr int P = 8;
+      const int grp = tid / P, part = tid % P, ngrp = nt / P;
+      double lam = 0.0;
+      for (int it = 0; it < 3; ++it) {
+        for (int kb = 0; kb < n; kb += ngrp) {   // t = L* z
+          const int k = kb + grp;
+          QT<R> acc{R(0), R(0), R(0), R(0)};
+          if (k < n)
+            for (int i = k + part; i < n; i += P) acc = qt_mac_conj_a(acc, L[tri(i, k)], z[i]);
+          acc = gsum8q(acc);
+          if (part == 0 && k < n) t.set(k, acc);
+        }
+        __syncthreads();
+        for (int ib = 0; ib < n; ib += ngrp) {   // u = L t
+          const int i = ib + grp;
+          QT<R> acc{R(0), R(0), R(0), R(0)};
+          if (i < n)
+            for (int k = part; k <= i; k += P) acc = qt_mac(acc, L[tri(i, k)], t[k]);
+          acc = gsum8q(acc);
+          if (part == 0 && i < n) u.set(i, acc);
+        }
+        if (warp == 0) {   // lambda = |t|^2 = z* G z
+          double st = 0.0;
+          for (int i = lane; i < n; i += 32) {
+            const QT<R> v = t[i];
+            st += to_d(v.w) * to_d(v.w) + to_d(v.x) * to_d(v.x) + to_d(v.y) * to_d(v.y) + to_d(v.z) * to_d(v.z);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) st += __shfl_xor_sync(0xffffffffu, st, o);
+          if (lane == 0) red[0] = st;
+        }
+        __syncthreads();
+        lam = red[0];
+        if (warp == 1) {
+          double su = 0.0;
+          for (int i = lane; i < n; i += 32) {
+            const QT<R> v = u[i];
+            su += to_d(v.w) * to_d(v.w) + to_d(v.x) * to_d(v.x) + to_d(v.y) * to_d(v.y) + to_d(v.z) * to_d(v.z);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) su += __shfl_xor_sync(0xffffffffu, su, o);
+          if (lane == 0) red[1] = su;
+        }
+        __syncthreads();
+        const R inv_u = from_d<R>(red[1] > 0.0 ? 1.0 / sqrt(red[1]) : 0.0);
+        for (int i = tid; i < n; i += nt) z.set(i, qt_scale(u[i], inv_u));
+        __syncthreads();
+      }
+      if (tid == 0) scalars[kScLamMax] = lam;
+    }
+  }
 }
 
 // ---------------------------------------------------------------- K2: L^{-1} by columns
-// Column c of X = L^{-1} solves L x = e_c by forward substitution,
-//     X_ic = (delta_ic - sum_{c<=k<i} L_ik X_kc) / L_ii,
-// independently of the other columns: one warp per column, kCB columns per CTA.  The CTA
-// stages the trailing triangle of L it needs (rows and columns >= its first column) in
-// shared memory; a warp keeps its column of X in registers (lane t holds rows c0 + t + 32 u)
-// and needs no barrier with the other warps.  n <= 128.
+// Column c of X = L^{-1} solves L x = e_c by forward substitution, independently of the
+// other columns: one warp per column, kCB columns per CTA.  Right-looking form: lane t owns
+// rows c0 + t + 32 u and their running sums acc_r = sum_{k<i} L_rk x_k; at step i the owner
+// of row i forms x_i = (delta_ic - acc_i) / L_ii, broadcasts it, and every lane adds
+// L_ri x_i to its rows r > i -- no reduction per row.  The CTA stages the trailing triangle
+// of L it needs (rows and columns >= its first column) in shared memory.  n <= 128.
 constexpr int kCB = 8;
+template <typename R>
+__device__ __forceinline__ R shfl_r(R v, int src) {
+  if constexpr (std::is_same<R, double>::value) return __shfl_sync(0xffffffffu, v, src);
+  else return df64(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+}
 template <typename R, bool C>
 __global__ void __launch_bounds__(32 * kCB) qtrinv_cols_kernel(const double* Lg, double* Li, int64_t ldl,
                                                                 int64_t psl, int n,
@@ -357,29 +423,36 @@ __global__ void __launch_bounds__(32 * kCB) qtrinv_cols_kernel(const double* Lg,
   __syncthreads();
   const int c = c0 + warp;
   if (c >= n) return;
-  QT<R> xs[4];
+  QT<R> acc[4], xs[4];
+  R invd[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) xs[u] = QT<R>{R(0), R(0), R(0), R(0)};
+  for (int u = 0; u < 4; ++u) {
+    acc[u] = QT<R>{R(0), R(0), R(0), R(0)};
+    xs[u] = acc[u];
+    const int lr = lane + 32 * u;
+    invd[u] = lr < nn ? rcp_(L[tri(lr, lr)].w) : R(0);
+  }
   for (int i = c; i < n; ++i) {
-    const int li = i - c0;
-    QT<R> acc{R(0), R(0), R(0), R(0)};
+    const int li = i - c0, owner = li & 31, uo = li >> 5;   // uo and owner are warp-uniform
+    QT<R> a = acc[0];
+    R id = invd[0];
+    if (uo == 1) { a = acc[1]; id = invd[1]; }
+    if (uo == 2) { a = acc[2]; id = invd[2]; }
+    if (uo == 3) { a = acc[3]; id = invd[3]; }
+    const R one = (i == c) ? R(1) : R(0);
+    QT<R> xi = qscale<R, C>(QT<R>{one - a.w, -a.x, -a.y, -a.z}, id);   // valid in the owner lane
+    xi.w = nrm_(shfl_r(xi.w, owner));
+    xi.x = nrm_(shfl_r(xi.x, owner));
+    if (!C) {
+      xi.y = nrm_(shfl_r(xi.y, owner));
+      xi.z = nrm_(shfl_r(xi.z, owner));
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int lk = lane + 32 * u, k = c0 + lk;
-      if (k >= c && k < i) acc = qmac<R, C>(acc, L[tri(li, lk)], xs[u]);
+      const int lr = lane + 32 * u;
+      if (lr == li) xs[u] = xi;
+      if (lr > li && lr < nn) acc[u] = qmac<R, C>(acc[u], L[tri(lr, li)], xi);
     }
-    acc.w = wsum(acc.w);
-    acc.x = wsum(acc.x);
-    if (!C) {
-      acc.y = wsum(acc.y);
-      acc.z = wsum(acc.z);
-    }
-    const R inv = rcp_(L[tri(li, li)].w);
-    const R one = (i == c) ? R(1) : R(0);
-    const QT<R> xi = qscale<R, C>(QT<R>{one - acc.w, -acc.x, -acc.y, -acc.z}, inv);
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (lane + 32 * u == li) xs[u] = QT<R>{nrm_(xi.w), nrm_(xi.x), nrm_(xi.y), nrm_(xi.z)};
   }
   // column c of Li: rows < c are zero
 #pragma unroll
@@ -400,12 +473,11 @@ __global__ void __launch_bounds__(32 * kCB) qtrinv_cols_kernel(const double* Lg,
 
 // ---------------------------------------------------------------- K3: power iterates (Sec. 3.1)
 // eps: rho = x* G^{-1} x = ||L^{-1} x||^2 on the iterates x <- G^{-1} x / |G^{-1} x| from
-// (c, 0, -c, 0), eps = 1 / sqrt(rho); lambda_max(G) from iterates z <- G z / |G z| on G
-// itself; kappa(H) = sqrt(lambda_max(G) rho).  Each output of a matrix-vector product is a
-// dot product shared by 8 lanes.
+// (c, 0, -c, 0), eps = 1 / sqrt(rho); with lambda_max(G) from the Cholesky kernel,
+// kappa(H) = sqrt(lambda_max(G) rho).  Each output of a matrix-vector product is a dot
+// product shared by 8 lanes.
 template <typename R>
-__global__ void __launch_bounds__(1024) qpower_kernel(const double* G, int64_t ldg, int64_t psg,
-                                                      const double* Li, int64_t ldl, int64_t psl,
+__global__ void __launch_bounds__(1024) qpower_kernel(const double* Li, int64_t ldl, int64_t psl,
                                                       int n, int power_slot, double kappa_stop,
                                                       int32_t* status, double* scalars) {
   if (scalars[kScCholOk] != 1.0) return;
@@ -414,10 +486,9 @@ __global__ void __launch_bounds__(1024) qpower_kernel(const double* G, int64_t l
   R* sbase = reinterpret_cast<R*>(smem_raw);
   const QS<R, false> L = QS<R, false>::make(sbase, ntri);                   // L^{-1}, lower
   const QS<R, false> row = QS<R, false>::make(sbase + 4 * ntri, n);
-  const QS<R, false> vec = QS<R, false>::make(sbase + 4 * ntri + 4 * n, 4 * n);
-  __shared__ double red[2][4];
-  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-  auto gget = [&](int i, int j, int p) { return G[p * psg + (int64_t)i * ldg + j]; };
+  const QS<R, false> vec = QS<R, false>::make(sbase + 4 * ntri + 4 * n, 2 * n);
+  __shared__ double red[2];
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
   for (int e = tid; e < ntri; e += nt) {
     int i, j;
     tri_rc(e, i, j);
@@ -425,36 +496,23 @@ __global__ void __launch_bounds__(1024) qpower_kernel(const double* G, int64_t l
                    from_d<R>(Li[2 * psl + (int64_t)i * ldl + j]), from_d<R>(Li[3 * psl + (int64_t)i * ldl + j])});
   }
   constexpr int P = 8;
-  const int X0 = 0, Y0 = n, Z0 = 2 * n, U0 = 3 * n;   // x, y = L^{-1} x, z, u = G z in vec
+  const int X0 = 0, Y0 = n;   // x and y = L^{-1} x in vec
   const double c0 = 1.0 / sqrt(2.0 * n);
-  for (int i = tid; i < n; i += nt) {
-    vec.set(X0 + i, QT<R>{from_d<R>(c0), R(0), from_d<R>(-c0), R(0)});
-    vec.set(Z0 + i, QT<R>{from_d<R>(c0), R(0), from_d<R>(-c0), R(0)});
-  }
+  for (int i = tid; i < n; i += nt) vec.set(X0 + i, QT<R>{from_d<R>(c0), R(0), from_d<R>(-c0), R(0)});
   __syncthreads();
-  double rho = 0.0, lam = 0.0;
+  double rho = 0.0;
   const int grp = tid / P, part = tid % P, ngrp = nt / P;
   for (int it = 0; it < 3; ++it) {
-    // y = L^{-1} x (lower) and u = G z
-    for (int ob = 0; ob < 2 * n; ob += ngrp) {   // trip count uniform over the block
+    for (int ob = 0; ob < n; ob += ngrp) {   // y = L^{-1} x (lower); trip count uniform
       const int o = ob + grp;
       QT<R> acc{R(0), R(0), R(0), R(0)};
-      if (o < n) {
+      if (o < n)
         for (int k = part; k <= o; k += P) acc = qt_mac(acc, L[tri(o, k)], vec[X0 + k]);
-      } else if (o < 2 * n) {
-        const int i = o - n;
-        for (int k = part; k < n; k += P) {
-          const QT<R> g{from_d<R>(gget(i, k, 0)), from_d<R>(gget(i, k, 1)), from_d<R>(gget(i, k, 2)),
-                        from_d<R>(gget(i, k, 3))};
-          acc = qt_mac(acc, g, vec[Z0 + k]);
-        }
-      }
       acc = gsum8q(acc);
-      if (part == 0 && o < 2 * n) vec.set((o < n ? Y0 : U0 - n) + o, acc);
+      if (part == 0 && o < n) vec.set(Y0 + o, acc);
     }
     __syncthreads();
-    // x <- L^{-*} y (into the row scratch first); |y|^2 = rho, z* u = lambda, |u|^2
-    for (int kb = 0; kb < n; kb += ngrp) {
+    for (int kb = 0; kb < n; kb += ngrp) {   // x <- L^{-*} y (into the row scratch first)
       const int k = kb + grp;
       QT<R> acc{R(0), R(0), R(0), R(0)};
       if (k < n)
@@ -462,26 +520,18 @@ __global__ void __launch_bounds__(1024) qpower_kernel(const double* G, int64_t l
       acc = gsum8q(acc);
       if (part == 0 && k < n) row.set(k, acc);
     }
-    if (warp == nw - 1) {
-      double sy = 0.0, zu = 0.0, su = 0.0;
+    if (warp == 1) {   // rho = |y|^2
+      double sy = 0.0;
       for (int i = lane; i < n; i += 32) {
-        const QT<R> yv = vec[Y0 + i], zv = vec[Z0 + i], uv = vec[U0 + i];
+        const QT<R> yv = vec[Y0 + i];
         sy += to_d(yv.w) * to_d(yv.w) + to_d(yv.x) * to_d(yv.x) + to_d(yv.y) * to_d(yv.y) + to_d(yv.z) * to_d(yv.z);
-        zu += to_d(zv.w) * to_d(uv.w) + to_d(zv.x) * to_d(uv.x) + to_d(zv.y) * to_d(uv.y) + to_d(zv.z) * to_d(uv.z);
-        su += to_d(uv.w) * to_d(uv.w) + to_d(uv.x) * to_d(uv.x) + to_d(uv.y) * to_d(uv.y) + to_d(uv.z) * to_d(uv.z);
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        sy += __shfl_xor_sync(0xffffffffu, sy, o);
-        zu += __shfl_xor_sync(0xffffffffu, zu, o);
-        su += __shfl_xor_sync(0xffffffffu, su, o);
-      }
-      if (lane == 0) { red[0][0] = sy; red[0][1] = zu; red[0][2] = su; }
+      for (int o = 16; o > 0; o >>= 1) sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      if (lane == 0) red[0] = sy;
     }
     __syncthreads();
-    rho = red[0][0];
-    lam = red[0][1];
-    const double su = red[0][2];
+    rho = red[0];
     if (warp == 0) {  // |L^{-*} y|^2
       double sv = 0.0;
       for (int i = lane; i < n; i += 32) {
@@ -490,19 +540,15 @@ __global__ void __launch_bounds__(1024) qpower_kernel(const double* G, int64_t l
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
-      if (lane == 0) red[1][0] = sv;
+      if (lane == 0) red[1] = sv;
     }
     __syncthreads();
-    const R inv_v = from_d<R>(red[1][0] > 0.0 ? 1.0 / sqrt(red[1][0]) : 0.0);
-    const R inv_u = from_d<R>(su > 0.0 ? 1.0 / sqrt(su) : 0.0);
-    for (int i = tid; i < n; i += nt) {
-      vec.set(X0 + i, qt_scale(row[i], inv_v));
-      vec.set(Z0 + i, qt_scale(vec[U0 + i], inv_u));
-    }
+    const R inv_v = from_d<R>(red[1] > 0.0 ? 1.0 / sqrt(red[1]) : 0.0);
+    for (int i = tid; i < n; i += nt) vec.set(X0 + i, qt_scale(row[i], inv_v));
     __syncthreads();
   }
   if (tid == 0) {
-    const double r = rho, lm = lam;
+    const double r = rho, lm = scalars[kScLamMax];
     if (!(r > 0.0) || !isfinite(r)) {
       scalars[power_slot] = 0.0;
       atomicOr(status, kDevRank | kDevStopCorr);
@@ -524,10 +570,13 @@ __global__ void __launch_bounds__(1024) qpower_kernel(const double* G, int64_t l
 }
 
 size_t smem_chol(int n, size_t rsize, bool cplx) {
+  return rsize * ((cplx ? 2 : 4) * ((size_t)n * (n + 1) / 2) + (cplx ? 0 : 12 * (size_t)n)) + 64;
+}
+size_t smem_trinv(int n, size_t rsize, bool cplx) {
   return rsize * (cplx ? 2 : 4) * ((size_t)n * (n + 1) / 2) + 64;
 }
 size_t smem_power(int n, size_t rsize) {
-  return rsize * (4 * ((size_t)n * (n + 1) / 2) + 20 * (size_t)n) + 64;
+  return rsize * (4 * ((size_t)n * (n + 1) / 2) + 12 * (size_t)n) + 64;
 }
 
 template <typename R, bool C>
@@ -542,7 +591,7 @@ cudaError_t launch_all(const double* G, int64_t ldg, int64_t psg, double* Lg, do
                                           power_slot, status, scalars, fail_bits);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t s2 = smem_chol(n, sizeof(R), C);
+  const size_t s2 = smem_trinv(n, sizeof(R), C);
   e = cudaFuncSetAttribute(qtrinv_cols_kernel<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
   if (e != cudaSuccess) return e;
   qtrinv_cols_kernel<R, C><<<(n + kCB - 1) / kCB, 32 * kCB, s2, st>>>(Lg, Li, ldl, psl, n, scalars);
@@ -552,8 +601,7 @@ cudaError_t launch_all(const double* G, int64_t ldg, int64_t psg, double* Lg, do
     const size_t s3 = smem_power(n, sizeof(R));
     e = cudaFuncSetAttribute(qpower_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3);
     if (e != cudaSuccess) return e;
-    qpower_kernel<R><<<1, 1024, s3, st>>>(G, ldg, psg, Li, ldl, psl, n, power_slot, kappa_stop,
-                                         status, scalars);
+    qpower_kernel<R><<<1, 1024, s3, st>>>(Li, ldl, psl, n, power_slot, kappa_stop, status, scalars);
     count_launch();
     e = cudaGetLastError();
   }
@@ -564,7 +612,9 @@ cudaError_t launch_all(const double* G, int64_t ldg, int64_t psg, double* Lg, do
 
 int qchol_inv_max_n() {
   int n = 1;
-  while (n + 1 <= 128 && smem_power(n + 1, sizeof(double)) <= 225 * 1024) ++n;
+  while (n + 1 <= 128 && std::max(smem_power(n + 1, sizeof(double)),
+                                   smem_chol(n + 1, sizeof(double), false)) <= 225 * 1024)
+    ++n;
   return n;
 }
 
