@@ -29,6 +29,25 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 N_SMS = 152
 FP32_LANES_PER_SM = 128
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the fused
+# sketch kernel on the c2 workload, from one ncu capture (profiles/fused_sketch_c2.md).  It
+# is reported only while the kernel's sources hash to what was captured.
+SKETCH_TRAFFIC = {"bytes": 1.249292e9 + 34.13888e6,
+                  "sources": ["qs_sketch_tc.cu", "qs_sketch_tc.cuh", "qs_tc_ptx.cuh"],
+                  "sha256": "e94ee477e7b76021025f2d7b68b06cb0151a5e5820e0defda94db23d10229c48"}
+
+
+def sketch_traffic(prec, workload_name):
+    """Captured per-launch DRAM bytes of the fused sketch, or None when not applicable."""
+    import hashlib
+    if prec != "bf16x3" or workload_name != "c2":
+        return None
+    h = hashlib.sha256()
+    for f in SKETCH_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_2404_14783_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return SKETCH_TRAFFIC["bytes"] if h.hexdigest() == SKETCH_TRAFFIC["sha256"] else None
+
 
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -279,7 +298,7 @@ def main():
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3"])
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--rangefinder", default="pseudo_qr")
-    ap.add_argument("--cpu-rows", type=int, default=1024)
+    ap.add_argument("--cpu-rows", type=int, default=4096)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -342,7 +361,7 @@ def main():
         roof = {"bound": "alu", "achieved": flops / (sk_ms * 1e-3) / 1e12, "peak": peak,
                 "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = sketch_traffic(args.prec, w["name"])
     roof["kernel"] = "fused sketch (qsketch_update)"
     roof["peak_source"] = peaks["_source"] + (" bf16 burst" if tc else " derived FP32 ALU")
     out = {"metric": metric, "value": res["gbs"], "unit": "GB/s", "n_gpus": world,

@@ -130,6 +130,18 @@ QS_API qs_status qsketch_update(qs_handle_t h, const void* const A_planes[4], in
                          int64_t row0, int64_t col0, int64_t mb, int64_t nb,
                          double theta, double eta, void* stream);
 
+/* Batched sketches (many independent matrices, Sec. 4.1 applied to each): for i in
+ * [0, count), the full-matrix update of handles[i] with theta = 0 and eta = 1, i.e.
+ *     Y_i = A_i Omega_i,   W_i = Psi_i A_i,
+ * where A_i is given by the four device planes A_planes[4 i .. 4 i + 3] (same conventions as
+ * qsketch_update; plane w may be NULL for a pure handle) with leading dimension lda[i].  The
+ * handles must be distinct.  All items are validated on the host before anything is
+ * enqueued: QS_ERR_INVALID for a bad handle, plane, alignment or lda, QS_ERR_UNSUPPORTED
+ * for a tensor-core handle with s > 256.  The updates are enqueued in order on `stream`. */
+QS_API qs_status qsketch_update_batched(int32_t count, const qs_handle_t* handles,
+                                        const void* const* A_planes, const int64_t* lda,
+                                        void* stream);
+
 /* Rangefinder H = F(Y) with R(H) = R(Y) (Sec. 3).
  *   QS_RF_PSEUDO_QR : Alg. 1.  Thin complex QR of Y_c (Cholesky-QR on the Gram of Y, with a
  *                     shift on breakdown), H from the Q factor, then n_correction steps

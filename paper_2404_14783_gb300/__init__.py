@@ -11,7 +11,8 @@ package is its thin Python binding.  See ``QSketch`` for the calls:
 """
 from .qsketch import (QSketch, QSError, QSConfig, load_library, ABI_SYMBOLS, LIB_PATH,
                       PRECISIONS, EMBEDDINGS, RANGEFINDERS, launch_count,
-                      reconstruct_error_static)
+                      reconstruct_error_static, update_batched)
 
 __all__ = ["QSketch", "QSError", "QSConfig", "load_library", "ABI_SYMBOLS", "LIB_PATH",
-           "PRECISIONS", "EMBEDDINGS", "RANGEFINDERS", "launch_count", "reconstruct_error_static"]
+           "PRECISIONS", "EMBEDDINGS", "RANGEFINDERS", "launch_count", "reconstruct_error_static",
+           "update_batched"]

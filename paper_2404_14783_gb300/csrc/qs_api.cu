@@ -439,6 +439,31 @@ qs_status qsketch_update(qs_handle_t h, const void* const A_planes[4], int64_t l
   return QS_OK;
 }
 
+// Independent full-matrix updates (theta = 0, eta = 1) of several sketches on one stream.
+// Every item is validated before the first launch, so an invalid batch enqueues nothing.
+qs_status qsketch_update_batched(int32_t count, const qs_handle_t* handles,
+                                 const void* const* A_planes, const int64_t* lda, void* stream) {
+  if (count < 0 || (count > 0 && (!handles || !A_planes || !lda))) return QS_ERR_INVALID;
+  for (int32_t i = 0; i < count; ++i) {
+    const qs_handle_t h = handles[i];
+    const void* const* A = A_planes + 4 * (int64_t)i;
+    if (!h || !planes_ok(h, A) || lda[i] < h->cfg.n) return QS_ERR_INVALID;
+    if (tc_mode(h->cfg.prec)) {   // the tensor-core sketch's TMA rules and TMEM plan
+      if (lda[i] % 4) return QS_ERR_INVALID;
+      for (int q = 0; q < 4; ++q)
+        if (A[q] && (reinterpret_cast<uintptr_t>(A[q]) & 15)) return QS_ERR_INVALID;
+      if ((h->cfg.s + 15) / 16 * 16 > 256) return QS_ERR_UNSUPPORTED;
+    }
+  }
+  for (int32_t i = 0; i < count; ++i) {
+    const qs_handle_t h = handles[i];
+    const qs_status r = qsketch_update(h, A_planes + 4 * (int64_t)i, lda[i], 0, 0, h->cfg.m,
+                                       h->cfg.n, 0.0, 1.0, stream);
+    if (r != QS_OK) return r;
+  }
+  return QS_OK;
+}
+
 qs_status qrangefinder(qs_handle_t h, int32_t kind, int32_t n_correction, void* stream) {
   if (!h) return QS_ERR_INVALID;
   if (kind != QS_RF_PSEUDO_QR && kind != QS_RF_PSEUDO_SVD) return QS_ERR_INVALID;

@@ -22,7 +22,8 @@
 //   warps 6-9   epilogue: TMEM -> registers -> red.global.add.v4.f32 into Y and W (L2).
 // TMEM (512 columns) is split into two halves used by alternating "waves": one W wave per
 // 128-row slice of Psi (W_q for q = 0..3, N = 64 columns each) and two Y waves (a pair of
-// output planes each, N = NS columns), so draining one wave overlaps the next wave's MMAs.
+// output planes each, N = NS columns) -- or, when NS > 128, four single-plane Y waves with
+// Omega staged in two row halves -- so draining one wave overlaps the next wave's MMAs.
 // Every wait is bounded (2 s of %globaltimer); on expiry the CTA records QS_ERR_TIMEOUT in
 // the workspace status word, stops issuing work, waits (bounded) for its own copies and
 // MMAs, frees TMEM and returns.
@@ -60,6 +61,9 @@ struct TcParams {
   int mb, nb, row0, col0;
   int tiles_m, tiles_n;
   int s, l, NS, MT, LS;
+  int YPW;   // output planes per Y wave: 2 when 2 NS <= 256, else 1 (then Omega is staged in
+             // two row halves of OB and NS - OB rows)
+  int OB;    // rows of one Omega stage (NS, or the first half when YPW == 1)
   int pure, nprod;
   float eta;
   float* Y[4];
@@ -140,9 +144,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   //       stages (k-half kh, Psi plane pa): 2 x 4.
   //   Y waves (one per pair of output planes): Y_q for q = 2 qp, 2 qp + 1 (NS columns each);
   //       stages (Omega plane pb): 4 (Omega is staged once per pair).
-  const int nwaves = p.MT + 2;
+  const int nwaves = p.MT + 4 / p.YPW;
   const uint32_t hl_tx = (p.nprod == 3) ? 2u : 1u;
-  auto wave_stages = [&](int wv) { return wv < p.MT ? 8 : 4; };
+  auto wave_stages = [&](int wv) { return wv < p.MT ? 8 : (p.YPW == 2 ? 4 : 8); };
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -175,10 +179,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tma_load_2d(dst + hl * 16384, &tPsi, p.row0 + ti * kBM + kh * 64,
                             (pl * 2 + hl) * p.LS + wv * 128, &sh->st_full[slot]);
             } else {
-              const int pl = st;
-              mbar_expect_tx(&sh->st_full[slot], hl_tx * (uint32_t)(p.NS * 128));
+              // Omega plane pl (YPW == 2), or row half h of plane pl (YPW == 1)
+              const int pl = p.YPW == 2 ? st : st >> 1, h = p.YPW == 2 ? 0 : st & 1;
+              mbar_expect_tx(&sh->st_full[slot], hl_tx * (uint32_t)(p.OB * 128));
               for (int hl = 0; hl < (int)hl_tx; ++hl)
-                tma_load_2d(dst + hl * 16384, &tOm, p.col0 + tj * kBN, (pl * 2 + hl) * p.NS,
+                tma_load_2d(dst + hl * 16384, &tOm, p.col0 + tj * kBN, (pl * 2 + hl) * p.NS + h * p.OB,
                             &sh->st_full[slot]);
             }
             ++slot_uses[slot];
@@ -238,17 +243,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                 started |= 1u << q;
               }
             } else {
-              // Y_q += sign A_a Omega_pb for q in the wave's pair  (M = 128 A rows, N = NS)
-              const int qp = wv - p.MT, pb = st;
+              // Y_q += sign A_a Omega_pb for q in the wave's plane(s)  (M = 128 A rows, N = NS,
+              // or the stage's row half of Omega when YPW == 1)
+              const int qp = wv - p.MT;
+              const int pb = p.YPW == 2 ? st : st >> 1, h = p.YPW == 2 ? 0 : st & 1;
+              const int nn = p.YPW == 2 ? p.NS : (h == 0 ? p.OB : p.NS - p.OB);
               const uint64_t dom = sdesc(stage, 16, 1024);
-              for (int j = 0; j < 2; ++j) {
-                const int q = 2 * qp + j;
+              for (int j = 0; j < p.YPW; ++j) {
+                const int q = p.YPW * qp + j;
                 const int a = kYPlaneA[q][pb];
                 if (p.pure && a == 0) continue;
-                const uint32_t idesc = idesc_bf16(128, p.NS, 0, kYSign[q][pb] < 0);
-                const uint32_t d = hbase + (uint32_t)(j * p.NS);
+                const uint32_t idesc = idesc_bf16(128, nn, 0, kYSign[q][pb] < 0);
+                const uint32_t d = hbase + (uint32_t)(p.YPW == 2 ? j * p.NS : h * p.OB);
+                const int sb = p.YPW == 2 ? j : h;   // accumulator region of this product
                 const uint64_t da = sdesc(a_base + a * 32768, 16, 2048);
-                uint32_t acc = (started >> j) & 1u;
+                uint32_t acc = (started >> sb) & 1u;
 #pragma unroll
                 for (int ks = 0; ks < 4; ++ks) {
                   const uint64_t ad = da + (uint64_t)((ks * 32) >> 4);
@@ -260,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     umma(d, ad, bd + (16384 >> 4), idesc, 1u);   // A_hi Omega_lo
                   }
                 }
-                started |= 1u << j;
+                started |= 1u << sb;
               }
             }
             umma_commit(&sh->st_empty[slot]);
@@ -352,11 +361,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         } else {
-          // lanes = A rows, NS columns per output plane of the pair
+          // lanes = A rows, NS columns per output plane of the wave
           const int qp = wv - p.MT;
           const int arow = ti * kBM + lq * 32 + lane;
-          for (int j = 0; j < 2; ++j) {
-            const int q = 2 * qp + j;
+          for (int j = 0; j < p.YPW; ++j) {
+            const int q = p.YPW * qp + j;
             float* yrow = p.Y[q] + (int64_t)(p.row0 + arow) * p.ldy;
             for (int c16 = 0; c16 < p.NS; c16 += 16) {
               float v[16];
@@ -489,7 +498,7 @@ qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t
                            int64_t col0, int64_t mb, int64_t nb, double eta, cudaStream_t st) {
   const qs_config& c = h.cfg;
   const PackGeom g = geom(c);
-  if (g.NS > 128 || g.LS > 256) return QS_ERR_UNSUPPORTED;   // TMEM plan of this kernel
+  if (g.NS > 256) return QS_ERR_UNSUPPORTED;   // a Y wave holds one plane of NS <= 256 columns
   if (lda % 4) return QS_ERR_INVALID;                         // TMA: 16-byte row pitch
   for (int q = 0; q < 4; ++q)
     if (A[q] && (reinterpret_cast<uintptr_t>(A[q]) & 15)) return QS_ERR_INVALID;
@@ -511,8 +520,10 @@ qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t
   const __nv_bfloat16* om = reinterpret_cast<const __nv_bfloat16*>(h.ws + h.off_pack);
   const __nv_bfloat16* ps =
       reinterpret_cast<const __nv_bfloat16*>(h.ws + h.off_pack + (g.om_bytes + 255) / 256 * 256);
+  const int ypw = 2 * g.NS <= 256 ? 2 : 1;
+  const int ob = ypw == 2 ? (int)g.NS : (int)((g.NS / 2 + 15) / 16 * 16);
   if (!make_map(&tOm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, om, c.n, 4 * 2 * g.NS, g.ldo, 64,
-                (uint32_t)g.NS, CU_TENSOR_MAP_SWIZZLE_128B))
+                (uint32_t)ob, CU_TENSOR_MAP_SWIZZLE_128B))
     return QS_ERR_CUDA;
   if (!make_map(&tPsi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ps, c.m, 4 * 2 * g.LS, g.ldp, 64, 128,
                 CU_TENSOR_MAP_SWIZZLE_128B))
@@ -523,6 +534,8 @@ qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t
   prm.tiles_n = (int)((nb + kBN - 1) / kBN);
   prm.s = (int)c.s; prm.l = (int)c.l; prm.NS = (int)g.NS; prm.LS = (int)g.LS;
   prm.MT = (int)(g.LS / 128);
+  prm.YPW = ypw;
+  prm.OB = ob;
   prm.pure = c.pure;
   prm.nprod = c.prec == QS_PREC_BF16X3 ? 3 : 1;
   prm.eta = (float)eta;

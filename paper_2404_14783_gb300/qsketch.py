@@ -29,7 +29,7 @@ RANGEFINDERS = {"pseudo_qr": QS_RF_PSEUDO_QR, "pseudo_svd": QS_RF_PSEUDO_SVD}
 ABI_SYMBOLS = ("qsketch_workspace_bytes", "qsketch_create", "qsketch_update", "qrangefinder",
                "qonepass_core", "qreconstruct_error", "qsketch_get", "qs_last_device_error",
                "qsketch_destroy", "qs_status_string", "qs_launch_count", "qs_version",
-               "qs_reconstruct_error_static")
+               "qs_reconstruct_error_static", "qsketch_update_batched")
 
 
 class QSConfig(ctypes.Structure):
@@ -73,9 +73,10 @@ def load_library(path=LIB_PATH):
     lib.qs_launch_count.restype = I64
     lib.qs_reconstruct_error_static.argtypes = [I64, I64, I64, I32, planes, I64, planes, I64,
                                                 planes, I64, VP, VP]
+    lib.qsketch_update_batched.argtypes = [I32, P(VP), P(VP), P(I64), VP]
     for name in ("qsketch_create", "qsketch_update", "qrangefinder", "qonepass_core",
                  "qreconstruct_error", "qsketch_get", "qs_last_device_error", "qsketch_destroy",
-                 "qs_reconstruct_error_static"):
+                 "qs_reconstruct_error_static", "qsketch_update_batched"):
         getattr(lib, name).restype = I32
     _lib = lib
     return lib
@@ -105,6 +106,24 @@ def reconstruct_error_static(A, H, X, out, stream=None):
                                            ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
            "qs_reconstruct_error_static")
     return out
+
+
+def update_batched(sketches, matrices, stream=None):
+    """Y_i = A_i Omega_i and W_i = Psi_i A_i for each (QSketch, A_i) pair in one call
+    (qsketch_update_batched); A_i as for QSketch.update, the whole matrix."""
+    lib = load_library()
+    count = len(sketches)
+    hs = (ctypes.c_void_p * max(count, 1))()
+    ptrs = (ctypes.c_void_p * max(4 * count, 1))()
+    lds = (ctypes.c_int64 * max(count, 1))()
+    for i, (qs, A) in enumerate(zip(sketches, matrices)):
+        p4, ld = _planes(A, qs.f64)
+        hs[i] = qs.handle
+        for q in range(4):
+            ptrs[4 * i + q] = p4[q]
+        lds[i] = ld
+    return _check(lib.qsketch_update_batched(count, hs, ptrs, lds, _stream_ptr(stream)),
+                  "qsketch_update_batched")
 
 
 def _dtype_of(M):

@@ -81,3 +81,16 @@ def test_host_validation_before_launch(lib):
     assert lib.qsketch_destroy(None) == QS_ERR_INVALID
     assert lib.qs_status_string(0) == b"ok"
     assert lib.qs_version() >= 100
+
+
+def test_batched_update_host_validation(lib):
+    """qsketch_update_batched validates every item before any CUDA call."""
+    from paper_2404_14783_gb300.qsketch import QS_ERR_INVALID, QS_OK
+    VP, I64 = ctypes.c_void_p, ctypes.c_int64
+    assert lib.qsketch_update_batched(0, None, None, None, None) == QS_OK
+    assert lib.qsketch_update_batched(-1, None, None, None, None) == QS_ERR_INVALID
+    hs = (VP * 1)(None)
+    ptrs = (VP * 4)(None, None, None, None)
+    lds = (I64 * 1)(8)
+    assert lib.qsketch_update_batched(1, hs, ptrs, lds, None) == QS_ERR_INVALID
+    assert lib.qsketch_update_batched(1, None, ptrs, lds, None) == QS_ERR_INVALID

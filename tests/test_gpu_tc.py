@@ -48,7 +48,10 @@ def _emb(n, s, l, m, seed, kind=O.EMB_GAUSSIAN):
 
 @pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
 @pytest.mark.parametrize("shape", [(256, 128, 21, 43), (300, 257, 13, 29), (128, 64, 1, 1),
-                                   (1000, 700, 101, 203), (129, 200, 16, 128)])
+                                   (1000, 700, 101, 203), (129, 200, 16, 128),
+                                   # s > 128: single-plane Y waves with Omega in two row halves;
+                                   # l > 256: three and four 128-row slices of Psi
+                                   (600, 500, 201, 403), (320, 300, 140, 290), (300, 260, 256, 256)])
 def test_tc_sketch_parity(pkg, prec, shape):
     m, n, s, l = shape
     A = WL.make_gaussian(m, n, seed=m * 7 + n).astype(np.float32)
@@ -105,3 +108,26 @@ def test_tc_pipeline_error_within_one_percent(pkg):
     Om, Psi = _emb(n, s, l, m, 8)
     ref = O.onepass(A.astype(np.float64), Om, Psi, "pseudo_qr", 3)
     assert abs(err - ref["err"]) <= 0.01 * ref["err"], (err, ref["err"])
+
+
+def test_tc_c3_shaped_pipeline(pkg):
+    """The c3 shape class (pure quaternion A, Rademacher test matrices, s = 201, l = 403) at
+    2048 x 1536: sketch parity, and the final error within 1e-3 of the oracle's (the sketch
+    error, <= 1e-5 relative, moves it far less; see test_gpu_pipeline)."""
+    m, n, s, l = 2048, 1536, 201, 403
+    A = WL.make_decay(m, n, seed=11, rank_cap=800, dtype=np.float32)
+    A[0] = 0.0
+    Ad = _dev(A)
+    planes = [None, Ad[1], Ad[2], Ad[3]]
+    qs = pkg.QSketch(m, n, s, l, emb="rademacher", prec="bf16x3", seed=13, pure=True)
+    qs.update(planes, theta=0.0)
+    qs.rangefinder("pseudo_qr", 3)
+    qs.core()
+    err = float(qs.error(planes).item())
+    assert qs.device_status() == 0
+    Om, Psi = _emb(n, s, l, m, 13, O.EMB_RADEMACHER)
+    A64 = Ad.double().cpu().numpy()
+    ref = O.onepass(A64, Om, Psi, "pseudo_qr", 3)
+    assert rel(qs.get("Y").cpu().numpy(), ref["Y"]) < 1e-5
+    assert rel(qs.get("W").cpu().numpy(), ref["W"]) < 1e-5
+    assert abs(err - ref["err"]) <= 1e-3 * ref["err"], (err, ref["err"])
