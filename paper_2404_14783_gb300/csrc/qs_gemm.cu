@@ -11,6 +11,7 @@
 // double-buffered slices (8 deep in FP32, 4 in FP64) with a register prefetch of the next
 // slice.  split-K (grid z) accumulates with atomics into a pre-scaled C.
 #include <algorithm>
+#include <type_traits>
 
 #include "qs_common.cuh"
 #include "qs_df64.cuh"
@@ -27,10 +28,13 @@ __device__ __forceinline__ T ld_elem(const void* base, int64_t idx) {
 // BCPLX: B has only its w and x planes (a complex matrix); the y and z products are skipped.
 // PARTIAL (error epilogue only): each CTA stores its two tile sums at err[2t], err[2t+1]
 // (t = its linear tile index) instead of adding them atomically into err[0], err[1].
+// TN: output columns per thread (4, or 2 for the double-float tall products: 4 x 2 outputs
+// per thread need about half the registers, so two CTAs share an SM, and the 32-column
+// tile wastes less of an N = s that is not a multiple of 64).
 template <typename ACC, typename TA, typename TB, typename TC, bool CONJ, bool BCPLX = false,
-          bool PARTIAL = false>
-__global__ void __launch_bounds__(256, sizeof(ACC) == 4 ? 2 : 1) qgemm_kernel(GemmDesc g) {
-  constexpr int BM = 64, BN = 64;
+          bool PARTIAL = false, int TN = 4>
+__global__ void __launch_bounds__(256, (sizeof(ACC) == 4 || TN == 2) ? 2 : 1) qgemm_kernel(GemmDesc g) {
+  constexpr int BM = 64, BN = 16 * TN;
   constexpr int BK = sizeof(ACC) == 8 ? 4 : 8;
   __shared__ __align__(16) ACC As[2][4][BK][BM];
   __shared__ __align__(16) ACC Bs[2][4][BK][BN];
@@ -68,7 +72,7 @@ __global__ void __launch_bounds__(256, sizeof(ACC) == 4 ? 2 : 1) qgemm_kernel(Ge
         if (!a_zero && k < kend && mm < g.M) va = ACC(A[mm * g.lda + k]);
       }
       const int64_t nn = n0 + lr;
-      if (!b_zero && k < kend && nn < g.N) vb = ACC(B[k * g.ldb + nn]);
+      if (!b_zero && lr < BN && k < kend && nn < g.N) vb = ACC(B[k * g.ldb + nn]);
       ra[kk] = va;
       rb[kk] = vb;
     }
@@ -77,17 +81,17 @@ __global__ void __launch_bounds__(256, sizeof(ACC) == 4 ? 2 : 1) qgemm_kernel(Ge
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       As[buf][lp][kk][lr] = ra[kk];
-      Bs[buf][lp][kk][lr] = rb[kk];
+      if (lr < BN) Bs[buf][lp][kk][lr] = rb[kk];
     }
   };
 
-  ACC acc[4][4][4];
+  ACC acc[4][4][TN];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[q][i][j] = ACC(0);
+      for (int j = 0; j < TN; ++j) acc[q][i][j] = ACC(0);
 
   int buf = 0;
   if (kbeg < kend) {
@@ -100,18 +104,18 @@ __global__ void __launch_bounds__(256, sizeof(ACC) == 4 ? 2 : 1) qgemm_kernel(Ge
     if (has_next) load_regs(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      ACC a[4][4], b[4][4];
+      ACC a[4][4], b[4][TN];
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
+      for (int p = 0; p < 4; ++p) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          a[p][i] = As[buf][p][kk][ty * 4 + i];
-          b[p][i] = Bs[buf][p][kk][tx * 4 + i];
-        }
+        for (int i = 0; i < 4; ++i) a[p][i] = As[buf][p][kk][ty * 4 + i];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) b[p][j] = Bs[buf][p][kk][tx * TN + j];
+      }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TN; ++j) {
           if (BCPLX) {  // b = b_w + b_x i: (a b)_w = a_w b_w - a_x b_x, (a b)_x = a_w b_x + a_x b_w,
                         // (a b)_y = a_y b_w + a_z b_x, (a b)_z = a_z b_w - a_y b_x
             acc[0][i][j] = fma(a[0][i], b[0][j], acc[0][i][j]);
@@ -143,8 +147,8 @@ __global__ void __launch_bounds__(256, sizeof(ACC) == 4 ? 2 : 1) qgemm_kernel(Ge
     for (int i = 0; i < 4; ++i) {
       const int64_t m = m0 + ty * 4 + i;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int64_t n = n0 + tx * 4 + j;
+      for (int j = 0; j < TN; ++j) {
+        const int64_t n = n0 + tx * TN + j;
         if (m < g.M && n < g.N) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
@@ -184,8 +188,8 @@ __global__ void __launch_bounds__(256, sizeof(ACC) == 4 ? 2 : 1) qgemm_kernel(Ge
     const int64_t m = m0 + ty * 4 + i;
     if (m >= g.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t n = n0 + tx * 4 + j;
+    for (int j = 0; j < TN; ++j) {
+      const int64_t n = n0 + tx * TN + j;
       if (n >= g.N) continue;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -383,8 +387,15 @@ cudaError_t launch_t(const GemmDesc& d, cudaStream_t st) {
   }
   dim3 grid((unsigned)((d.M + 63) / 64), (unsigned)((d.N + 63) / 64), (unsigned)d.splits);
   const bool bcplx = !d.b[2] && !d.b[3] && d.b[0] && d.b[1];
+  // double-float tall products with a narrow N: 64 x 32 tiles (4 x 2 outputs per thread)
+  const bool narrow = std::is_same<ACC, df64>::value && !d.conj_a && d.epi == 0;
+  dim3 grid2((unsigned)((d.M + 63) / 64), (unsigned)((d.N + 31) / 32), (unsigned)d.splits);
   if (d.conj_a)
     qgemm_kernel<ACC, TA, TB, TC, true><<<grid, 256, 0, st>>>(d);
+  else if (narrow && bcplx)
+    qgemm_kernel<ACC, TA, TB, TC, false, true, false, 2><<<grid2, 256, 0, st>>>(d);
+  else if (narrow)
+    qgemm_kernel<ACC, TA, TB, TC, false, false, false, 2><<<grid2, 256, 0, st>>>(d);
   else if (bcplx && sizeof(ACC) == 8)
     qgemm_kernel<ACC, TA, TB, TC, false, true><<<grid, 256, 0, st>>>(d);
   else
