@@ -182,6 +182,13 @@ __device__ __forceinline__ df64 sqrt_(df64 d) {
   return df_fast_two_sum(s0, corr);
 }
 
+// Number of 4-entry row chunks in rows 0..N-1 of a lower triangle (row ii has ii + 1
+// entries): sum_{u=1..N} ceil(u / 4) = 2 q (q + 1) + r (q + 1) for N = 4 q + r.
+__host__ __device__ __forceinline__ int chunks_before(int N) {
+  const int q = N >> 2, r = N & 3;
+  return 2 * q * (q + 1) + r * (q + 1);
+}
+
 // Row (ii) and column (kk) of entry f of a packed lower triangle (0 <= kk <= ii).
 __device__ __forceinline__ void tri_rc(int f, int& ii, int& kk) {
   int i = (int)((sqrtf(8.0f * (float)f + 1.0f) - 1.0f) * 0.5f);
@@ -247,6 +254,29 @@ __global__ void __launch_bounds__(1024) qchol_kernel(const double* G, int64_t ld
     give_up();
     return;
   }
+  // chunk table: work item t of a trailing update is up to 4 consecutive entries of one row,
+  // table[t] = (row << 5) | chunk over rows 0..n-2 of the trailing triangle (the triangle of
+  // any later pass is a prefix of it)
+  uint16_t* ctab = reinterpret_cast<uint16_t*>(reinterpret_cast<R*>(smem_raw) + (C ? 2 : 4) * ntri +
+                                               (C ? 0 : 12 * n));
+  for (int ii = tid; ii < n - 1; ii += nt) {
+    const int base = chunks_before(ii), cnt = (ii + 4) >> 2;
+    for (int c = 0; c < cnt; ++c) ctab[base + c] = (uint16_t)((ii << 5) | c);
+  }
+  // pivot quantities of column c in slot c % 3: d, 1/d, r = sqrt(d), 1/r, and a failure flag;
+  // the thread that updates the next diagonal entry fills the next slot, so no thread
+  // recomputes them and no extra barrier is needed
+  __shared__ R piv[3][4];
+  __shared__ int pfail[3];
+  auto set_pivot = [&](int c, R d) {
+    const int sl = c % 3;
+    const double dd = to_d(d);
+    pfail[sl] = (!(dd > 0.0) || !isfinite(dd)) ? 1 : 0;
+    if (!pfail[sl]) {
+      const R r = sqrt_(d);
+      piv[sl][0] = d; piv[sl][1] = rcp_(d); piv[sl][2] = r; piv[sl][3] = rcp_(r);
+    }
+  };
   double shift = 0.0;
   bool fail = false;
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -257,37 +287,37 @@ __global__ void __launch_bounds__(1024) qchol_kernel(const double* G, int64_t ld
       if (!C) { y = gget(i, j, 2); z = gget(i, j, 3); }
       if (i == j) { x = y = z = 0.0; w += shift; }
       L.set(e, QT<R>{from_d<R>(w), from_d<R>(x), from_d<R>(y), from_d<R>(z)});
+      if (e == 0) set_pivot(0, L[0].w);
     }
     __syncthreads();
     fail = false;
-    R dprev = R(0);
     for (int j = 0; j <= n; ++j) {
-      R inv_d = R(0), dj = R(0);
+      R inv_d = R(0);
       if (j < n) {
-        dj = L[tri(j, j)].w;
-        const double dd = to_d(dj);
-        if (!(dd > 0.0) || !isfinite(dd)) { fail = true; break; }   // same value in every thread
-        inv_d = rcp_(dj);
+        if (pfail[j % 3]) { fail = true; break; }   // same value in every thread
+        inv_d = piv[j % 3][1];
       }
       const int c = j - 1;
       const int S = c >= 0 ? n - c : 0;
-      const int T = j < n ? (n - j - 1) * (n - j) / 2 : 0;
-      R r = R(0), inv_r = R(0);
-      if (S > 0) { r = sqrt_(dprev); inv_r = rcp_(r); }
+      const int T = j < n - 1 ? chunks_before(n - j - 1) : 0;
+      const R r = c >= 0 ? piv[c % 3][2] : R(0), inv_r = c >= 0 ? piv[c % 3][3] : R(0);
       for (int e = tid; e < S + T; e += nt) {
         if (e < S) {
           const int i = c + e;
           if (e == 0) L.set(tri(c, c), QT<R>{r, R(0), R(0), R(0)});
           else L.set(tri(i, c), qscale<R, C>(L[tri(i, c)], inv_r));
         } else {
-          int ii, kk;
-          tri_rc(e - S, ii, kk);
-          const int i = j + 1 + ii, k = j + 1 + kk;
+          const int t = ctab[e - S], ii = t >> 5, k0 = (t & 31) << 2;
+          const int i = j + 1 + ii, k1 = min(k0 + 3, ii);
           const QT<R> a = qscale<R, C>(L[tri(i, j)], inv_d);
-          L.set(tri(i, k), qsub_mul_conj<R, C>(L[tri(i, k)], a, L[tri(k, j)]));
+          for (int kk = k0; kk <= k1; ++kk) {
+            const int k = j + 1 + kk;
+            const QT<R> v = qsub_mul_conj<R, C>(L[tri(i, k)], a, L[tri(k, j)]);
+            L.set(tri(i, k), v);
+            if (ii == 0) set_pivot(j + 1, L[tri(i, k)].w);   // the next diagonal entry
+          }
         }
       }
-      dprev = dj;
       __syncthreads();
     }
     if (!fail) break;
@@ -570,7 +600,8 @@ __global__ void __launch_bounds__(1024) qpower_kernel(const double* Li, int64_t 
 }
 
 size_t smem_chol(int n, size_t rsize, bool cplx) {
-  return rsize * ((cplx ? 2 : 4) * ((size_t)n * (n + 1) / 2) + (cplx ? 0 : 12 * (size_t)n)) + 64;
+  return rsize * ((cplx ? 2 : 4) * ((size_t)n * (n + 1) / 2) + (cplx ? 0 : 12 * (size_t)n)) +
+         2 * (size_t)chunks_before(n) + 64;
 }
 size_t smem_trinv(int n, size_t rsize, bool cplx) {
   return rsize * (cplx ? 2 : 4) * ((size_t)n * (n + 1) / 2) + 64;
