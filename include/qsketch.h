@@ -75,7 +75,8 @@ typedef enum { QS_EMB_GAUSSIAN = 0, QS_EMB_RADEMACHER = 1 } qs_embedding;
  *   FP32   : FP32 SIMT sketch (FP32 accumulation).
  *   BF16   : tensor-core sketch, A and the test matrices rounded to BF16, FP32 accumulation.
  *   BF16X3 : tensor-core sketch with a hi/lo BF16 split of A and of the test matrices;
- *            the products hi*hi + lo*hi + hi*lo are accumulated in FP32 (lo*lo dropped). */
+ *            the products hi*hi + lo*hi + hi*lo are accumulated in FP32 (lo*lo dropped);
+ *            Rademacher test matrices are exact in BF16, so only hi*hi + lo*hi is formed. */
 typedef enum { QS_PREC_FP64 = 0, QS_PREC_FP32 = 1, QS_PREC_BF16 = 2, QS_PREC_BF16X3 = 3 } qs_precision;
 
 typedef enum { QS_RF_PSEUDO_QR = 0, QS_RF_PSEUDO_SVD = 1 } qs_rangefinder_kind;
@@ -104,8 +105,15 @@ typedef struct {
   int32_t prec;     /* qs_precision                                               */
   uint64_t seed;    /* key of the counter-based generator                         */
   int32_t pure;     /* 1: A_w == 0 (pure quaternion); plane w is never read        */
-  int32_t flags;    /* reserved, must be 0                                         */
+  int32_t flags;    /* 0, or QS_FLAG_TEST_WITHHOLD_COPY (tensor-core precisions)  */
 } qs_config;
+
+/* qs_config.flags.  QS_FLAG_TEST_WITHHOLD_COPY is a test aid for the failure path of the
+ * bounded device waits (it has no counterpart in the paper): the tensor-core sketch never
+ * issues the copy of its first A tile, so each of its waits gives up after about 2 s and
+ * qs_last_device_error returns QS_ERR_TIMEOUT; Y and W are then undefined, and the CUDA
+ * context stays usable.  Valid only with QS_PREC_BF16 / QS_PREC_BF16X3. */
+#define QS_FLAG_TEST_WITHHOLD_COPY 1
 
 /* Bytes of device workspace qsketch_create needs for cfg (0 if cfg is invalid). */
 QS_API size_t qsketch_workspace_bytes(const qs_config* cfg);

@@ -35,7 +35,8 @@ bool valid_cfg(const qs_config* c) {
   if (c->emb != QS_EMB_GAUSSIAN && c->emb != QS_EMB_RADEMACHER) return false;
   if (c->prec < QS_PREC_FP64 || c->prec > QS_PREC_BF16X3) return false;
   if (c->pure != 0 && c->pure != 1) return false;
-  if (c->flags != 0) return false;
+  if (c->flags & ~QS_FLAG_TEST_WITHHOLD_COPY) return false;
+  if (c->flags && c->prec != QS_PREC_BF16 && c->prec != QS_PREC_BF16X3) return false;
   return true;
 }
 

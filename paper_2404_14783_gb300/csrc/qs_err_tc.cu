@@ -70,13 +70,17 @@ struct Shared {
   volatile int abort;
 };
 
-__device__ bool wait_bar(uint64_t* bar, uint32_t parity, Shared* sh, int32_t* status) {
+// drain: a role's final wait for its own copies or MMAs; it ignores the abort flag (only
+// the time bound ends it), so nothing the CTA started is in flight when it frees TMEM and
+// exits.
+__device__ bool wait_bar(uint64_t* bar, uint32_t parity, Shared* sh, int32_t* status,
+                         bool drain = false) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = gtime();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255) == 255) {
-      if (sh->abort) return false;
+      if (!drain && sh->abort) return false;
       if (gtime() - t0 > kWaitNs) {
         sh->abort = 1;
         atomicOr(status, kDevTimeout);
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       for (int s = 0; s < kStages; ++s)
-        if (uses[s] > 0) wait_bar(&sh->st_full[s], (uses[s] - 1) & 1, sh, p.status);
+        if (uses[s] > 0) wait_bar(&sh->st_full[s], (uses[s] - 1) & 1, sh, p.status, true);
     }
   } else if (warp == 6) {
     // ------------------------------------------------------------ A producer
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       for (int s = 0; s < kASlots; ++s)
-        if (uses[s] > 0) wait_bar(&sh->a_full[s], (uses[s] - 1) & 1, sh, p.status);
+        if (uses[s] > 0) wait_bar(&sh->a_full[s], (uses[s] - 1) & 1, sh, p.status, true);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         umma_commit(&sh->h_full[half]);
       }
       umma_commit(&sh->done);
-      wait_bar(&sh->done, 0, sh, p.status);
+      wait_bar(&sh->done, 0, sh, p.status, true);
     }
   } else {
     // ------------------------------------------------------------ epilogue (warps 2-5)

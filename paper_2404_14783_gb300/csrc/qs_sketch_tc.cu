@@ -11,7 +11,8 @@
 //
 // Precision: A (FP32) is split on chip into BF16 hi = bf16(a) and lo = bf16(a - hi); the
 // test matrices are packed the same way.  QS_PREC_BF16X3 accumulates hi*hi + lo*hi + hi*lo
-// in FP32 (TMEM); QS_PREC_BF16 only hi*hi.
+// in FP32 (TMEM) -- hi*hi + lo*hi for Rademacher test matrices, which are exact in BF16;
+// QS_PREC_BF16 only hi*hi.
 //
 // One CTA per SM (persistent).  Tile = 128 rows x 64 columns of A, all four planes:
 //   warp 0      TMA producer: A tile (FP32, 4 x 32 KB) and a 3-stage ring of BF16 operand
@@ -64,7 +65,8 @@ struct TcParams {
   int YPW;   // output planes per Y wave: 2 when 2 NS <= 256, else 1 (then Omega is staged in
              // two row halves of OB and NS - OB rows)
   int OB;    // rows of one Omega stage (NS, or the first half when YPW == 1)
-  int pure, nprod;
+  int pure, nprod;   // 1: hi*hi; 2: + A_lo*T_hi; 3: + A_hi*T_lo (T = Omega or Psi)
+  int withhold;      // test aid: the copy of the first A tile is never issued
   float eta;
   float* Y[4];
   int64_t ldy;
@@ -81,13 +83,17 @@ struct Shared {
   volatile int abort;
 };
 
-__device__ bool wait_bar(uint64_t* bar, uint32_t parity, Shared* sh, int32_t* status) {
+// drain: a role's final wait for its own copies or MMAs; it ignores the abort flag (only
+// the time bound ends it), so nothing the CTA started is in flight when it frees TMEM and
+// exits.
+__device__ bool wait_bar(uint64_t* bar, uint32_t parity, Shared* sh, int32_t* status,
+                         bool drain = false) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = gtime();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255) == 255) {
-      if (sh->abort) return false;
+      if (!drain && sh->abort) return false;
       if (gtime() - t0 > kWaitNs) {
         sh->abort = 1;
         atomicOr(status, kDevTimeout);
@@ -109,7 +115,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* sRing = smem + kABytes;
   Shared* sh = reinterpret_cast<Shared*>(smem + kABytes + kStages * kStageBytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const CUtensorMap* tA[4] = {&tA0, &tA1, &tA2, &tA3};
+  auto tA = [&](int q) { return q == 0 ? &tA0 : q == 1 ? &tA1 : q == 2 ? &tA2 : &tA3; };
   const int ntiles = p.tiles_m * p.tiles_n;
   const int nplanes_a = p.pure ? 3 : 4;
   const int p0 = p.pure ? 1 : 0;  // first A plane present
@@ -151,8 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      int slot = 0;
-      uint32_t slot_uses[kStages] = {0, 0, 0};
+      uint32_t gs = 0;   // stages issued: ring slot gs % kStages, its use gs / kStages
       int t_local = 0;
       bool a_outstanding = false;
       uint32_t a_fills = 0;
@@ -160,14 +165,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int t = blockIdx.x; t < ntiles && !stop && !sh->abort; t += gridDim.x, ++t_local) {
         const int ti = t / p.tiles_n, tj = t % p.tiles_n;
         if (t_local > 0 && !wait_bar(&sh->a_free, (t_local - 1) & 1, sh, p.status)) break;
-        mbar_expect_tx(&sh->a_full, nplanes_a * 32768u);
-        for (int q = p0; q < 4; ++q) tma_load_2d(sA + q * 32768, tA[q], tj * kBN, ti * kBM, &sh->a_full);
-        a_outstanding = true;
-        ++a_fills;
+        if (!(p.withhold && t_local == 0)) {
+          mbar_expect_tx(&sh->a_full, nplanes_a * 32768u);
+          for (int q = p0; q < 4; ++q) tma_load_2d(sA + q * 32768, tA(q), tj * kBN, ti * kBM, &sh->a_full);
+          a_outstanding = true;
+          ++a_fills;
+        }
         for (int wv = 0; wv < nwaves && !stop; ++wv) {
           for (int st = 0; st < wave_stages(wv); ++st) {
-            if (slot_uses[slot] > 0 &&
-                !wait_bar(&sh->st_empty[slot], (slot_uses[slot] - 1) & 1, sh, p.status)) {
+            const uint32_t slot = gs % kStages, use = gs / kStages;
+            if (use > 0 && !wait_bar(&sh->st_empty[slot], (use - 1) & 1, sh, p.status)) {
               stop = true;
               break;
             }
@@ -186,24 +193,35 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tma_load_2d(dst + hl * 16384, &tOm, p.col0 + tj * kBN, (pl * 2 + hl) * p.NS + h * p.OB,
                             &sh->st_full[slot]);
             }
-            ++slot_uses[slot];
-            slot = (slot + 1) % kStages;
+            ++gs;
           }
         }
       }
       // wait (bounded) for our own copies before leaving
-      if (a_outstanding) wait_bar(&sh->a_full, (a_fills - 1) & 1, sh, p.status);
-      for (int s = 0; s < kStages; ++s)
-        if (slot_uses[s] > 0) wait_bar(&sh->st_full[s], (slot_uses[s] - 1) & 1, sh, p.status);
+      if (a_outstanding) wait_bar(&sh->a_full, (a_fills - 1) & 1, sh, p.status, true);
+      for (uint32_t k = gs > kStages ? gs - kStages : 0; k < gs; ++k)
+        wait_bar(&sh->st_full[k % kStages], (k / kStages) & 1, sh, p.status, true);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      int slot = 0;
-      uint32_t slot_uses[kStages] = {0, 0, 0};
-      uint32_t g = 0;  // global wave counter: half = g & 1, use of that half = g >> 1
+      uint32_t gs = 0;  // stages consumed: ring slot gs % kStages, parity (gs / kStages) & 1
+      uint32_t g = 0;   // global wave counter: half = g & 1, use of that half = g >> 1
       int t_local = 0;
       const uint32_t a_base = smem_u32(sA), r_base = smem_u32(sRing);
+      // Hamilton-product signs as bit masks (bit 4 q + p: negative), planes q ^ p
+      uint32_t wneg = 0, yneg = 0;
+      for (int q = 0; q < 4; ++q)
+        for (int k = 0; k < 4; ++k) {
+          wneg |= (kWSign[q][k] < 0 ? 1u : 0u) << (4 * q + k);
+          yneg |= (kYSign[q][k] < 0 ? 1u : 0u) << (4 * q + k);
+        }
+      // products: hi*hi, then A_lo * (test hi) when nprod >= 2, (test lo) * A_hi when nprod == 3
+      const bool alo = p.nprod >= 2, three = p.nprod == 3, pure = p.pure != 0;
+      const int MT = p.MT, YPW = p.YPW, NS = p.NS, OB = p.OB;
+      const uint32_t wid_pos = idesc_bf16(128, 64, 1, 0), wid_neg = idesc_bf16(128, 64, 1, 1);
+      const uint64_t dA_w = sdesc(a_base, 32768, 2048);   // A tile as the W products' B operand
+      const uint64_t dA_y = sdesc(a_base, 16, 2048);      // A tile as the Y products' A operand
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok && !sh->abort; t += gridDim.x, ++t_local) {
         if (!wait_bar(&sh->a_ready, t_local & 1, sh, p.status)) break;
@@ -214,67 +232,64 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint32_t hbase = tmem + half * 256;
           uint32_t started = 0;
-          for (int st = 0; st < wave_stages(wv); ++st) {
-            if (!wait_bar(&sh->st_full[slot], slot_uses[slot] & 1, sh, p.status)) { ok = false; break; }
+          const int nst = wave_stages(wv);
+          for (int st = 0; st < nst; ++st, ++gs) {
+            const uint32_t slot = gs % kStages;
+            if (!wait_bar(&sh->st_full[slot], (gs / kStages) & 1, sh, p.status)) { ok = false; break; }
             tc_fence_after();
             const uint32_t stage = r_base + slot * kStageBytes;
-            if (wv < p.MT) {
-              // W_q[mt] += sign Psi_pa A_b  (M = 128 Psi rows, N = 64 A columns)
+            const uint64_t dst = sdesc(stage, 16, 1024);
+            if (wv < MT) {
+              // W_q[mt] += sign Psi_pa A_b, b = q ^ pa  (M = 128 Psi rows, N = 64 A columns)
               const int kh = st >> 2, pa = st & 3;
-              const uint64_t dpsi = sdesc(stage, 16, 1024);
+#pragma unroll
               for (int q = 0; q < 4; ++q) {
-                const int b = kWPlaneB[q][pa];
-                if (p.pure && b == 0) continue;
-                const uint32_t idesc = idesc_bf16(128, 64, 1, kWSign[q][pa] < 0);
+                const int b = q ^ pa;
+                if (pure && b == 0) continue;
+                const uint32_t idesc = ((wneg >> (4 * q + pa)) & 1u) ? wid_neg : wid_pos;
                 const uint32_t d = hbase + (uint32_t)(q * 64);
-                const uint64_t da = sdesc(a_base + b * 32768 + (uint32_t)(kh * 8) * 2048, 32768, 2048);
+                const uint64_t da = dA_w + (uint64_t)((b * 32768 + kh * 16384) >> 4);
                 uint32_t acc = (started >> q) & 1u;
 #pragma unroll
                 for (int ks = 0; ks < 4; ++ks) {
-                  const uint64_t ad = dpsi + (uint64_t)((ks * 32) >> 4);
-                  const uint64_t bd = da + (uint64_t)((ks * 2 * 2048) >> 4);
-                  umma(d, ad, bd, idesc, acc);                   // Psi_hi A_hi
+                  const uint64_t ad = dst + (uint64_t)(ks * 2);          // 32 B along K
+                  const uint64_t bd = da + (uint64_t)(ks * 256);         // 2 x 2048 B along K
+                  umma(d, ad, bd, idesc, acc);                           // Psi_hi A_hi
                   acc = 1u;
-                  if (p.nprod == 3) {
-                    umma(d, ad, bd + (1024 >> 4), idesc, 1u);    // Psi_hi A_lo
-                    umma(d, ad + (16384 >> 4), bd, idesc, 1u);   // Psi_lo A_hi
-                  }
+                  if (alo) umma(d, ad, bd + 64, idesc, 1u);              // Psi_hi A_lo
+                  if (three) umma(d, ad + 1024, bd, idesc, 1u);          // Psi_lo A_hi
                 }
                 started |= 1u << q;
               }
             } else {
-              // Y_q += sign A_a Omega_pb for q in the wave's plane(s)  (M = 128 A rows, N = NS,
-              // or the stage's row half of Omega when YPW == 1)
-              const int qp = wv - p.MT;
-              const int pb = p.YPW == 2 ? st : st >> 1, h = p.YPW == 2 ? 0 : st & 1;
-              const int nn = p.YPW == 2 ? p.NS : (h == 0 ? p.OB : p.NS - p.OB);
-              const uint64_t dom = sdesc(stage, 16, 1024);
-              for (int j = 0; j < p.YPW; ++j) {
-                const int q = p.YPW * qp + j;
-                const int a = kYPlaneA[q][pb];
-                if (p.pure && a == 0) continue;
-                const uint32_t idesc = idesc_bf16(128, nn, 0, kYSign[q][pb] < 0);
-                const uint32_t d = hbase + (uint32_t)(p.YPW == 2 ? j * p.NS : h * p.OB);
-                const int sb = p.YPW == 2 ? j : h;   // accumulator region of this product
-                const uint64_t da = sdesc(a_base + a * 32768, 16, 2048);
+              // Y_q += sign A_a Omega_pb, a = q ^ pb, for q in the wave's plane(s)  (M = 128 A
+              // rows, N = NS, or the stage's row half of Omega when YPW == 1)
+              const int qp = wv - MT;
+              const int pb = YPW == 2 ? st : st >> 1, h = YPW == 2 ? 0 : st & 1;
+              const int nn = YPW == 2 ? NS : (h == 0 ? OB : NS - OB);
+              const uint32_t yid_pos = idesc_bf16(128, nn, 0, 0), yid_neg = idesc_bf16(128, nn, 0, 1);
+              for (int j = 0; j < YPW; ++j) {
+                const int q = YPW * qp + j;
+                const int a = q ^ pb;
+                if (pure && a == 0) continue;
+                const uint32_t idesc = ((yneg >> (4 * q + pb)) & 1u) ? yid_neg : yid_pos;
+                const uint32_t d = hbase + (uint32_t)(YPW == 2 ? j * NS : h * OB);
+                const int sb = YPW == 2 ? j : h;   // accumulator region of this product
+                const uint64_t da = dA_y + (uint64_t)((a * 32768) >> 4);
                 uint32_t acc = (started >> sb) & 1u;
 #pragma unroll
                 for (int ks = 0; ks < 4; ++ks) {
-                  const uint64_t ad = da + (uint64_t)((ks * 32) >> 4);
-                  const uint64_t bd = dom + (uint64_t)((ks * 32) >> 4);
-                  umma(d, ad, bd, idesc, acc);                   // A_hi Omega_hi
+                  const uint64_t ad = da + (uint64_t)(ks * 2);
+                  const uint64_t bd = dst + (uint64_t)(ks * 2);
+                  umma(d, ad, bd, idesc, acc);                           // A_hi Omega_hi
                   acc = 1u;
-                  if (p.nprod == 3) {
-                    umma(d, ad + (1024 >> 4), bd, idesc, 1u);    // A_lo Omega_hi
-                    umma(d, ad, bd + (16384 >> 4), idesc, 1u);   // A_hi Omega_lo
-                  }
+                  if (alo) umma(d, ad + 64, bd, idesc, 1u);              // A_lo Omega_hi
+                  if (three) umma(d, ad, bd + 1024, idesc, 1u);          // A_hi Omega_lo
                 }
                 started |= 1u << sb;
               }
             }
             umma_commit(&sh->st_empty[slot]);
-            ++slot_uses[slot];
-            slot = (slot + 1) % kStages;
           }
           if (!ok) break;
           if (wv == nwaves - 1) umma_commit(&sh->a_free);
@@ -283,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // drain: every MMA issued so far completes before TMEM is released
       umma_commit(&sh->done);
-      wait_bar(&sh->done, 0, sh, p.status);
+      wait_bar(&sh->done, 0, sh, p.status, true);
     }
   } else if (warp >= 2 && warp <= 5) {
     // ------------------------------------------------------------ converters
@@ -537,8 +552,11 @@ qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t
   prm.YPW = ypw;
   prm.OB = ob;
   prm.pure = c.pure;
-  prm.nprod = c.prec == QS_PREC_BF16X3 ? 3 : 1;
+  // split BF16: Rademacher test matrices are exact in BF16 (their lo half is zero), so the
+  // product with it is dropped
+  prm.nprod = c.prec == QS_PREC_BF16X3 ? (c.emb == QS_EMB_RADEMACHER ? 2 : 3) : 1;
   prm.eta = (float)eta;
+  prm.withhold = (c.flags & QS_FLAG_TEST_WITHHOLD_COPY) ? 1 : 0;
   const int64_t sy = (c.s + 3) / 4 * 4;
   for (int q = 0; q < 4; ++q) {
     prm.Y[q] = reinterpret_cast<float*>(h.ws + h.off_y) + q * c.m * sy;

@@ -20,6 +20,7 @@ QS_RF_PSEUDO_QR, QS_RF_PSEUDO_SVD = 0, 1
 QS_OBJ_Y, QS_OBJ_W, QS_OBJ_OMEGA, QS_OBJ_PSI, QS_OBJ_H, QS_OBJ_X, QS_OBJ_PSIH, \
     QS_OBJ_SCALARS = range(8)
 QS_DT_F64, QS_DT_F32 = 0, 1
+QS_FLAG_TEST_WITHHOLD_COPY = 1
 
 PRECISIONS = {"fp64": QS_PREC_FP64, "fp32": QS_PREC_FP32, "bf16": QS_PREC_BF16,
               "bf16x3": QS_PREC_BF16X3}
@@ -181,10 +182,10 @@ class QSketch:
     """One sketch state (Omega, Psi, Y, W and the results) in a caller-owned workspace."""
 
     def __init__(self, m, n, s, l, emb="gaussian", prec="fp64", seed=0, pure=False,
-                 device="cuda", stream=None):
+                 device="cuda", stream=None, flags=0):
         self.lib = load_library()
         self.cfg = QSConfig(m, n, s, l, EMBEDDINGS.get(emb, emb), PRECISIONS.get(prec, prec),
-                            seed, int(bool(pure)), 0)
+                            seed, int(bool(pure)), int(flags))
         self.f64 = self.cfg.prec == QS_PREC_FP64
         nbytes = self.lib.qsketch_workspace_bytes(ctypes.byref(self.cfg))
         if nbytes == 0:

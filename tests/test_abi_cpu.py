@@ -94,3 +94,10 @@ def test_batched_update_host_validation(lib):
     lds = (I64 * 1)(8)
     assert lib.qsketch_update_batched(1, hs, ptrs, lds, None) == QS_ERR_INVALID
     assert lib.qsketch_update_batched(1, None, ptrs, lds, None) == QS_ERR_INVALID
+
+
+def test_test_flag_only_in_tensor_core_modes(lib):
+    # the withhold switch is valid with the tensor-core precisions only
+    assert lib.qsketch_workspace_bytes(ctypes.byref(_cfg(flags=1, prec=3))) > 0
+    assert lib.qsketch_workspace_bytes(ctypes.byref(_cfg(flags=1, prec=1))) == 0
+    assert lib.qsketch_workspace_bytes(ctypes.byref(_cfg(flags=2, prec=3))) == 0
