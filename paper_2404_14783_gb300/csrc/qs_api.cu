@@ -25,6 +25,10 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 constexpr int kSmallSlots = 16;  // s x s FP64 scratch matrices
 constexpr double kKappaStop = 1e8;
+// FP32 modes: the core's Cholesky-QR2 of P = Psi H runs in FP32 when the last kappa(H)
+// estimate is below this (kappa(P) ~ a few kappa(H), so u32 kappa(P)^2 stays far below 1 and
+// the second pass restores orthogonality; P itself carries FP32-level error).
+constexpr double kFp32Kappa = 30.0;
 
 bool valid_cfg(const qs_config* c) {
   if (!c) return false;
@@ -195,14 +199,14 @@ cudaError_t gram(const Ctx& x, const Mat& A, int64_t rows, int64_t cols, const M
 // kernels.
 cudaError_t chol_inv(const Ctx& x, const Mat& G, const Mat& L, const Mat& Li, int complex_only,
                      int allow_shift, double shift_rows, int slot, int fail_bits,
-                     bool want_L = false) {
+                     bool want_L = false, const double* fp32_gate = nullptr) {
   const int s = (int)x.s;
   int32_t* st = x.status();
   double* sc = x.scalars();
   if (s <= qchol_inv_max_n())
     return launch_qchol_inv((const double*)G.p, G.ld, G.ps, (double*)Li.p, Li.ld, Li.ps, s,
                             complex_only, allow_shift, shift_rows, slot, kKappaStop, !x.f64, st, sc,
-                            fail_bits, (double*)L.p, x.st);
+                            fail_bits, (double*)L.p, x.st, fp32_gate, kFp32Kappa);
   cudaError_t e = launch_qchol((const double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s,
                                complex_only, allow_shift, shift_rows, st, sc, fail_bits, x.st);
   if (e == cudaSuccess && slot >= 0)
@@ -287,12 +291,13 @@ qs_status core_solve(const Ctx& x) {
     QS_CU(launch_qcopy(P32.p, 0, P32.ld, P32.ps, P.p, 1, P.ld, P.ps, l, s, x.st));
   }
   // Alg. QLEQ on chi_P: QR of P (quaternion Cholesky-QR, twice), X = R^{-1} Q* W
+  const double* lo = (!x.f64 && x.h->h_well_conditioned) ? sc + kScKappa : nullptr;
   QS_CU(gram(x, P, l, s, G));
-  QS_CU(chol_inv(x, G, L, L1i, 0, 1, 4.0 * l, -1, kDevRank));
+  QS_CU(chol_inv(x, G, L, L1i, 0, 1, 4.0 * l, -1, kDevRank, false, lo));
   QS_CU(launch_qconjT(L1i.p, 1, L1i.ld, L1i.ps, R1.p, 1, R1.ld, R1.ps, s, s, x.st));
   QS_CU(gemm(x, P, false, R1, Tp, l, s, s, 1.0, 0.0, x.acc_hi(), false));
   QS_CU(gram(x, Tp, l, s, G));
-  QS_CU(chol_inv(x, G, L, L2i, 0, 0, 4.0 * l, -1, kDevRank));
+  QS_CU(chol_inv(x, G, L, L2i, 0, 0, 4.0 * l, -1, kDevRank, false, lo));
   QS_CU(launch_qconjT(L2i.p, 1, L2i.ld, L2i.ps, R2.p, 1, R2.ld, R2.ps, s, s, x.st));
   QS_CU(gemm(x, Tp, false, R2, Qp, l, s, s, 1.0, 0.0, x.acc_hi(), false));       // Q (l x s)
   QS_CU(gemm(x, L2i, false, L1i, S, s, s, s, 1.0, 0.0, x.acc_hi(), false));      // (R^{-1})* = L2^{-1} L1^{-1}

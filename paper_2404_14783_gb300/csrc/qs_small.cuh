@@ -25,11 +25,13 @@ cudaError_t launch_qgram_update(const double* G, double* Gn, const double* Gi, i
                                 cudaStream_t st);
 // Shared-memory Cholesky G = L L* (writes L, lower, to Lg), L^{-1} to Li (several CTAs, one
 // warp per column) and, when power_slot >= 0, the power-iteration eps into
-// scalars[power_slot] (same leading dimension and plane stride for Lg and Li).
-// n <= qchol_inv_max_n().
+// scalars[power_slot] (same leading dimension and plane stride for Lg and Li).  With use_df64
+// and fp32_gate, the factorisation runs in FP32 instead when *fp32_gate < fp32_below (decided
+// on the device).  n <= qchol_inv_max_n().
 int qchol_inv_max_n();
 cudaError_t launch_qchol_inv(const double* G, int64_t ldg, int64_t psg, double* Li, int64_t ldl,
                              int64_t psl, int n, int complex_only, int allow_shift, double shift_rows,
                              int power_slot, double kappa_stop, int use_df64, int32_t* status,
-                             double* scalars, int fail_bits, double* Lg, cudaStream_t st);
+                             double* scalars, int fail_bits, double* Lg, cudaStream_t st,
+                             const double* fp32_gate = nullptr, double fp32_below = 0.0);
 }  // namespace qs

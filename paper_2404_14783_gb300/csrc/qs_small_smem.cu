@@ -25,6 +25,7 @@ namespace qs {
 namespace {
 
 __device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(float v) { return (double)v; }
 __device__ __forceinline__ double to_d(df64 v) { return static_cast<double>(v); }
 template <typename R>
 __device__ __forceinline__ R from_d(double v) { return R(v); }
@@ -139,6 +140,7 @@ __device__ __forceinline__ QT<R> qscale(const QT<R>& a, R s) {
 }
 
 __device__ __forceinline__ double nrm_(double v) { return v; }
+__device__ __forceinline__ float nrm_(float v) { return v; }
 __device__ __forceinline__ df64 nrm_(df64 v) { return df_norm(v); }
 
 // Quaternion array in shared memory stored component-wise (structure of arrays); with C only
@@ -168,6 +170,8 @@ struct QS {
 // plus one Newton step, about 46 correct bits).
 __device__ __forceinline__ double rcp_(double d) { return 1.0 / d; }
 __device__ __forceinline__ double sqrt_(double d) { return sqrt(d); }
+__device__ __forceinline__ float rcp_(float d) { return 1.0f / d; }
+__device__ __forceinline__ float sqrt_(float d) { return sqrtf(d); }
 __device__ __forceinline__ df64 rcp_(df64 d) {
   d = df_norm(d);
   const float r0 = __frcp_rn(d.hi);
@@ -203,10 +207,10 @@ template <typename R>
 __device__ __forceinline__ R gsum8(R v) {
 #pragma unroll
   for (int o = 4; o > 0; o >>= 1) {
-    if constexpr (std::is_same<R, double>::value) {
-      v = v + __shfl_xor_sync(0xffffffffu, v, o);
-    } else {
+    if constexpr (std::is_same<R, df64>::value) {
       v = v + df64(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+    } else {
+      v = v + __shfl_xor_sync(0xffffffffu, v, o);
     }
   }
   return v;
@@ -214,6 +218,13 @@ __device__ __forceinline__ R gsum8(R v) {
 template <typename R>
 __device__ __forceinline__ QT<R> gsum8q(QT<R> v) {
   return QT<R>{gsum8(v.w), gsum8(v.x), gsum8(v.y), gsum8(v.z)};
+}
+
+// Device-side choice between two precisions of the same factorisation: gate_mode 1 runs only
+// when *gate < thr, gate_mode 2 only when it is not, 0 always.
+__device__ __forceinline__ bool skip_by_gate(const double* gate, double thr, int gate_mode) {
+  if (gate_mode == 0) return false;
+  return (*gate < thr) != (gate_mode == 1);
 }
 
 // ---------------------------------------------------------------- K1: Cholesky
@@ -229,7 +240,9 @@ __global__ void __launch_bounds__(1024) qchol_kernel(const double* G, int64_t ld
                                                      double* Lg, double* Li, int64_t ldl, int64_t psl,
                                                      int n, int allow_shift, double shift_rows,
                                                      int power_slot, int32_t* status, double* scalars,
-                                                     int fail_bits) {
+                                                     int fail_bits, const double* gate, double thr,
+                                                     int gate_mode) {
+  if (skip_by_gate(gate, thr, gate_mode)) return;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int ntri = n * (n + 1) / 2;
   const QS<R, C> L = QS<R, C>::make(reinterpret_cast<R*>(smem_raw), ntri);   // packed lower triangle
@@ -429,14 +442,17 @@ __global__ void __launch_bounds__(1024) qchol_kernel(const double* G, int64_t ld
 constexpr int kCB = 8;
 template <typename R>
 __device__ __forceinline__ R shfl_r(R v, int src) {
-  if constexpr (std::is_same<R, double>::value) return __shfl_sync(0xffffffffu, v, src);
-  else return df64(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+  if constexpr (std::is_same<R, df64>::value)
+    return df64(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+  else return __shfl_sync(0xffffffffu, v, src);
 }
 template <typename R, bool C>
 __global__ void __launch_bounds__(32 * kCB) qtrinv_cols_kernel(const double* Lg, double* Li, int64_t ldl,
                                                                 int64_t psl, int n,
-                                                                const double* scalars) {
-  if (scalars[kScCholOk] != 1.0) return;
+                                                                const double* scalars,
+                                                                const double* gate, double thr,
+                                                                int gate_mode) {
+  if (skip_by_gate(gate, thr, gate_mode) || scalars[kScCholOk] != 1.0) return;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int c0 = blockIdx.x * kCB, nn = n - c0;
   const int ntri = nn * (nn + 1) / 2;
@@ -509,8 +525,9 @@ __global__ void __launch_bounds__(32 * kCB) qtrinv_cols_kernel(const double* Lg,
 template <typename R>
 __global__ void __launch_bounds__(1024) qpower_kernel(const double* Li, int64_t ldl, int64_t psl,
                                                       int n, int power_slot, double kappa_stop,
-                                                      int32_t* status, double* scalars) {
-  if (scalars[kScCholOk] != 1.0) return;
+                                                      int32_t* status, double* scalars,
+                                                      const double* gate, double thr, int gate_mode) {
+  if (skip_by_gate(gate, thr, gate_mode) || scalars[kScCholOk] != 1.0) return;
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int ntri = n * (n + 1) / 2;
   R* sbase = reinterpret_cast<R*>(smem_raw);
@@ -593,7 +610,9 @@ __global__ void __launch_bounds__(1024) qpower_kernel(const double* Li, int64_t 
       }
       // The next Gram H_{k+1}* H_{k+1} may be formed in s x s space when its rounding error
       // (u kappa^2 relative) stays far below its smallest eigenvalue (~4/kappa): u kappa^3 < 0.04.
-      const double u = std::is_same<R, double>::value ? 1.1102230246251565e-16 : 3.552713678800501e-15;
+      const double u = std::is_same<R, double>::value ? 1.1102230246251565e-16
+                       : std::is_same<R, float>::value  ? 5.9604644775390625e-8
+                                                        : 3.552713678800501e-15;
       scalars[kScGate] = (u * kap * kap * kap < 0.04) ? 1.0 : 0.0;
     }
   }
@@ -614,25 +633,29 @@ template <typename R, bool C>
 cudaError_t launch_all(const double* G, int64_t ldg, int64_t psg, double* Lg, double* Li, int64_t ldl,
                        int64_t psl, int n, int allow_shift, double shift_rows, int power_slot,
                        double kappa_stop, int32_t* status, double* scalars, int fail_bits,
-                       cudaStream_t st) {
+                       cudaStream_t st, const double* gate = nullptr, double thr = 0.0,
+                       int gate_mode = 0) {
   const size_t s1 = smem_chol(n, sizeof(R), C);
   cudaError_t e = cudaFuncSetAttribute(qchol_kernel<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
   if (e != cudaSuccess) return e;
   qchol_kernel<R, C><<<1, 1024, s1, st>>>(G, ldg, psg, Lg, Li, ldl, psl, n, allow_shift, shift_rows,
-                                          power_slot, status, scalars, fail_bits);
+                                          power_slot, status, scalars, fail_bits, gate, thr,
+                                          gate_mode);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t s2 = smem_trinv(n, sizeof(R), C);
   e = cudaFuncSetAttribute(qtrinv_cols_kernel<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
   if (e != cudaSuccess) return e;
-  qtrinv_cols_kernel<R, C><<<(n + kCB - 1) / kCB, 32 * kCB, s2, st>>>(Lg, Li, ldl, psl, n, scalars);
+  qtrinv_cols_kernel<R, C><<<(n + kCB - 1) / kCB, 32 * kCB, s2, st>>>(Lg, Li, ldl, psl, n, scalars,
+                                                                      gate, thr, gate_mode);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (power_slot >= 0 && !C) {
     const size_t s3 = smem_power(n, sizeof(R));
     e = cudaFuncSetAttribute(qpower_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s3);
     if (e != cudaSuccess) return e;
-    qpower_kernel<R><<<1, 1024, s3, st>>>(Li, ldl, psl, n, power_slot, kappa_stop, status, scalars);
+    qpower_kernel<R><<<1, 1024, s3, st>>>(Li, ldl, psl, n, power_slot, kappa_stop, status, scalars,
+                                         gate, thr, gate_mode);
     count_launch();
     e = cudaGetLastError();
   }
@@ -652,9 +675,29 @@ int qchol_inv_max_n() {
 cudaError_t launch_qchol_inv(const double* G, int64_t ldg, int64_t psg, double* Li, int64_t ldl,
                              int64_t psl, int n, int complex_only, int allow_shift, double shift_rows,
                              int power_slot, double kappa_stop, int use_df64, int32_t* status,
-                             double* scalars, int fail_bits, double* Lg, cudaStream_t st) {
+                             double* scalars, int fail_bits, double* Lg, cudaStream_t st,
+                             const double* fp32_gate, double fp32_below) {
   if (n > qchol_inv_max_n() || !Lg) return cudaErrorInvalidValue;
   if (complex_only && power_slot >= 0) return cudaErrorInvalidValue;
+  if (use_df64 && fp32_gate) {
+    // exactly one of the two runs, chosen on the device by *fp32_gate < fp32_below
+    cudaError_t e =
+        complex_only
+            ? launch_all<float, true>(G, ldg, psg, Lg, Li, ldl, psl, n, allow_shift, shift_rows,
+                                      power_slot, kappa_stop, status, scalars, fail_bits, st,
+                                      fp32_gate, fp32_below, 1)
+            : launch_all<float, false>(G, ldg, psg, Lg, Li, ldl, psl, n, allow_shift, shift_rows,
+                                       power_slot, kappa_stop, status, scalars, fail_bits, st,
+                                       fp32_gate, fp32_below, 1);
+    if (e != cudaSuccess) return e;
+    return complex_only
+               ? launch_all<df64, true>(G, ldg, psg, Lg, Li, ldl, psl, n, allow_shift, shift_rows,
+                                        power_slot, kappa_stop, status, scalars, fail_bits, st,
+                                        fp32_gate, fp32_below, 2)
+               : launch_all<df64, false>(G, ldg, psg, Lg, Li, ldl, psl, n, allow_shift, shift_rows,
+                                         power_slot, kappa_stop, status, scalars, fail_bits, st,
+                                         fp32_gate, fp32_below, 2);
+  }
   if (use_df64)
     return complex_only
                ? launch_all<df64, true>(G, ldg, psg, Lg, Li, ldl, psl, n, allow_shift, shift_rows,
