@@ -29,6 +29,11 @@ constexpr double kKappaStop = 1e8;
 // estimate is below this (kappa(P) ~ a few kappa(H), so u32 kappa(P)^2 stays far below 1 and
 // the second pass restores orthogonality; P itself carries FP32-level error).
 constexpr double kFp32Kappa = 30.0;
+// FP32 modes, corrections after the first: the factorisation of G_k = H_k* H_k runs in FP32
+// when the estimate kappa(H_{k-1}) of the previous correction is below this; a correction
+// takes kappa to below its square root (Sec. 3.1), so kappa(G_k) < 1e3 and FP32 rounding
+// perturbs G_k^{-1} by ~6e-5 relative, which changes eps and kappa(H) but not R(H).
+constexpr double kFp32KappaCorr = 1e3;
 
 bool valid_cfg(const qs_config* c) {
   if (!c) return false;
@@ -199,14 +204,15 @@ cudaError_t gram(const Ctx& x, const Mat& A, int64_t rows, int64_t cols, const M
 // kernels.
 cudaError_t chol_inv(const Ctx& x, const Mat& G, const Mat& L, const Mat& Li, int complex_only,
                      int allow_shift, double shift_rows, int slot, int fail_bits,
-                     bool want_L = false, const double* fp32_gate = nullptr) {
+                     bool want_L = false, const double* fp32_gate = nullptr,
+                     double fp32_below = kFp32Kappa) {
   const int s = (int)x.s;
   int32_t* st = x.status();
   double* sc = x.scalars();
   if (s <= qchol_inv_max_n())
     return launch_qchol_inv((const double*)G.p, G.ld, G.ps, (double*)Li.p, Li.ld, Li.ps, s,
                             complex_only, allow_shift, shift_rows, slot, kKappaStop, !x.f64, st, sc,
-                            fail_bits, (double*)L.p, x.st, fp32_gate, kFp32Kappa);
+                            fail_bits, (double*)L.p, x.st, fp32_gate, fp32_below);
   cudaError_t e = launch_qchol((const double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s,
                                complex_only, allow_shift, shift_rows, st, sc, fail_bits, x.st);
   if (e == cudaSuccess && slot >= 0)
@@ -241,7 +247,14 @@ qs_status pseudo_qr(const Ctx& x, int ncorr) {
   Mat Gk = G0;
   // (Alg. 1 step 4) corrections H <- (1-eps) H + eps (H^dagger)* = H ((1-eps) I + eps G^{-1})
   for (int k = 0; k < ncorr; ++k) {
-    QS_CU(chol_inv(x, Gk, L, Li, 0, 0, 2.0 * x.m, kScEps0 + k, kDevRank | kDevStopCorr));
+    const double* lo = nullptr;
+    if (!x.f64 && k > 0) {   // snapshot: the factorisation itself rewrites the kappa estimate
+      QS_CU(cudaMemcpyAsync(sc + kScFp32Gate, sc + kScKappa, sizeof(double), cudaMemcpyDeviceToDevice,
+                            x.st));
+      lo = sc + kScFp32Gate;
+    }
+    QS_CU(chol_inv(x, Gk, L, Li, 0, 0, 2.0 * x.m, kScEps0 + k, kDevRank | kDevStopCorr, false, lo,
+                   kFp32KappaCorr));
     QS_CU(gemm(x, Li, true, Li, Gi, s, s, s, 1.0, 0.0, x.acc_hi(), false));  // G^{-1} = L^{-*} L^{-1}
     QS_CU(launch_qaxpby_eye((double*)Gi.p, Gi.ld, Gi.ps, (double*)M.p, M.ld, M.ps, s, sc,
                             kScEps0 + k, x.st));

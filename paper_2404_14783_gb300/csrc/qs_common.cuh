@@ -31,6 +31,7 @@ enum {
   kScGate = 10,     // 1: next Gram of the corrections by the s x s update, 0: explicit pass
   kScCholOk = 11,   // internal: 1 when the last shared-memory Cholesky succeeded
   kScLamMax = 12,   // internal: lambda_max(G) estimate of the last factorised Gram
+  kScFp32Gate = 13, // internal: kappa snapshot choosing the precision of a factorisation
   kScCount = 16
 };
 
