@@ -32,9 +32,9 @@ FP32_LANES_PER_SM = 128
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the fused
 # sketch kernel on the c2 workload, from one ncu capture (profiles/fused_sketch_c2.md).  It
 # is reported only while the kernel's sources hash to what was captured.
-SKETCH_TRAFFIC = {"bytes": 1.240201e9 + 36.659712e6,
+SKETCH_TRAFFIC = {"bytes": 1.243270e9 + 35.247872e6,
                   "sources": ["qs_sketch_tc.cu", "qs_sketch_tc.cuh", "qs_tc_ptx.cuh"],
-                  "sha256": "749af0ff969fc733383a5d8899921ff08cca23e74fb0d0719976a12f898ddfd7"}
+                  "sha256": "2aeb21b7c76cf7e9f91253c75047f8302417b50898437ff6966b7f2669332479"}
 
 
 def sketch_traffic(prec, workload_name):
