@@ -24,6 +24,6 @@ from .philox import (philox4x32_10, draw_embedding, draw_uniform_f, EMB_GAUSSIAN
                      EMB_RADEMACHER, STREAM_OMEGA, STREAM_PSI, STREAM_PSVD_F)
 from .method import (sketch, thin_qr_complex, pseudo_qr, correction_step, epsilon_rule,
                      pseudo_svd, classify_pairs, qls_solve, qb_core, rel_error,
-                     qmgs2, qsvd_dense, onepass)
+                     qmgs2, qsvd_dense, onepass, truncate, truncated_core)
 
 __all__ = [n for n in dir() if not n.startswith("_")]

@@ -158,6 +158,20 @@ def onepass(A, Omega, Psi, rangefinder="pseudo_qr", n_correction=3, f=None):
 
 
 # ---------------------------------------------------------------- independent references
+def truncate(H, X, r):
+    """Truncation stage (Alg. 4): the QSVD X = U Sigma V* (qsvd_dense), its r leading
+    triples, and H_r = H U_r.  Returns (H_r, sigma_r, V_r), so that the rank-r approximation
+    is H_r diag(sigma_r) V_r* = H floor(X)_r."""
+    U, S, V = qsvd_dense(X)
+    return qmatmul(H, U[:, :, :r]), S[:r], V[:, :, :r]
+
+
+def truncated_core(sigma, V):
+    """diag(sigma) V* (r x n): the factor that multiplies H_r in the truncated approximation."""
+    Vs = qconjT(V)
+    return Vs * np.asarray(sigma)[None, :, None]
+
+
 def _qip(u, v):
     """Quaternion inner product <u, v> = u* v of two (4, m, 1) vectors (Sec. 2.1)."""
     return qmatmul(qconjT(u), v)

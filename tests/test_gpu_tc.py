@@ -131,3 +131,24 @@ def test_tc_c3_shaped_pipeline(pkg):
     assert rel(qs.get("Y").cpu().numpy(), ref["Y"]) < 1e-5
     assert rel(qs.get("W").cpu().numpy(), ref["W"]) < 1e-5
     assert abs(err - ref["err"]) <= 1e-3 * ref["err"], (err, ref["err"])
+
+
+def test_tc_c5_shaped_tall_pipeline(pkg):
+    """The c5 shape class (tall and narrow pure quaternion A, Gaussian test matrices, s = 41,
+    l = 83) at 65536 x 256: sketch parity and the final error within 1e-3 of the oracle's."""
+    m, n, s, l = 65536, 256, 41, 83
+    A = WL.make_decay(m, n, seed=17, rank_cap=256, dtype=np.float32)
+    A[0] = 0.0
+    Ad = torch.as_tensor(A, device="cuda")
+    planes = [None, Ad[1], Ad[2], Ad[3]]
+    qs = pkg.QSketch(m, n, s, l, emb="gaussian", prec="bf16x3", seed=19, pure=True)
+    qs.update(planes, theta=0.0)
+    qs.rangefinder("pseudo_qr", 3)
+    qs.core()
+    err = float(qs.error(planes).item())
+    assert qs.device_status() == 0
+    Om, Psi = _emb(n, s, l, m, 19)
+    ref = O.onepass(A.astype(np.float64), Om, Psi, "pseudo_qr", 3)
+    assert rel(qs.get("Y").cpu().numpy(), ref["Y"]) < 1e-5
+    assert rel(qs.get("W").cpu().numpy(), ref["W"]) < 1e-5
+    assert abs(err - ref["err"]) <= 1e-3 * ref["err"], (err, ref["err"])

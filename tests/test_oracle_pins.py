@@ -426,3 +426,54 @@ def test_c1_pipeline():
     assert best <= r["err"] < 4 * best
     r2 = O.onepass(A, Om, Psi, "pseudo_svd", f=O.draw_uniform_f(2 * w["s"], 0))
     assert abs(r2["err"] - r["err"]) < 1e-3 * r["err"]
+
+
+# ----------------------------------------------------------------- truncation stage (Alg. 4)
+def _c1_like_factors(seed=3):
+    A = WL.make_c1() if seed == 3 else None
+    w = WL.WORKLOADS["c1"]
+    Om = O.draw_embedding(w["n"], w["s"], O.EMB_GAUSSIAN, O.STREAM_OMEGA, seed)
+    Psi = O.draw_embedding(w["l"], w["m"], O.EMB_GAUSSIAN, O.STREAM_PSI, seed)
+    res = O.onepass(A, Om, Psi, "pseudo_qr", 3)
+    return A, res["H"], res["X"]
+
+
+def test_truncation_eckart_young_and_full_rank():
+    """floor(X)_r = U_r Sigma_r V_r* leaves exactly the tail energy of X (Eckart-Young, a
+    closed form from the QSVD), and r = s reproduces H X."""
+    A, H, X = _c1_like_factors()
+    s = X.shape[1]
+    _, S, _ = O.qsvd_dense(X)
+    for r in (1, 5, 10, s):
+        Hr, sig, V = O.truncate(H, X, r)
+        U, _, _ = O.qsvd_dense(X)
+        Xr = O.qmatmul(U[:, :, :r], O.truncated_core(sig, V))
+        tail = np.sqrt(np.sum(S[r:] ** 2))
+        assert abs(O.qnorm(X - Xr) - tail) <= 1e-10 * O.qnorm(X)
+        np.testing.assert_allclose(O.qmatmul(Hr, O.truncated_core(sig, V)), O.qmatmul(H, Xr),
+                                   atol=1e-12 * O.qnorm(H) * O.qnorm(X))
+    Hs, sig, V = O.truncate(H, X, s)
+    assert O.qnorm(O.qmatmul(Hs, O.truncated_core(sig, V)) - O.qmatmul(H, X)) <= 1e-11 * O.qnorm(O.qmatmul(H, X))
+
+
+def test_truncation_error_theorem():
+    """Thm truncationError: ||H floor(X)_r - H X|| <= kappa(H) (||A - HX|| + ||Sigma_2||_F)."""
+    A, H, X = _c1_like_factors()
+    _, SA, _ = O.qsvd_dense(A)
+    sv = np.linalg.svd(O.chi(H), compute_uv=False)
+    kap = sv[0] / sv[-1]
+    HX = O.qmatmul(H, X)
+    for r in (3, 8, 10, 15):
+        Hr, sig, V = O.truncate(H, X, r)
+        lhs = O.qnorm(O.qmatmul(Hr, O.truncated_core(sig, V)) - HX)
+        rhs = kap * (O.qnorm(A - HX) + np.sqrt(np.sum(SA[r:] ** 2)))
+        assert lhs <= rhs, (r, lhs, rhs)
+
+
+def test_truncation_planted_mistake_fails():
+    """Taking the trailing instead of the leading singular triples breaks Eckart-Young."""
+    A, H, X = _c1_like_factors()
+    U, S, V = O.qsvd_dense(X)
+    r = 5
+    Xbad = O.qmatmul(U[:, :, -r:], O.truncated_core(S[-r:], V[:, :, -r:]))
+    assert abs(O.qnorm(X - Xbad) - np.sqrt(np.sum(S[r:] ** 2))) > 1e-3 * O.qnorm(X)
