@@ -33,8 +33,8 @@ FP32_LANES_PER_SM = 128
 # sketch kernel on the c2 workload, from one ncu capture (profiles/fused_sketch_c2.md).  It
 # is reported only while the kernel's sources hash to what was captured.
 SKETCH_TRAFFIC = {"bytes": 1.243270e9 + 35.247872e6,
-                  "sources": ["qs_sketch_tc.cu", "qs_sketch_tc.cuh", "qs_tc_ptx.cuh"],
-                  "sha256": "2aeb21b7c76cf7e9f91253c75047f8302417b50898437ff6966b7f2669332479"}
+                  "sources": ["qs_sketch_tc.cu", "qs_tc_ptx.cuh"],
+                  "sha256": "85a4f1b4c86088310b96ee99772ab9dfeeda9f4c9c8ee7a17fb72c4b6733e47a"}
 
 
 def sketch_traffic(prec, workload_name):
@@ -214,6 +214,17 @@ def run_ours(args, rank, world, local_rank):
     total_ms = max_over_ranks(total_ms, world)
     final_err = float(err_out.item())
     status = qs.device_status()
+    # truncation stage (Alg. 4, rank k) after the step: informational, not in the step time
+    k = int(w.get("k", min(w["s"], 50)))
+    tr0 = torch.cuda.Event(enable_timing=True)
+    tr1 = torch.cuda.Event(enable_timing=True)
+    qs.truncate(k)
+    tr0.record(stream)
+    for _ in range(3):
+        qs.truncate(k)
+    tr1.record(stream)
+    torch.cuda.synchronize()
+    truncate_ms = tr0.elapsed_time(tr1) / 3
 
     # end to end through the public API: pinned host A copied in every step, error read back
     A_host = A.cpu().pin_memory()
@@ -242,7 +253,7 @@ def run_ours(args, rank, world, local_rank):
     result = dict(ms=ms, gbs=gbs, stage_ms=stage_ms, clocks=clocks, launches=launches / args.steps,
                   final_err=final_err, status=status, e2e_ms=e2e_ms, flops=flops, abytes=abytes,
                   cfg=cfg, w=w, e2e_gbs=world * abytes / (e2e_ms * 1e-3) / 1e9,
-                  h2d=A.numel() * A.element_size(), d2h=8)
+                  h2d=A.numel() * A.element_size(), d2h=8, truncate_ms=truncate_ms, trunc_rank=k)
     # FP32 SIMT comparison path at equal error (rank 0 only, device resident)
     if rank == 0 and args.prec != "fp32" and not args.no_compare:
         qs32 = pkg.QSketch(cfg["m"], cfg["n"], cfg["s"], cfg["l"], emb=cfg["emb"], prec="fp32",
@@ -375,6 +386,8 @@ def main():
                       "issued_sketch": products * flops / (sk_ms * 1e-3) / 1e12 if tc else None},
            "sketch_gbs": abytes / (sk_ms * 1e-3) / 1e9,
            "stages_ms": res["stage_ms"], "final_rel_error": res["final_err"],
+           "truncation_stage_ms": {"rank": res["trunc_rank"], "ms": res["truncate_ms"],
+                                   "note": "Alg. 4 after the step, not in ms_per_step"},
            "device_status": res["status"],
            "e2e": {"value": res["e2e_gbs"], "unit": "GB/s", "h2d_bytes_per_step": res["h2d"],
                    "d2h_bytes_per_step": res["d2h"]},

@@ -90,9 +90,12 @@ typedef enum {
   QS_OBJ_H = 4,      /* m x s rangefinder (after qrangefinder)                 */
   QS_OBJ_X = 5,      /* s x n core factor (after qonepass_core)                */
   QS_OBJ_PSIH = 6,   /* l x s product Psi H (after qonepass_core)              */
-  QS_OBJ_SCALARS = 7 /* 16 doubles: [0] last relative error, [1] kappa estimate of H,
+  QS_OBJ_SCALARS = 7, /* 16 doubles: [0] last relative error, [1] kappa estimate of H,
                         [2..4] correction parameters eps_1..eps_3, [5] pseudo-SVD bad
                         pair count t, [6] shift used by Cholesky (0 if none) */
+  QS_OBJ_HR = 8,     /* m x r   H_r = H U_r       (after qtruncate with rank r)      */
+  QS_OBJ_XR = 9,     /* r x n   X_r = Sigma_r V_r* = U_r* X   (after qtruncate)     */
+  QS_OBJ_SIGMA = 10  /* r doubles: the r leading singular values of X (after qtruncate) */
 } qs_object;
 
 /* Element types reported by qsketch_get. */
@@ -164,6 +167,14 @@ QS_API qs_status qrangefinder(qs_handle_t h, int32_t kind, int32_t n_correction,
 /* QB stage (Alg. 3): P = Psi H, then X = P^dagger W through the complex representation
  * (Alg. QLEQ) with a Householder QR of chi_P. */
 QS_API qs_status qonepass_core(qs_handle_t h, void* stream);
+
+/* Truncation stage (Alg. 4): the rank-r approximation A ~= H_r Sigma_r V_r* from the QSVD of
+ * X.  Forms the Gram X X* = L L* (double-float / FP64), the r leading left singular pairs of
+ * L through chi_L (one-sided complex Jacobi), then H_r = H U_r (QS_OBJ_HR), X_r = U_r* X =
+ * Sigma_r V_r* (QS_OBJ_XR) and Sigma_r (QS_OBJ_SIGMA); V_r = X_r* Sigma_r^{-1}.  The error
+ * of the truncated approximation is qs_reconstruct_error_static with H_r and X_r.  Needs
+ * qonepass_core first; 1 <= r <= s (QS_ERR_INVALID otherwise). */
+QS_API qs_status qtruncate(qs_handle_t h, int64_t r, void* stream);
 
 /* Relative error ||A - H X||_F / ||A||_F (Sec. 5) for the full matrix A (same plane
  * conventions as qsketch_update, block = whole matrix).  Writes one double to the

@@ -78,12 +78,15 @@ size_t plan(const qs_config& c, qs_handle_s* h) {
   size_t o_pack = take(pack_bytes);
   size_t o_psvd = take(psvd_work_bytes(c.s));
   size_t o_epack = take(tc_mode(c.prec) ? err_tc_pack_bytes(c.m, c.n, c.s) : 0);
+  // truncation stage: X* (n x s, FP64), H_r (m x s), X_r (s x n), sigma (s)
+  size_t o_trunc = take(align_up(4 * n * s * 8) + align_up(4 * m * s * es) + align_up(4 * s * n * es) +
+                        s * 8);
   if (h) {
     h->esize = (int)es;
     h->off_status = o_status; h->off_scalars = o_scal; h->off_omega = o_om; h->off_psi = o_psi;
     h->off_y = o_y; h->off_w = o_w; h->off_h = o_h; h->off_x = o_x; h->off_gram = o_gram;
     h->off_small = o_small; h->off_p = o_p; h->off_core = o_core; h->off_pack = o_pack;
-    h->off_psvd = o_psvd; h->off_epack = o_epack;
+    h->off_psvd = o_psvd; h->off_epack = o_epack; h->off_trunc = o_trunc;
     h->off_tail = off; h->small_bytes = small_bytes; h->core_bytes = core_bytes;
     h->pack_bytes = pack_bytes;
   }
@@ -121,6 +124,16 @@ struct Ctx {
   Mat H() const { return {h->ws + h->off_h, s, m * s, f64}; }
   Mat X() const { return {h->ws + h->off_x, n, s * n, f64}; }
   Mat T() const { return {h->ws + h->off_gram, s, m * s, 1}; }
+  // truncation stage: X* (n x s FP64), H_r (m x r, ld r), X_r (r x n), sigma (r doubles)
+  Mat XT() const { return {h->ws + h->off_trunc, s, n * s, 1}; }
+  Mat Hr(int64_t r) const { return {h->ws + h->off_trunc + align_up(4 * n * s * 8), r, m * r, f64}; }
+  Mat Xr(int64_t r) const {
+    return {h->ws + h->off_trunc + align_up(4 * n * s * 8) + align_up(4 * m * s * h->esize), n, r * n, f64};
+  }
+  double* sigma() const {
+    return reinterpret_cast<double*>(h->ws + h->off_trunc + align_up(4 * n * s * 8) +
+                                     align_up(4 * m * s * h->esize) + align_up(4 * s * n * h->esize));
+  }
   Mat T2() const { return {h->ws + h->off_gram + 4 * m * s * 8, s, m * s, 1}; }
   Mat small(int i) const {
     return {h->ws + h->off_small + i * align_up(4 * s * s * 8), s, s * s, 1};
@@ -506,6 +519,30 @@ qs_status qonepass_core(qs_handle_t h, void* stream) {
   return core_solve(x);
 }
 
+// Truncation stage (Alg. 4): QSVD of X through the Gram G = X X* = L L* (the left singular
+// vectors and values of X are those of L), one-sided complex Jacobi on chi_L for the r
+// leading pairs U_r, Sigma_r; then H_r = H U_r and X_r = U_r* X = Sigma_r V_r*, so that
+// A ~= H_r X_r = H floor(X)_r.
+qs_status qtruncate(qs_handle_t h, int64_t r, void* stream) {
+  if (!h) return QS_ERR_INVALID;
+  const qs_config& c = h->cfg;
+  if (r < 1 || r > c.s) return QS_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ctx x{h, st, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64};
+  const int s = (int)c.s;
+  const Mat XT = x.XT(), G = x.small(0), L = x.small(1), Li = x.small(2), U = x.small(3);
+  const Mat X = x.X(), H = x.H(), Hr = x.Hr(r), Xr = x.Xr(r);
+  QS_CU(launch_qconjT(X.p, X.f64, X.ld, X.ps, XT.p, 1, XT.ld, XT.ps, s, (int)c.n, st));   // X*
+  QS_CU(gram(x, XT, c.n, s, G));                                                          // X X*
+  QS_CU(chol_inv(x, G, L, Li, 0, 1, 4.0 * c.n, -1, kDevRank, /*want_L=*/true));
+  QS_CU(launch_qsvd_left((const double*)L.p, L.ld, L.ps, s, (int)r, x.h->ws + x.h->off_psvd,
+                         (double*)U.p, U.ld, U.ps, x.sigma(), st));
+  QS_CU(gemm(x, H, false, U, Hr, c.m, r, s, 1.0, 0.0, x.acc_hi(), false));   // H U_r
+  QS_CU(gemm(x, U, true, X, Xr, r, c.n, s, 1.0, 0.0, x.acc_hi(), true));     // U_r* X
+  h->trunc_r = (int)r;
+  return QS_OK;
+}
+
 qs_status qreconstruct_error(qs_handle_t h, const void* const A_planes[4], int64_t lda,
                              double* rel_err_dev, void* stream) {
   if (!h || !planes_ok(h, A_planes)) return QS_ERR_INVALID;
@@ -553,6 +590,12 @@ qs_status qsketch_get(qs_handle_t h, int32_t which, void** dev_ptr, int64_t* ld,
     case QS_OBJ_X: v = x.X(); break;
     case QS_OBJ_PSIH: v = x.P(); break;
     case QS_OBJ_SCALARS: v = {x.scalars(), kScCount, kScCount, 1}; break;
+    case QS_OBJ_HR: if (!h->trunc_r) return QS_ERR_INVALID; v = x.Hr(h->trunc_r); break;
+    case QS_OBJ_XR: if (!h->trunc_r) return QS_ERR_INVALID; v = x.Xr(h->trunc_r); break;
+    case QS_OBJ_SIGMA:
+      if (!h->trunc_r) return QS_ERR_INVALID;
+      v = {x.sigma(), h->trunc_r, h->trunc_r, 1};
+      break;
     default: return QS_ERR_INVALID;
   }
   *dev_ptr = v.p;

@@ -20,8 +20,12 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "qs_sketch_tc.cuh"
 #include "qs_small.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace qs {
 namespace {
@@ -42,15 +46,21 @@ __device__ __forceinline__ C2 cmul_conj_a(C2 a, C2 b) {  // conj(a) * b
 
 // One-sided Jacobi on the columns of the complex rows x cols matrix A (column-major, ld =
 // rows) held in global memory.  Afterwards A's columns are mutually orthogonal; nrm[j]
-// holds their norms.  Executed by the whole CTA.
-__device__ void jacobi_columns(C2* A, int rows, int cols, double* nrm, int* perm, int* flag,
-                               int max_sweeps) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+// holds their norms and perm the descending order.  Executed by the whole cooperative grid:
+// the column pairs of a round-robin round are independent, one warp rotates one pair (held
+// in registers when rows <= 32 kJacRegRows: one L2 round trip per pair), and a grid barrier
+// separates the rounds -- spreading the FP64 rotations over many SMs.  flag: a global word.
+constexpr int kJacRegRows = 8;
+__device__ void jacobi_columns(C2* A, int rows, int cols, double* nrm, int* perm,
+                               volatile int* flag, int max_sweeps) {
+  cg::grid_group grid = cg::this_grid();
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int warp = gtid >> 5, lane = threadIdx.x & 31, nwarps = (gridDim.x * blockDim.x) >> 5;
   const int n = cols + (cols & 1);  // even count for the round-robin tournament
   const double tol = (double)rows * 1.1102230246251565e-16;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) *flag = 0;
-    __syncthreads();
+    if (gtid == 0) *flag = 0;
+    grid.sync();
     for (int round = 0; round < n - 1; ++round) {
       for (int pr = warp; pr < n / 2; pr += nwarps) {
         // round-robin pairing: position 0 fixed, the others rotate
@@ -60,6 +70,49 @@ __device__ void jacobi_columns(C2* A, int rows, int cols, double* nrm, int* perm
         if (q >= cols) continue;
         C2* ap = A + (int64_t)p * rows;
         C2* aq = A + (int64_t)q * rows;
+        if (rows <= 32 * kJacRegRows) {
+          C2 xs[kJacRegRows], ys[kJacRegRows];
+          double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
+#pragma unroll
+          for (int u = 0; u < kJacRegRows; ++u) {
+            const int i = lane + 32 * u;
+            xs[u] = i < rows ? ap[i] : C2{0.0, 0.0};
+            ys[u] = i < rows ? aq[i] : C2{0.0, 0.0};
+          }
+#pragma unroll
+          for (int u = 0; u < kJacRegRows; ++u) {
+            al += xs[u].re * xs[u].re + xs[u].im * xs[u].im;
+            be += ys[u].re * ys[u].re + ys[u].im * ys[u].im;
+            const C2 g = cmul_conj_a(xs[u], ys[u]);
+            gr += g.re;
+            gi += g.im;
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            al += __shfl_xor_sync(0xffffffffu, al, o);
+            be += __shfl_xor_sync(0xffffffffu, be, o);
+            gr += __shfl_xor_sync(0xffffffffu, gr, o);
+            gi += __shfl_xor_sync(0xffffffffu, gi, o);
+          }
+          const double ga = sqrt(gr * gr + gi * gi);
+          if (!(ga > tol * sqrt(al * be)) || al == 0.0 || be == 0.0) continue;
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+          const double er = gr / ga, ei = -gi / ga;  // e^{-i phi}
+#pragma unroll
+          for (int u = 0; u < kJacRegRows; ++u) {
+            const int i = lane + 32 * u;
+            if (i < rows) {
+              const C2 x = xs[u], y = ys[u];
+              const C2 ey{er * y.re - ei * y.im, er * y.im + ei * y.re};
+              ap[i] = C2{c * x.re - sn * ey.re, c * x.im - sn * ey.im};
+              aq[i] = C2{sn * x.re + c * ey.re, sn * x.im + c * ey.im};
+            }
+          }
+          if (lane == 0) *flag = 1;
+          continue;
+        }
         double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
         for (int i = lane; i < rows; i += 32) {
           const C2 x = ap[i], y = aq[i];
@@ -90,11 +143,11 @@ __device__ void jacobi_columns(C2* A, int rows, int cols, double* nrm, int* perm
         }
         if (lane == 0) *flag = 1;
       }
-      __syncthreads();
+      grid.sync();
     }
-    __syncthreads();
-    if (*flag == 0) break;
-    __syncthreads();
+    const int rotated = *flag;
+    grid.sync();   // everyone has read the flag before the next sweep resets it
+    if (rotated == 0) break;
   }
   // column norms and the descending order
   for (int j = warp; j < cols; j += nwarps) {
@@ -107,8 +160,8 @@ __device__ void jacobi_columns(C2* A, int rows, int cols, double* nrm, int* perm
     for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     if (lane == 0) nrm[j] = sqrt(s2);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  grid.sync();
+  if (gtid == 0) {
     for (int j = 0; j < cols; ++j) perm[j] = j;
     for (int j = 0; j < cols; ++j) {  // selection sort (cols <= 2048)
       int best = j;
@@ -117,10 +170,9 @@ __device__ void jacobi_columns(C2* A, int rows, int cols, double* nrm, int* perm
       const int tmp = perm[j]; perm[j] = perm[best]; perm[best] = tmp;
     }
   }
-  __syncthreads();
+  grid.sync();
 }
 
-// quaternion column from a complex 2s-vector u (the map X = u_top - conj(u_bot) j)
 __device__ __forceinline__ void from_comp_col(const C2* u, double scale, int s, double* Z,
                                               int64_t ldz, int64_t psz, int col) {
   for (int i = threadIdx.x & 31; i < s; i += 32) {
@@ -132,17 +184,19 @@ __device__ __forceinline__ void from_comp_col(const C2* u, double scale, int s, 
   }
 }
 
-__global__ void __launch_bounds__(1024) psvd_small_kernel(const double* R, int64_t ldr, int64_t psr,
-                                                          int s, C2* work1, C2* work2, double* nrm,
-                                                          int* perm, double* Z, int64_t ldz, int64_t psz,
-                                                          uint32_t k0, uint32_t k1, double* scalars,
-                                                          int32_t* status) {
-  __shared__ int flag;
-  __shared__ int good;
+__global__ void __launch_bounds__(32) psvd_small_kernel(const double* R, int64_t ldr, int64_t psr,
+                                                         int s, C2* work1, C2* work2, double* nrm,
+                                                         int* perm, int* gwords, double* Z, int64_t ldz,
+                                                         int64_t psz, uint32_t k0, uint32_t k1,
+                                                         double* scalars, int32_t* status) {
+  cg::grid_group grid = cg::this_grid();
+  volatile int* flag = gwords;
+  volatile int* good = gwords + 1;
   const int n2 = 2 * s;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  const int warp = gtid >> 5, nwarps = nthr >> 5;
   // chi_R (column-major 2s x 2s): [[R0, R1], [-conj R1, conj R0]], R0 = Rw + i Rx, R1 = Ry + i Rz
-  for (int e = threadIdx.x; e < n2 * n2; e += blockDim.x) {
+  for (int e = gtid; e < n2 * n2; e += nthr) {
     const int col = e / n2, row = e % n2;
     const int i = row % s, j = col % s;
     const double w = R[0 * psr + (int64_t)i * ldr + j], x = R[1 * psr + (int64_t)i * ldr + j];
@@ -154,10 +208,10 @@ __global__ void __launch_bounds__(1024) psvd_small_kernel(const double* R, int64
     else v = C2{w, -x};
     work1[(int64_t)col * n2 + row] = v;
   }
-  __syncthreads();
-  jacobi_columns(work1, n2, n2, nrm, perm, &flag, 40);
+  grid.sync();
+  jacobi_columns(work1, n2, n2, nrm, perm, flag, 40);
   // classification of pairs (sorted values nrm[perm[.]])
-  if (threadIdx.x == 0) {
+  if (gtid == 0) {
     const double tau = 2.0 * s * 1e3 * 1.1102230246251565e-16;
     const double thr = tau * nrm[perm[0]];
     int g = s;
@@ -168,11 +222,11 @@ __global__ void __launch_bounds__(1024) psvd_small_kernel(const double* R, int64
       if (i < s - 1) ok = ok && (b - nrm[perm[2 * i + 2]]) > thr;
       if (!ok) { g = i; break; }
     }
-    good = g;
+    *good = g;
     scalars[kScBadPairs] = (double)(s - g);
   }
-  __syncthreads();
-  const int g = good, t = s - g;
+  grid.sync();
+  const int g = *good, t = s - g;
   // Z_g: one normalised left vector per good pair
   for (int j = warp; j < g; j += nwarps) {
     const int c = perm[2 * j];
@@ -182,7 +236,7 @@ __global__ void __launch_bounds__(1024) psvd_small_kernel(const double* R, int64
   if (t > 0) {
     // H_b with (H_b)_c = U_b, times diag(f): chi(Z_b diag f) is 2s x 4t
     const int nb = 4 * t;
-    for (int e = threadIdx.x; e < n2 * nb; e += blockDim.x) {
+    for (int e = gtid; e < n2 * nb; e += nthr) {
       const int col = e / n2, row = e % n2;
       const int jb = col % (2 * t);             // column of Z_b
       const int c = perm[2 * g + jb];
@@ -199,8 +253,8 @@ __global__ void __launch_bounds__(1024) psvd_small_kernel(const double* R, int64
       else v = (row < s) ? X1 : C2{X0.re, -X0.im};
       work2[(int64_t)col * n2 + row] = v;
     }
-    __syncthreads();
-    jacobi_columns(work2, n2, nb, nrm + n2, perm + n2, &flag, 40);
+    grid.sync();
+    jacobi_columns(work2, n2, nb, nrm + n2, perm + n2, flag, 40);
     for (int j = warp; j < t; j += nwarps) {
       const int c = perm[n2 + 2 * j];
       const double nv = nrm[n2 + c];
@@ -208,6 +262,41 @@ __global__ void __launch_bounds__(1024) psvd_small_kernel(const double* R, int64
     }
   }
   (void)status;
+}
+
+// Leading r left singular vectors and values of a quaternion s x s matrix L through chi_L
+// (the QSVD through the complex representation, Sec. 2.2): one-sided Jacobi on the columns of
+// chi_L gives U_chi Sigma; the columns come in pairs of equal norm, and the first column of
+// each pair (descending order) is, in compact form, a left singular vector of L.
+__global__ void __launch_bounds__(32) qsvd_left_kernel(const double* L, int64_t ldl, int64_t psl,
+                                                        int s, int r, C2* work, double* nrm,
+                                                        int* perm, int* gwords, double* U, int64_t ldu,
+                                                        int64_t psu, double* sigma) {
+  cg::grid_group grid = cg::this_grid();
+  const int n2 = 2 * s;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  const int warp = gtid >> 5, nwarps = nthr >> 5;
+  // chi_L (column-major 2s x 2s): [[L0, L1], [-conj L1, conj L0]], L0 = Lw + i Lx, L1 = Ly + i Lz
+  for (int e = gtid; e < n2 * n2; e += nthr) {
+    const int col = e / n2, row = e % n2;
+    const int i = row % s, j = col % s;
+    const double w = L[0 * psl + (int64_t)i * ldl + j], x = L[1 * psl + (int64_t)i * ldl + j];
+    const double y = L[2 * psl + (int64_t)i * ldl + j], z = L[3 * psl + (int64_t)i * ldl + j];
+    C2 v;
+    if (row < s && col < s) v = C2{w, x};
+    else if (row < s) v = C2{y, z};
+    else if (col < s) v = C2{-y, z};
+    else v = C2{w, -x};
+    work[(int64_t)col * n2 + row] = v;
+  }
+  grid.sync();
+  jacobi_columns(work, n2, n2, nrm, perm, gwords, 40);
+  for (int j = warp; j < r; j += nwarps) {
+    const int c = perm[2 * j];
+    const double nv = nrm[c];
+    if ((threadIdx.x & 31) == 0) sigma[j] = nv;
+    from_comp_col(work + (int64_t)c * n2, nv > 0.0 ? 1.0 / nv : 0.0, s, U, ldu, psu, j);
+  }
 }
 
 }  // namespace
@@ -223,6 +312,14 @@ size_t psvd_work_bytes(int64_t s) {
   return (size_t)(n2 * n2 + n2 * 4 * s) * sizeof(C2) + (size_t)(2 * n2 + 4 * s) * (sizeof(double) + sizeof(int)) + 1024;
 }
 
+// Grid of the cooperative Jacobi kernels: one warp per block and one block per column pair
+// of a round (up to the SMs available), so each pair has an SM's FP64 pipe to itself.
+static int jacobi_grid(int cols) {
+  int dev = 0, sms = kNumSMs;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, std::min(cols / 2 + 1, sms));
+}
+
 cudaError_t launch_psvd_small(const double* R, int64_t ldr, int64_t psr, int s, void* work,
                               double* Z, int64_t ldz, int64_t psz, uint64_t seed, double* scalars,
                               int32_t* status, cudaStream_t st) {
@@ -231,10 +328,33 @@ cudaError_t launch_psvd_small(const double* R, int64_t ldr, int64_t psr, int s, 
   C2* w2 = w1 + n2 * n2;
   double* nrm = reinterpret_cast<double*>(w2 + n2 * 4 * s);
   int* perm = reinterpret_cast<int*>(nrm + 2 * n2 + 4 * s);
-  psvd_small_kernel<<<1, 1024, 0, st>>>(R, ldr, psr, s, w1, w2, nrm, perm, Z, ldz, psz,
-                                        (uint32_t)seed, (uint32_t)(seed >> 32), scalars, status);
+  int* gwords = perm + 2 * n2 + 4 * s - 2;   // two spare words at the end of perm
+  int si = s;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  void* args[] = {(void*)&R, (void*)&ldr, (void*)&psr, (void*)&si, (void*)&w1, (void*)&w2,
+                  (void*)&nrm, (void*)&perm, (void*)&gwords, (void*)&Z, (void*)&ldz, (void*)&psz,
+                  (void*)&k0, (void*)&k1, (void*)&scalars, (void*)&status};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)psvd_small_kernel,
+                                              dim3(jacobi_grid((int)n2)), dim3(32), args, 0, st);
   count_launch();
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_qsvd_left(const double* L, int64_t ldl, int64_t psl, int s, int r, void* work,
+                             double* U, int64_t ldu, int64_t psu, double* sigma, cudaStream_t st) {
+  const int64_t n2 = 2 * s;
+  C2* w1 = static_cast<C2*>(work);
+  double* nrm = reinterpret_cast<double*>(w1 + n2 * n2 + n2 * 4 * s);
+  int* perm = reinterpret_cast<int*>(nrm + 2 * n2 + 4 * s);
+  int* gwords = perm + 2 * n2 + 4 * s - 2;
+  int si = s, ri = r;
+  void* args[] = {(void*)&L, (void*)&ldl, (void*)&psl, (void*)&si, (void*)&ri, (void*)&w1,
+                  (void*)&nrm, (void*)&perm, (void*)&gwords, (void*)&U, (void*)&ldu, (void*)&psu,
+                  (void*)&sigma};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)qsvd_left_kernel,
+                                              dim3(jacobi_grid((int)n2)), dim3(32), args, 0, st);
+  count_launch();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace qs

@@ -17,4 +17,7 @@ cudaError_t launch_psvd_small(const double* R, int64_t ldr, int64_t psr, int s, 
                               double* Z, int64_t ldz, int64_t psz, uint64_t seed, double* scalars,
                               int32_t* status, cudaStream_t st);
 cudaError_t launch_finalize_err(double* scalars, double* out, cudaStream_t st);
+// truncation stage: leading r left singular vectors U (s x r) and values of the s x s L
+cudaError_t launch_qsvd_left(const double* L, int64_t ldl, int64_t psl, int s, int r, void* work,
+                             double* U, int64_t ldu, int64_t psu, double* sigma, cudaStream_t st);
 }  // namespace qs

@@ -18,7 +18,7 @@ QS_EMB_GAUSSIAN, QS_EMB_RADEMACHER = 0, 1
 QS_PREC_FP64, QS_PREC_FP32, QS_PREC_BF16, QS_PREC_BF16X3 = 0, 1, 2, 3
 QS_RF_PSEUDO_QR, QS_RF_PSEUDO_SVD = 0, 1
 QS_OBJ_Y, QS_OBJ_W, QS_OBJ_OMEGA, QS_OBJ_PSI, QS_OBJ_H, QS_OBJ_X, QS_OBJ_PSIH, \
-    QS_OBJ_SCALARS = range(8)
+    QS_OBJ_SCALARS, QS_OBJ_HR, QS_OBJ_XR, QS_OBJ_SIGMA = range(11)
 QS_DT_F64, QS_DT_F32 = 0, 1
 QS_FLAG_TEST_WITHHOLD_COPY = 1
 
@@ -30,7 +30,7 @@ RANGEFINDERS = {"pseudo_qr": QS_RF_PSEUDO_QR, "pseudo_svd": QS_RF_PSEUDO_SVD}
 ABI_SYMBOLS = ("qsketch_workspace_bytes", "qsketch_create", "qsketch_update", "qrangefinder",
                "qonepass_core", "qreconstruct_error", "qsketch_get", "qs_last_device_error",
                "qsketch_destroy", "qs_status_string", "qs_launch_count", "qs_version",
-               "qs_reconstruct_error_static", "qsketch_update_batched")
+               "qs_reconstruct_error_static", "qsketch_update_batched", "qtruncate")
 
 
 class QSConfig(ctypes.Structure):
@@ -75,9 +75,10 @@ def load_library(path=LIB_PATH):
     lib.qs_reconstruct_error_static.argtypes = [I64, I64, I64, I32, planes, I64, planes, I64,
                                                 planes, I64, VP, VP]
     lib.qsketch_update_batched.argtypes = [I32, P(VP), P(VP), P(I64), VP]
+    lib.qtruncate.argtypes = [VP, I64, VP]
     for name in ("qsketch_create", "qsketch_update", "qrangefinder", "qonepass_core",
                  "qreconstruct_error", "qsketch_get", "qs_last_device_error", "qsketch_destroy",
-                 "qs_reconstruct_error_static", "qsketch_update_batched"):
+                 "qs_reconstruct_error_static", "qsketch_update_batched", "qtruncate"):
         getattr(lib, name).restype = I32
     _lib = lib
     return lib
@@ -247,26 +248,36 @@ class QSketch:
                                            _stream_ptr(stream)), "qreconstruct_error")
         return out
 
+    def truncate(self, r, stream=None):
+        """Truncation stage (Alg. 4): rank-r H_r, X_r = Sigma_r V_r* and Sigma_r, read with
+        get("Hr"), get("Xr"), get("sigma")."""
+        _check(self.lib.qtruncate(self.handle, int(r), _stream_ptr(stream)), "qtruncate")
+        self.trunc_r = int(r)
+
     def device_status(self, stream=None):
         return self.lib.qs_last_device_error(self.handle, _stream_ptr(stream))
 
     def get(self, which):
         """Tensor view (4, rows, cols) of a workspace object (no copy)."""
         names = {"Y": QS_OBJ_Y, "W": QS_OBJ_W, "Omega": QS_OBJ_OMEGA, "Psi": QS_OBJ_PSI,
-                 "H": QS_OBJ_H, "X": QS_OBJ_X, "PsiH": QS_OBJ_PSIH, "scalars": QS_OBJ_SCALARS}
+                 "H": QS_OBJ_H, "X": QS_OBJ_X, "PsiH": QS_OBJ_PSIH, "scalars": QS_OBJ_SCALARS,
+                 "Hr": QS_OBJ_HR, "Xr": QS_OBJ_XR, "sigma": QS_OBJ_SIGMA}
         code = names.get(which, which)
         ptr, ld, ps, dt = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
         _check(self.lib.qsketch_get(self.handle, code, ctypes.byref(ptr), ctypes.byref(ld),
                                     ctypes.byref(ps), ctypes.byref(dt)), "qsketch_get")
         c = self.cfg
+        r = getattr(self, "trunc_r", 0)
         shapes = {QS_OBJ_Y: (c.m, c.s), QS_OBJ_W: (c.l, c.n), QS_OBJ_OMEGA: (c.n, c.s),
                   QS_OBJ_PSI: (c.l, c.m), QS_OBJ_H: (c.m, c.s), QS_OBJ_X: (c.s, c.n),
-                  QS_OBJ_PSIH: (c.l, c.s)}
+                  QS_OBJ_PSIH: (c.l, c.s), QS_OBJ_HR: (c.m, r), QS_OBJ_XR: (r, c.n)}
         dtype = torch.float64 if dt.value == QS_DT_F64 else torch.float32
         esize = 8 if dtype == torch.float64 else 4
         off = ptr.value - self.workspace.data_ptr()
         if code == QS_OBJ_SCALARS:
             return self.workspace[off:off + 16 * 8].view(torch.float64)
+        if code == QS_OBJ_SIGMA:
+            return self.workspace[off:off + ld.value * 8].view(torch.float64)
         rows, cols = shapes[code]
         nel = 3 * ps.value + (rows - 1) * ld.value + cols
         flat = self.workspace[off:off + nel * esize].view(dtype)
