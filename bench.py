@@ -226,26 +226,54 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     truncate_ms = tr0.elapsed_time(tr1) / 3
 
-    # end to end through the public API: pinned host A copied in every step, error read back
+    # end to end through the public API, every step: pinned host A streamed in by row blocks
+    # (qsketch_update_host, resident staging: the copy of block b+1 overlaps the sketch of
+    # block b and A stays on the device for the error pass), the step, the error read back to
+    # the host.  Reported: two staging buffers taken in turn, each with an event after the
+    # error pass that last read it, so one step's copies overlap the previous step's
+    # rangefinder, core and error pass.  One staging buffer (copies wait for the previous
+    # step) and the plain copy-then-step loop are timed beside it.
     A_host = A.cpu().pin_memory()
-    A_dev2 = torch.empty_like(A)
+    n = cfg["n"]
+    staging = [torch.empty(qs.staging_shape(), dtype=A.dtype, device=dev) for _ in range(2)]
+    freed = [torch.cuda.Event(), torch.cuda.Event()]
     err_host = torch.zeros(1, dtype=torch.float64).pin_memory()
-    for _ in range(max(1, args.warmup // 2)):
-        A_dev2.copy_(A_host, non_blocking=True)
-        step(A_in=A_dev2)
-        err_host.copy_(err_out, non_blocking=True)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        A_dev2.copy_(A_host, non_blocking=True)
-        step(A_in=A_dev2)
-        err_host.copy_(err_out, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    del A_dev2, A_host
+
+    def e2e_loop(mode, steps, used):
+        for i in range(steps):
+            j = i & 1 if mode == "pipelined" else 0
+            stg = staging[j]
+            qs.reset(seed=w["seed"] + rank)
+            if mode == "copy":
+                stg[:, :, :n].copy_(A_host, non_blocking=True)
+                qs.update(stg[:, :, :n], theta=0.0)
+            else:
+                qs.update_host(A_host, stg, block_rows=args.stream_rows, theta=0.0,
+                               staging_free=freed[j] if mode == "pipelined" and used[j] else None)
+            qs.rangefinder(args.rangefinder, 3)
+            qs.core()
+            qs.error(stg[:, :, :n], out=err_out)
+            freed[j].record(stream)
+            used[j] = True
+            err_host.copy_(err_out, non_blocking=True)
+
+    e2e = {}
+    for mode in ("pipelined", "streamed", "copy"):
+        used = [False, False]          # both staging buffers have an event once warmed up
+        e2e_loop(mode, max(2, args.warmup), used)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_loop(mode, args.steps, used)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e[mode] = e0.elapsed_time(e1) / args.steps
+        if mode == "pipelined":
+            e2e_err = float(err_host.item())
+    e2e_ms = e2e["pipelined"]
+    e2e_status = qs.device_status()
+    del staging, A_host
 
     flops, abytes = algorithmic(cfg)
     ms = total_ms / args.steps
@@ -253,7 +281,8 @@ def run_ours(args, rank, world, local_rank):
     result = dict(ms=ms, gbs=gbs, stage_ms=stage_ms, clocks=clocks, launches=launches / args.steps,
                   final_err=final_err, status=status, e2e_ms=e2e_ms, flops=flops, abytes=abytes,
                   cfg=cfg, w=w, e2e_gbs=world * abytes / (e2e_ms * 1e-3) / 1e9,
-                  h2d=A.numel() * A.element_size(), d2h=8, truncate_ms=truncate_ms, trunc_rank=k)
+                  h2d=A.numel() * A.element_size(), d2h=8, truncate_ms=truncate_ms, trunc_rank=k,
+                  e2e_modes=e2e, e2e_err=e2e_err, e2e_status=e2e_status)
     # FP32 SIMT comparison path at equal error (rank 0 only, device resident)
     if rank == 0 and args.prec != "fp32" and not args.no_compare:
         qs32 = pkg.QSketch(cfg["m"], cfg["n"], cfg["s"], cfg["l"], emb=cfg["emb"], prec="fp32",
@@ -310,6 +339,8 @@ def main():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--rangefinder", default="pseudo_qr")
     ap.add_argument("--cpu-rows", type=int, default=4096)
+    ap.add_argument("--stream-rows", type=int, default=1024,
+                    help="row-block height of the streamed host update in the e2e loop")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -390,7 +421,12 @@ def main():
                                    "note": "Alg. 4 after the step, not in ms_per_step"},
            "device_status": res["status"],
            "e2e": {"value": res["e2e_gbs"], "unit": "GB/s", "h2d_bytes_per_step": res["h2d"],
-                   "d2h_bytes_per_step": res["d2h"]},
+                   "d2h_bytes_per_step": res["d2h"], "ms_per_step": res["e2e_ms"],
+                   "mode": f"qsketch_update_host, row blocks of {args.stream_rows}, two resident "
+                           "staging buffers in turn (next step's copies overlap this step)",
+                   "one_staging_ms": res["e2e_modes"]["streamed"],
+                   "copy_then_step_ms": res["e2e_modes"]["copy"],
+                   "final_err": res["e2e_err"], "device_status": res["e2e_status"]},
            "gpu_launches": res["launches"], "clocks": res["clocks"]}
     if "fp32" in res:
         out["fp32_path"] = {"sketch_ms": res["fp32"]["sketch_ms"],

@@ -136,10 +136,37 @@ QS_API qs_status qsketch_create(const qs_config* cfg, void* workspace, size_t by
  *     W <- theta W + eta * Psi[:, row0:row0+mb] A_b E_c
  * where E_r, E_c place the block's rows/columns.  theta = 0 overwrites (old contents
  * are not read).  The planes are FP64 for QS_PREC_FP64, FP32 otherwise, 16-byte aligned
- * with lda a multiple of 4 elements for the tensor-core modes. */
+ * with lda a multiple of 4 elements for the tensor-core modes.  Any row0 / col0 is accepted;
+ * in the tensor-core modes a block whose col0 is not a multiple of 4 runs on the FP32 kernels
+ * (its tensor-core operands could not be copied from an aligned address). */
 QS_API qs_status qsketch_update(qs_handle_t h, const void* const A_planes[4], int64_t lda,
                          int64_t row0, int64_t col0, int64_t mb, int64_t nb,
                          double theta, double eta, void* stream);
+
+/* Streamed update from host memory (Sec. 4, streaming by linear updates; the out-of-core mode
+ * of the paper's image experiment): the full-matrix update
+ *     Y <- theta Y + eta A Omega,   W <- theta W + eta Psi A
+ * for A given as four HOST planes (row-major, leading dimension lda >= n; A_host[0] may be
+ * NULL when cfg.pure; page-locked memory lets the copies overlap the sketch).  Row blocks
+ * of block_rows rows are copied into the caller's device staging buffer (256-byte aligned)
+ * on a copy stream the handle creates on first use (with four events; released by
+ * qsketch_destroy), while the previous block is sketched on `stream`.  The copies wait for
+ * the event staging_free (a cudaEvent_t marking the last use of the staging buffer, e.g. the
+ * error pass that read an earlier resident copy), or, when it is NULL, for all work enqueued
+ * on `stream` before the call; with two staging buffers and an event for each, the copies of
+ * one matrix overlap the processing of the previous one.  Staging rows have
+ * the leading dimension ldd = ceil(n / 4) * 4 elements; a host pitch lda == ldd makes each
+ * block's copy one contiguous range (pitched copies run at about half the rate).
+ *   - ring mode: staging_bytes >= 2 * 4 * block_rows * ldd * esize (two block slots);
+ *   - resident mode: staging_bytes >= 4 * m * ldd * esize; block b lands in its rows of a
+ *     full device copy of A (plane p at staging + p * m * ldd * esize), which stays valid
+ *     after the call (e.g. for qreconstruct_error).
+ * esize is 8 for QS_PREC_FP64, 4 otherwise.  QS_ERR_NOMEM if staging is too small for
+ * either mode, QS_ERR_INVALID for bad arguments; the call returns once all copies and
+ * updates are enqueued. */
+QS_API qs_status qsketch_update_host(qs_handle_t h, const void* const A_host[4], int64_t lda,
+                                     int64_t block_rows, void* staging, size_t staging_bytes,
+                                     void* staging_free, double theta, double eta, void* stream);
 
 /* Batched sketches (many independent matrices, Sec. 4.1 applied to each): for i in
  * [0, count), the full-matrix update of handles[i] with theta = 0 and eta = 1, i.e.

@@ -440,8 +440,10 @@ qs_status qsketch_update(qs_handle_t h, const void* const A_planes[4], int64_t l
   }
   if (mb == 0 || nb == 0) return QS_OK;
   if (tc_mode(c.prec)) {
+    // a column offset that is not a multiple of 4 cannot be aligned for the tensor-core
+    // operands' copies: that block runs on the FP32 kernels below
     const qs_status ts = tc_sketch_update(*h, A_planes, lda, row0, col0, mb, nb, eta, st);
-    return ts;
+    if (ts != QS_ERR_UNSUPPORTED || (col0 & 3) == 0) return ts;
   }
   const Mat Y = x.Y(), W = x.W(), Om = x.omega(), Ps = x.psi();
   const int es = h->esize;
@@ -621,7 +623,85 @@ qs_status qs_last_device_error(qs_handle_t h, void* stream) {
 
 qs_status qsketch_destroy(qs_handle_t h) {
   if (!h) return QS_ERR_INVALID;
+  if (h->copy_stream) {
+    cudaStreamSynchronize(h->copy_stream);
+    cudaEventDestroy(h->ev_start);
+    for (int i = 0; i < 2; ++i) {
+      cudaEventDestroy(h->ev_copied[i]);
+      cudaEventDestroy(h->ev_done[i]);
+    }
+    cudaStreamDestroy(h->copy_stream);
+  }
   delete h;
+  return QS_OK;
+}
+
+// Full-matrix update from host memory (Sec. 4, streaming by linear updates): row blocks of
+// A are copied into the device staging buffer on the handle's copy stream while the
+// previous block is sketched on `stream`; events order the two.  Staging is either a ring of
+// two block slots or, when it holds all of A, a resident copy that stays valid afterwards.
+qs_status qsketch_update_host(qs_handle_t h, const void* const A_host[4], int64_t lda,
+                              int64_t block_rows, void* staging, size_t staging_bytes,
+                              void* staging_free, double theta, double eta, void* stream) {
+  if (!h || !planes_ok(h, A_host) || !staging || block_rows < 1) return QS_ERR_INVALID;
+  const qs_config& c = h->cfg;
+  if (lda < c.n || !std::isfinite(theta) || !std::isfinite(eta)) return QS_ERR_INVALID;
+  if (reinterpret_cast<uintptr_t>(staging) & 255) return QS_ERR_INVALID;
+  const int64_t es = h->esize, ldd = (c.n + 3) / 4 * 4;            // staging rows: 16-byte pitch
+  const int64_t br = std::min<int64_t>(block_rows, c.m);
+  const size_t slot_bytes = (size_t)4 * br * ldd * es;
+  const size_t full_bytes = (size_t)4 * c.m * ldd * es;
+  const bool resident = staging_bytes >= full_bytes;
+  if (!resident && staging_bytes < 2 * slot_bytes) return QS_ERR_NOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!h->copy_stream) {
+    if (cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return QS_ERR_CUDA;
+    bool ok = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < 2; ++i) {
+      ok = ok && cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming) == cudaSuccess;
+      ok = ok && cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) return QS_ERR_CUDA;
+  }
+  // the staging buffer may still be read by earlier work: by default everything enqueued on
+  // `stream` so far, else what the caller's event covers (copies may then start early)
+  cudaEvent_t free_ev = static_cast<cudaEvent_t>(staging_free);
+  if (!free_ev) {
+    QS_CU(cudaEventRecord(h->ev_start, st));
+    free_ev = h->ev_start;
+  }
+  QS_CU(cudaStreamWaitEvent(h->copy_stream, free_ev, 0));
+  char* stage = static_cast<char*>(staging);
+  const int64_t nblocks = (c.m + br - 1) / br;
+  for (int64_t b = 0; b < nblocks; ++b) {
+    const int64_t row0 = b * br, rows = std::min<int64_t>(br, c.m - row0);
+    const int slot = (int)(b & 1);
+    // plane p of this block: resident -> its rows of the full copy; ring -> its slot
+    auto dst_plane = [&](int p) -> char* {
+      return resident ? stage + ((size_t)p * c.m * ldd + (size_t)row0 * ldd) * es
+                      : stage + (size_t)slot * slot_bytes + (size_t)p * br * ldd * es;
+    };
+    if (!resident && b >= 2) QS_CU(cudaStreamWaitEvent(h->copy_stream, h->ev_done[slot], 0));
+    for (int p = 0; p < 4; ++p) {
+      if (!A_host[p]) continue;
+      const char* src = static_cast<const char*>(A_host[p]) + (size_t)row0 * lda * es;
+      if (lda == ldd)   // equal pitches: the block is one contiguous range (the faster copy)
+        QS_CU(cudaMemcpyAsync(dst_plane(p), src, (size_t)rows * ldd * es, cudaMemcpyHostToDevice,
+                              h->copy_stream));
+      else
+        QS_CU(cudaMemcpy2DAsync(dst_plane(p), ldd * es, src, lda * es, c.n * es, rows,
+                                cudaMemcpyHostToDevice, h->copy_stream));
+    }
+    QS_CU(cudaEventRecord(h->ev_copied[slot], h->copy_stream));
+    QS_CU(cudaStreamWaitEvent(st, h->ev_copied[slot], 0));
+    const void* blk[4];
+    for (int p = 0; p < 4; ++p) blk[p] = A_host[p] ? dst_plane(p) : nullptr;
+    const int64_t ldb = ldd;
+    const qs_status r = qsketch_update(h, blk, ldb, row0, 0, rows, c.n, b == 0 ? theta : 1.0, eta, stream);
+    if (r != QS_OK) return r;
+    if (!resident) QS_CU(cudaEventRecord(h->ev_done[slot], st));
+  }
   return QS_OK;
 }
 

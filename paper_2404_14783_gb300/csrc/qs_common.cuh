@@ -92,6 +92,9 @@ struct qs_handle_s {
   // forms Psi H in the FP64 class in the FP32 modes
   int h_well_conditioned;
   int trunc_r;          // rank of the last truncation stage (0: none yet)
+  // host-input streaming (qsketch_update_host): copy stream and events, created on first use
+  cudaStream_t copy_stream;
+  cudaEvent_t ev_start, ev_copied[2], ev_done[2];
   int32_t* d_status() const { return reinterpret_cast<int32_t*>(ws + off_status); }
   double* d_scalars() const { return reinterpret_cast<double*>(ws + off_scalars); }
 };

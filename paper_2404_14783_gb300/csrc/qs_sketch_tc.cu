@@ -60,6 +60,7 @@ __constant__ int8_t kWSign[4][4] = {{1, -1, -1, -1}, {1, 1, 1, -1}, {1, -1, 1, 1
 
 struct TcParams {
   int mb, nb, row0, col0;
+  int rsh, csh;  // row0 / col0 (multiples of 8 here) + rsh / csh = the block's first row / column
   int tiles_m, tiles_n;
   int s, l, NS, MT, LS;
   int YPW;   // output planes per Y wave: 2 when 2 NS <= 256, else 1 (then Omega is staged in
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (t_local > 0 && !wait_bar(&sh->a_free, (t_local - 1) & 1, sh, p.status)) break;
         if (!(p.withhold && t_local == 0)) {
           mbar_expect_tx(&sh->a_full, nplanes_a * 32768u);
-          for (int q = p0; q < 4; ++q) tma_load_2d(sA + q * 32768, tA(q), tj * kBN, ti * kBM, &sh->a_full);
+          for (int q = p0; q < 4; ++q) tma_load_2d(sA + q * 32768, tA(q), tj * kBN - p.csh, ti * kBM - p.rsh, &sh->a_full);
           a_outstanding = true;
           ++a_fills;
         }
@@ -365,11 +366,12 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (prow < p.l) {
                 for (int k = 0; k < 16; k += 4) {
                   const int col = cbase + c16 + k;
-                  if (wvec && col + 3 < p.nb) {
+                  if (col < p.csh) continue;   // csh is 0 or 4: whole groups of 4 lie before it
+                  if (wvec && col + 3 < p.nb + p.csh) {
                     red_v4(wrow + c16 + k, p.eta * v[k], p.eta * v[k + 1], p.eta * v[k + 2], p.eta * v[k + 3]);
                   } else {
                     for (int u = 0; u < 4; ++u)
-                      if (col + u < p.nb) atomicAdd(wrow + c16 + k + u, p.eta * v[k + u]);
+                      if (col + u < p.nb + p.csh) atomicAdd(wrow + c16 + k + u, p.eta * v[k + u]);
                   }
                 }
               }
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int c16 = 0; c16 < p.NS; c16 += 16) {
               float v[16];
               tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + hcol + (uint32_t)(j * p.NS + c16), v);
-              if (arow < p.mb) {
+              if (arow >= p.rsh && arow < p.mb + p.rsh) {
                 for (int k = 0; k < 16; k += 4) {
                   const int col = c16 + k;
                   if (col + 3 < p.s) {
@@ -543,10 +545,17 @@ qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t
   if (!make_map(&tPsi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ps, c.m, 4 * 2 * g.LS, g.ldp, 64, 128,
                 CU_TENSOR_MAP_SWIZZLE_128B))
     return QS_ERR_CUDA;
+  // TMA x coordinates of the BF16 Psi / Omega operands must be multiples of 8 elements (16
+  // bytes): the tiles start at row0 / col0 rounded down to 8, and the A tile is loaded from y =
+  // -rsh (x = -csh), which the copy fills with zeros, so the extra rows / columns add nothing
+  // and the epilogue skips them.  A's x must itself stay 16-byte aligned, so csh is 0 or 4.
+  const int rsh = (int)(row0 & 7), csh = (int)(col0 & 7);
+  if (csh & 3) return QS_ERR_UNSUPPORTED;
   TcParams prm{};
-  prm.mb = (int)mb; prm.nb = (int)nb; prm.row0 = (int)row0; prm.col0 = (int)col0;
-  prm.tiles_m = (int)((mb + kBM - 1) / kBM);
-  prm.tiles_n = (int)((nb + kBN - 1) / kBN);
+  prm.mb = (int)mb; prm.nb = (int)nb; prm.row0 = (int)(row0 - rsh); prm.col0 = (int)(col0 - csh);
+  prm.rsh = rsh; prm.csh = csh;
+  prm.tiles_m = (int)((mb + rsh + kBM - 1) / kBM);
+  prm.tiles_n = (int)((nb + csh + kBN - 1) / kBN);
   prm.s = (int)c.s; prm.l = (int)c.l; prm.NS = (int)g.NS; prm.LS = (int)g.LS;
   prm.MT = (int)(g.LS / 128);
   prm.YPW = ypw;

@@ -30,7 +30,8 @@ RANGEFINDERS = {"pseudo_qr": QS_RF_PSEUDO_QR, "pseudo_svd": QS_RF_PSEUDO_SVD}
 ABI_SYMBOLS = ("qsketch_workspace_bytes", "qsketch_create", "qsketch_update", "qrangefinder",
                "qonepass_core", "qreconstruct_error", "qsketch_get", "qs_last_device_error",
                "qsketch_destroy", "qs_status_string", "qs_launch_count", "qs_version",
-               "qs_reconstruct_error_static", "qsketch_update_batched", "qtruncate")
+               "qs_reconstruct_error_static", "qsketch_update_batched", "qtruncate",
+               "qsketch_update_host")
 
 
 class QSConfig(ctypes.Structure):
@@ -76,9 +77,11 @@ def load_library(path=LIB_PATH):
                                                 planes, I64, VP, VP]
     lib.qsketch_update_batched.argtypes = [I32, P(VP), P(VP), P(I64), VP]
     lib.qtruncate.argtypes = [VP, I64, VP]
+    lib.qsketch_update_host.argtypes = [VP, planes, I64, I64, VP, ctypes.c_size_t, VP, D, D, VP]
     for name in ("qsketch_create", "qsketch_update", "qrangefinder", "qonepass_core",
                  "qreconstruct_error", "qsketch_get", "qs_last_device_error", "qsketch_destroy",
-                 "qs_reconstruct_error_static", "qsketch_update_batched", "qtruncate"):
+                 "qs_reconstruct_error_static", "qsketch_update_batched", "qtruncate",
+               "qsketch_update_host"):
         getattr(lib, name).restype = I32
     _lib = lib
     return lib
@@ -247,6 +250,38 @@ class QSketch:
         _check(self.lib.qreconstruct_error(self.handle, ptrs, ld, ctypes.c_void_p(out.data_ptr()),
                                            _stream_ptr(stream)), "qreconstruct_error")
         return out
+
+    def staging_shape(self):
+        """(4, m, ldd) of a resident staging copy for update_host (ldd = ceil(n / 4) * 4)."""
+        c = self.cfg
+        return (4, c.m, (c.n + 3) // 4 * 4)
+
+    def update_host(self, A_host, staging, block_rows=1024, theta=0.0, eta=1.0, staging_free=None,
+                    stream=None):
+        """Full-matrix update from host memory (qsketch_update_host).  A_host: (4, m, n) CPU
+        tensor (pinned for overlap) or a list of four planes (the first may be None when
+        pure); staging: CUDA tensor -- a resident copy of shape staging_shape() (A stays on
+        the device afterwards) or at least two blocks of block_rows rows; staging_free: a
+        recorded torch.cuda.Event after which staging may be overwritten (default: all work
+        enqueued on the stream so far)."""
+        want = torch.float64 if self.f64 else torch.float32
+        mats = [A_host[p] for p in range(4)] if isinstance(A_host, torch.Tensor) else list(A_host)
+        ptrs = (ctypes.c_void_p * 4)()
+        ld = None
+        for p, t in enumerate(mats):
+            if t is None:
+                ptrs[p] = None
+                continue
+            if t.is_cuda or t.dtype != want or t.stride(1) != 1:
+                raise ValueError(f"host plane {p} must be a CPU {want} row-major matrix")
+            ld = t.stride(0)
+            ptrs[p] = t.data_ptr()
+        nbytes = staging.numel() * staging.element_size()
+        ev = ctypes.c_void_p(staging_free.cuda_event) if staging_free is not None else None
+        return _check(self.lib.qsketch_update_host(self.handle, ptrs, ld, int(block_rows),
+                                                   ctypes.c_void_p(staging.data_ptr()), nbytes, ev,
+                                                   theta, eta, _stream_ptr(stream)),
+                      "qsketch_update_host")
 
     def truncate(self, r, stream=None):
         """Truncation stage (Alg. 4): rank-r H_r, X_r = Sigma_r V_r* and Sigma_r, read with
