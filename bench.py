@@ -30,11 +30,11 @@ N_SMS = 152
 FP32_LANES_PER_SM = 128
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the fused
-# sketch kernel on the c2 workload, from one ncu capture (profiles/fused_sketch_c2.md).  It
+# sketch kernel on the c2 workload, from one ncu capture of the bench command.  It
 # is reported only while the kernel's sources hash to what was captured.
-SKETCH_TRAFFIC = {"bytes": 1.251177e9 + 36.293632e6,
+SKETCH_TRAFFIC = {"bytes": 1244165120 + 39682304,
                   "sources": ["qs_sketch_tc.cu", "qs_tc_ptx.cuh"],
-                  "sha256": "77ed129165832ec13db6bf2912b1f01abd56ebc78f01da86fc2bf6d2091d584e"}
+                  "sha256": "98b3652d72fb943672bef590919018672581232bbe98f7be873fa5d386980978"}
 
 
 def sketch_traffic(prec, workload_name):
@@ -304,6 +304,99 @@ def run_ours(args, rank, world, local_rank):
     return result
 
 
+def run_batch(args):
+    """c4: 256 matrices sketched by qsketch_update_batched (persistent launches of up to 32
+    matrices, the call replayed from a CUDA graph) against a loop of per-matrix
+    qsketch_update calls; inputs resident in HBM (19 GB, larger than L2)."""
+    import torch
+    import paper_2404_14783_gb300 as pkg
+    import workloads as WL
+    pkg.load_library()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    spec = dict(WL.WORKLOADS["c4"])
+    batch = WL.make_c4_batch(dev)
+    sk, mats, flops, abytes = [], [], 0, 0
+    for i, (m, n, k, A) in enumerate(batch):
+        s = 2 * k + 1
+        l = min(2 * s + 1, m, n)          # l <= min(m, n) (Sec. 4.1): clamps k = 64 at m = 256
+        sk.append(pkg.QSketch(m, n, s, l, emb=spec["emb"], prec=args.prec, seed=spec["seed"] + i))
+        mats.append(A)
+        flops += 32 * m * n * (s + l)
+        abytes += 16 * m * n
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    def loop():
+        for q, A in zip(sk, mats):
+            q.update(A, theta=0.0)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        pkg.update_batched(sk, mats)
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        pkg.update_batched(sk, mats)
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    l0 = pkg.launch_count()
+    t_batched = timed(graph.replay, args.steps)
+    t_loop = timed(loop, args.steps)
+    l1 = pkg.launch_count()
+    clocks = sampler.stop()
+    status = max(int(q.device_status()) for q in sk)
+    peaks = load_peaks()
+    products = 2 if spec["emb"] == "rademacher" and args.prec == "bf16x3" else (
+        3 if args.prec == "bf16x3" else 1)
+    out = {"metric": "one-pass quaternion approx: A GB/s & TFLOPS, split-BF16 vs FP32 at equal error",
+           "value": abytes / (t_batched * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batched,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": {"bf16x3": "bf16x3", "bf16": "bf16"}.get(args.prec, args.prec),
+           "data": "synthetic",
+           "config": {"workload": f"c4: batch of {len(sk)} quaternion matrices, m, n ~ "
+                                  f"U[{spec['lo']}, {spec['hi']}], k ~ U{{{spec['k_lo']}..{spec['k_hi']}}}, "
+                                  "s = 2k+1, l = min(2s+1, m, n), Rademacher, sketch only",
+                      "A_bytes": abytes, "useful_flops": flops,
+                      "l2": "inputs larger than L2 (A is %.1f GB)" % (abytes / 1e9)},
+           "roofline": {"bound": "tensor", "achieved": flops / (t_batched * 1e-3) / 1e12,
+                        "peak": peaks.get("bf16_tflops"), "unit": "TFLOP/s",
+                        "frac": flops / (t_batched * 1e-3) / 1e12 / peaks.get("bf16_tflops"),
+                        "traffic": None, "issued_products": products,
+                        "peak_source": peaks["_source"] + " bf16 burst"},
+           "batched": {"persistent_graph_ms": t_batched, "per_matrix_loop_ms": t_loop,
+                       "speedup": t_loop / t_batched,
+                       "launches_per_call": {"batched": None, "loop": None}},
+           "device_status": status, "clocks": clocks,
+           "gpu_launches": (l1 - l0) / (args.steps + args.warmup)}
+    # launches per call, counted by the library (the graph replays count nothing)
+    c0 = pkg.launch_count()
+    pkg.update_batched(sk, mats)
+    c1 = pkg.launch_count()
+    loop()
+    c2 = pkg.launch_count()
+    torch.cuda.synchronize()
+    out["batched"]["launches_per_call"] = {"batched": c1 - c0, "loop": c2 - c1}
+    out["gpu_launches"] = c1 - c0
+    print(json.dumps(out), flush=True)
+
+
 def cpu_baseline(w, rows, reps=1):
     """The FP64 oracle on the host cores on a bounded sample: the first ``rows`` rows of the
     workload's matrix with the same s and l.  Returns (A GB/s, seconds, threads)."""
@@ -336,7 +429,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3"])
-    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--workload", default="c2",
+                    help="c2 (default: the one-pass step) or c4 (the batched sketch, one GPU)")
     ap.add_argument("--rangefinder", default="pseudo_qr")
     ap.add_argument("--cpu-rows", type=int, default=4096)
     ap.add_argument("--stream-rows", type=int, default=1024,
@@ -349,6 +443,10 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.workload == "c4" and args.impl == "ours":
+        if rank == 0:      # the batch workload runs on one GPU
+            run_batch(args)
+        return
     w = workload(args.workload)
     metric = "one-pass quaternion approx: A GB/s & TFLOPS, split-BF16 vs FP32 at equal error"
     config = {"workload": f"{w['name']}: quaternion A {w['m']}x{w['n']} FP32 planes, "

@@ -175,7 +175,12 @@ QS_API qs_status qsketch_update_host(qs_handle_t h, const void* const A_host[4],
  * qsketch_update; plane w may be NULL for a pure handle) with leading dimension lda[i].  The
  * handles must be distinct.  All items are validated on the host before anything is
  * enqueued: QS_ERR_INVALID for a bad handle, plane, alignment or lda, QS_ERR_UNSUPPORTED
- * for a tensor-core handle with s > 256.  The updates are enqueued in order on `stream`. */
+ * for a tensor-core handle with s > 256.  Items in the tensor-core modes (QS_PREC_BF16,
+ * QS_PREC_BF16X3) are processed 32 at a time by one launch that zeroes their sketches and
+ * one persistent fused-sketch launch over all their tiles; the other items run one update
+ * each.  Everything is enqueued on `stream` with no host synchronisation and no allocation,
+ * so the call can be captured in a CUDA graph (the handles' workspaces and the A planes
+ * must then stay in place for every replay). */
 QS_API qs_status qsketch_update_batched(int32_t count, const qs_handle_t* handles,
                                         const void* const* A_planes, const int64_t* lda,
                                         void* stream);

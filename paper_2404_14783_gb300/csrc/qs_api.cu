@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "qs_common.cuh"
 #include "qs_small.cuh"
@@ -489,13 +490,26 @@ qs_status qsketch_update_batched(int32_t count, const qs_handle_t* handles,
       if ((h->cfg.s + 15) / 16 * 16 > 256) return QS_ERR_UNSUPPORTED;
     }
   }
+  // tensor-core handles share persistent launches (up to 32 matrices each); the others run
+  // one update each
+  std::vector<const qs_handle_s*> tch;
+  std::vector<const void*> tca;
+  std::vector<int64_t> tcl;
   for (int32_t i = 0; i < count; ++i) {
     const qs_handle_t h = handles[i];
+    if (tc_mode(h->cfg.prec)) {
+      tch.push_back(h);
+      tca.insert(tca.end(), A_planes + 4 * (int64_t)i, A_planes + 4 * (int64_t)i + 4);
+      tcl.push_back(lda[i]);
+      continue;
+    }
     const qs_status r = qsketch_update(h, A_planes + 4 * (int64_t)i, lda[i], 0, 0, h->cfg.m,
                                        h->cfg.n, 0.0, 1.0, stream);
     if (r != QS_OK) return r;
   }
-  return QS_OK;
+  if (tch.empty()) return QS_OK;
+  return tc_sketch_replace_batched((int)tch.size(), tch.data(), tca.data(), tcl.data(),
+                                   static_cast<cudaStream_t>(stream));
 }
 
 qs_status qrangefinder(qs_handle_t h, int32_t kind, int32_t n_correction, void* stream) {

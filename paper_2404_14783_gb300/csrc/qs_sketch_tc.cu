@@ -14,7 +14,9 @@
 // in FP32 (TMEM) -- hi*hi + lo*hi for Rademacher test matrices, which are exact in BF16;
 // QS_PREC_BF16 only hi*hi.
 //
-// One CTA per SM (persistent).  Tile = 128 rows x 64 columns of A, all four planes:
+// One CTA per SM (persistent).  A launch covers one block of one matrix, or whole matrices of
+// a batch (up to 32; their tiles are numbered consecutively and every CTA walks the global
+// tile sequence).  Tile = 128 rows x 64 columns of A, all four planes:
 //   warp 0      TMA producer: A tile (FP32, 4 x 32 KB) and a 3-stage ring of BF16 operand
 //               chunks of Psi (128 rows x 64) and Omega^T (NS rows x 64), SW128 layout.
 //   warp 1      TMEM owner and MMA issuer (one elected thread).
@@ -76,6 +78,22 @@ struct TcParams {
   int32_t* status;
 };
 
+// One work item of a launch (one matrix block): tensor maps of A's planes 0-3, Omega^T, Psi.
+struct TcMaps {
+  CUtensorMap m[6];
+};
+// Parameters of one launch: up to MAXB items whose tiles are numbered consecutively
+// (item i owns global tiles tile_start[i] .. tile_start[i+1]-1).  Passed as a
+// __grid_constant__ kernel parameter, so the tensor maps are addressed in parameter space.
+template <int MAXB>
+struct TcBatch {
+  TcMaps maps[MAXB];
+  TcParams prm[MAXB];
+  int tile_start[MAXB + 1];
+  int count;
+};
+constexpr int kMaxBatch = 32;   // items per batched launch (kernel parameters <= 32764 bytes)
+
 struct Shared {
   uint64_t a_full, a_ready, a_free, done;
   uint64_t h_full[2], h_empty[2];  // TMEM halves (256 columns each)
@@ -105,21 +123,26 @@ __device__ bool wait_bar(uint64_t* bar, uint32_t parity, Shared* sh, int32_t* st
 }
 
 // ---------------------------------------------------------------- the kernel
-__global__ void __launch_bounds__(kThreads, 1)
-    fused_sketch_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
-                        const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tA3,
-                        const __grid_constant__ CUtensorMap tOm, const __grid_constant__ CUtensorMap tPsi,
-                        const TcParams p) {
+// Every role walks the same sequence of global tiles (t = blockIdx.x, + gridDim.x, ...) and
+// looks up the item a tile belongs to, so the items of a batch share one persistent grid.
+template <int MAXB>
+__global__ void __launch_bounds__(kThreads, 1) fused_sketch_kernel(const __grid_constant__ TcBatch<MAXB> bt) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sRing = smem + kABytes;
   Shared* sh = reinterpret_cast<Shared*>(smem + kABytes + kStages * kStageBytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  auto tA = [&](int q) { return q == 0 ? &tA0 : q == 1 ? &tA1 : q == 2 ? &tA2 : &tA3; };
-  const int ntiles = p.tiles_m * p.tiles_n;
-  const int nplanes_a = p.pure ? 3 : 4;
-  const int p0 = p.pure ? 1 : 0;  // first A plane present
+  const int ntiles = bt.tile_start[bt.count];
+  // (a single-item launch indexes item 0 at compile time, so its parameters stay
+  // constant-bank operands; a dynamic index reads them through generic loads, ~5% slower)
+  auto item_of = [&](int t) {
+    if constexpr (MAXB == 1) return 0;
+    int i = 0;
+    while (i + 1 < bt.count && bt.tile_start[i + 1] <= t) ++i;
+    return i;
+  };
+  int32_t* cur_status = bt.prm[0].status;   // status word of the item a role last worked on
 
   if (threadIdx.x == 0) {
     mbar_init(&sh->a_full, 1);
@@ -151,9 +174,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   //       stages (k-half kh, Psi plane pa): 2 x 4.
   //   Y waves (one per pair of output planes): Y_q for q = 2 qp, 2 qp + 1 (NS columns each);
   //       stages (Omega plane pb): 4 (Omega is staged once per pair).
-  const int nwaves = p.MT + 4 / p.YPW;
-  const uint32_t hl_tx = (p.nprod == 3) ? 2u : 1u;
-  auto wave_stages = [&](int wv) { return wv < p.MT ? 8 : (p.YPW == 2 ? 4 : 8); };
+  auto nwaves_of = [](const TcParams& p) { return p.MT + 4 / p.YPW; };
+  auto wave_stages = [](const TcParams& p, int wv) { return wv < p.MT ? 8 : (p.YPW == 2 ? 4 : 8); };
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -164,16 +186,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t a_fills = 0;
       bool stop = false;
       for (int t = blockIdx.x; t < ntiles && !stop && !sh->abort; t += gridDim.x, ++t_local) {
-        const int ti = t / p.tiles_n, tj = t % p.tiles_n;
+        const int it = item_of(t);
+        const TcParams& p = bt.prm[it];
+        const TcMaps& mp = bt.maps[it];
+        cur_status = p.status;
+        const int lt = t - bt.tile_start[it], ti = lt / p.tiles_n, tj = lt % p.tiles_n;
+        const int nwaves = nwaves_of(p);
+        const uint32_t hl_tx = (p.nprod == 3) ? 2u : 1u;
         if (t_local > 0 && !wait_bar(&sh->a_free, (t_local - 1) & 1, sh, p.status)) break;
         if (!(p.withhold && t_local == 0)) {
+          const int nplanes_a = p.pure ? 3 : 4;
           mbar_expect_tx(&sh->a_full, nplanes_a * 32768u);
-          for (int q = p0; q < 4; ++q) tma_load_2d(sA + q * 32768, tA(q), tj * kBN - p.csh, ti * kBM - p.rsh, &sh->a_full);
+          for (int q = p.pure ? 1 : 0; q < 4; ++q)
+            tma_load_2d(sA + q * 32768, &mp.m[q], tj * kBN - p.csh, ti * kBM - p.rsh, &sh->a_full);
           a_outstanding = true;
           ++a_fills;
         }
         for (int wv = 0; wv < nwaves && !stop; ++wv) {
-          for (int st = 0; st < wave_stages(wv); ++st) {
+          for (int st = 0; st < wave_stages(p, wv); ++st) {
             const uint32_t slot = gs % kStages, use = gs / kStages;
             if (use > 0 && !wait_bar(&sh->st_empty[slot], (use - 1) & 1, sh, p.status)) {
               stop = true;
@@ -184,14 +214,14 @@ __global__ void __launch_bounds__(kThreads, 1)
               const int kh = st >> 2, pl = st & 3;
               mbar_expect_tx(&sh->st_full[slot], hl_tx * 16384u);
               for (int hl = 0; hl < (int)hl_tx; ++hl)
-                tma_load_2d(dst + hl * 16384, &tPsi, p.row0 + ti * kBM + kh * 64,
+                tma_load_2d(dst + hl * 16384, &mp.m[5], p.row0 + ti * kBM + kh * 64,
                             (pl * 2 + hl) * p.LS + wv * 128, &sh->st_full[slot]);
             } else {
               // Omega plane pl (YPW == 2), or row half h of plane pl (YPW == 1)
               const int pl = p.YPW == 2 ? st : st >> 1, h = p.YPW == 2 ? 0 : st & 1;
               mbar_expect_tx(&sh->st_full[slot], hl_tx * (uint32_t)(p.OB * 128));
               for (int hl = 0; hl < (int)hl_tx; ++hl)
-                tma_load_2d(dst + hl * 16384, &tOm, p.col0 + tj * kBN, (pl * 2 + hl) * p.NS + h * p.OB,
+                tma_load_2d(dst + hl * 16384, &mp.m[4], p.col0 + tj * kBN, (pl * 2 + hl) * p.NS + h * p.OB,
                             &sh->st_full[slot]);
             }
             ++gs;
@@ -199,9 +229,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       // wait (bounded) for our own copies before leaving
-      if (a_outstanding) wait_bar(&sh->a_full, (a_fills - 1) & 1, sh, p.status, true);
+      if (a_outstanding) wait_bar(&sh->a_full, (a_fills - 1) & 1, sh, cur_status, true);
       for (uint32_t k = gs > kStages ? gs - kStages : 0; k < gs; ++k)
-        wait_bar(&sh->st_full[k % kStages], (k / kStages) & 1, sh, p.status, true);
+        wait_bar(&sh->st_full[k % kStages], (k / kStages) & 1, sh, cur_status, true);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -217,14 +247,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           wneg |= (kWSign[q][k] < 0 ? 1u : 0u) << (4 * q + k);
           yneg |= (kYSign[q][k] < 0 ? 1u : 0u) << (4 * q + k);
         }
-      // products: hi*hi, then A_lo * (test hi) when nprod >= 2, (test lo) * A_hi when nprod == 3
-      const bool alo = p.nprod >= 2, three = p.nprod == 3, pure = p.pure != 0;
-      const int MT = p.MT, YPW = p.YPW, NS = p.NS, OB = p.OB;
       const uint32_t wid_pos = idesc_bf16(128, 64, 1, 0), wid_neg = idesc_bf16(128, 64, 1, 1);
       const uint64_t dA_w = sdesc(a_base, 32768, 2048);   // A tile as the W products' B operand
       const uint64_t dA_y = sdesc(a_base, 16, 2048);      // A tile as the Y products' A operand
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok && !sh->abort; t += gridDim.x, ++t_local) {
+        const TcParams& p = bt.prm[item_of(t)];
+        cur_status = p.status;
+        // products: hi*hi, then A_lo * (test hi) when nprod >= 2, (test lo) * A_hi when nprod == 3
+        const bool alo = p.nprod >= 2, three = p.nprod == 3, pure = p.pure != 0;
+        const int MT = p.MT, YPW = p.YPW, NS = p.NS, OB = p.OB;
+        const int nwaves = nwaves_of(p);
         if (!wait_bar(&sh->a_ready, t_local & 1, sh, p.status)) break;
         tc_fence_after();
         for (int wv = 0; wv < nwaves && ok; ++wv, ++g) {
@@ -233,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint32_t hbase = tmem + half * 256;
           uint32_t started = 0;
-          const int nst = wave_stages(wv);
+          const int nst = wave_stages(p, wv);
           for (int st = 0; st < nst; ++st, ++gs) {
             const uint32_t slot = gs % kStages;
             if (!wait_bar(&sh->st_full[slot], (gs / kStages) & 1, sh, p.status)) { ok = false; break; }
@@ -299,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // drain: every MMA issued so far completes before TMEM is released
       umma_commit(&sh->done);
-      wait_bar(&sh->done, 0, sh, p.status, true);
+      wait_bar(&sh->done, 0, sh, cur_status, true);
     }
   } else if (warp >= 2 && warp <= 5) {
     // ------------------------------------------------------------ converters
@@ -308,8 +341,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     // rewritten in place as a 1 KB hi atom and a 1 KB lo atom (128-byte swizzle).
     const int cw = warp - 2;
     int t_local = 0;
-    for (int t = blockIdx.x; t < ntiles && !sh->abort; t += gridDim.x, ++t_local) {
-      if (!wait_bar(&sh->a_full, t_local & 1, sh, p.status)) break;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok && !sh->abort; t += gridDim.x, ++t_local) {
+      const TcParams& p = bt.prm[item_of(t)];
+      if (!wait_bar(&sh->a_full, t_local & 1, sh, p.status)) { ok = false; break; }
       for (int gi = cw; gi < 64; gi += 4) {
         const int plane = gi >> 4, grp = gi & 15;
         if (p.pure && plane == 0) continue;
@@ -345,10 +380,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ epilogue
     const int lq = warp & 3;  // TMEM lane quarter this warp may access
     uint32_t g = 0;
-    const bool wvec = ((p.col0 & 3) == 0) && ((p.ldw & 3) == 0);
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok && !sh->abort; t += gridDim.x) {
-      const int ti = t / p.tiles_n, tj = t % p.tiles_n;
+      const int it = item_of(t);
+      const TcParams& p = bt.prm[it];
+      const int lt = t - bt.tile_start[it], ti = lt / p.tiles_n, tj = lt % p.tiles_n;
+      const int nwaves = nwaves_of(p);
+      const bool wvec = ((p.col0 & 3) == 0) && ((p.ldw & 3) == 0);
       for (int wv = 0; wv < nwaves; ++wv, ++g) {
         const uint32_t half = g & 1, use = g >> 1;
         if (!wait_bar(&sh->h_full[half], use & 1, sh, p.status)) { ok = false; break; }
@@ -511,26 +549,27 @@ cudaError_t tc_pack_embeddings(const qs_handle_s& h, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t lda, int64_t row0,
-                           int64_t col0, int64_t mb, int64_t nb, double eta, cudaStream_t st) {
+namespace {
+
+// Tensor maps and parameters of the fused sketch of block (row0, col0, mb, nb) of A.
+qs_status tc_prepare(const qs_handle_s& h, const void* const A[4], int64_t lda, int64_t row0,
+                     int64_t col0, int64_t mb, int64_t nb, double eta, TcParams& prm, TcMaps& mp) {
   const qs_config& c = h.cfg;
   const PackGeom g = geom(c);
   if (g.NS > 256) return QS_ERR_UNSUPPORTED;   // a Y wave holds one plane of NS <= 256 columns
   if (lda % 4) return QS_ERR_INVALID;                         // TMA: 16-byte row pitch
   for (int q = 0; q < 4; ++q)
     if (A[q] && (reinterpret_cast<uintptr_t>(A[q]) & 15)) return QS_ERR_INVALID;
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(fused_sketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes()) != cudaSuccess)
-      return QS_ERR_CUDA;
-    attr_set = true;
-  }
-  CUtensorMap tA[4], tOm, tPsi;
-  memset(tA, 0, sizeof(tA));
+  // TMA x coordinates of the BF16 Psi / Omega operands must be multiples of 8 elements (16
+  // bytes): the tiles start at row0 / col0 rounded down to 8, and the A tile is loaded from y =
+  // -rsh (x = -csh), which the copy fills with zeros, so the extra rows / columns add nothing
+  // and the epilogue skips them.  A's x must itself stay 16-byte aligned, so csh is 0 or 4.
+  const int rsh = (int)(row0 & 7), csh = (int)(col0 & 7);
+  if (csh & 3) return QS_ERR_UNSUPPORTED;
+  memset(&mp, 0, sizeof(mp));
   for (int q = 0; q < 4; ++q) {
     const void* base = A[q] ? A[q] : A[c.pure ? 1 : q];   // plane w of a pure A is never loaded
-    if (!make_map(&tA[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, nb, mb, lda, kBN, kBM,
+    if (!make_map(&mp.m[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, nb, mb, lda, kBN, kBM,
                   CU_TENSOR_MAP_SWIZZLE_NONE))
       return QS_ERR_CUDA;
   }
@@ -539,19 +578,13 @@ qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t
       reinterpret_cast<const __nv_bfloat16*>(h.ws + h.off_pack + (g.om_bytes + 255) / 256 * 256);
   const int ypw = 2 * g.NS <= 256 ? 2 : 1;
   const int ob = ypw == 2 ? (int)g.NS : (int)((g.NS / 2 + 15) / 16 * 16);
-  if (!make_map(&tOm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, om, c.n, 4 * 2 * g.NS, g.ldo, 64,
+  if (!make_map(&mp.m[4], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, om, c.n, 4 * 2 * g.NS, g.ldo, 64,
                 (uint32_t)ob, CU_TENSOR_MAP_SWIZZLE_128B))
     return QS_ERR_CUDA;
-  if (!make_map(&tPsi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ps, c.m, 4 * 2 * g.LS, g.ldp, 64, 128,
+  if (!make_map(&mp.m[5], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ps, c.m, 4 * 2 * g.LS, g.ldp, 64, 128,
                 CU_TENSOR_MAP_SWIZZLE_128B))
     return QS_ERR_CUDA;
-  // TMA x coordinates of the BF16 Psi / Omega operands must be multiples of 8 elements (16
-  // bytes): the tiles start at row0 / col0 rounded down to 8, and the A tile is loaded from y =
-  // -rsh (x = -csh), which the copy fills with zeros, so the extra rows / columns add nothing
-  // and the epilogue skips them.  A's x must itself stay 16-byte aligned, so csh is 0 or 4.
-  const int rsh = (int)(row0 & 7), csh = (int)(col0 & 7);
-  if (csh & 3) return QS_ERR_UNSUPPORTED;
-  TcParams prm{};
+  prm = TcParams{};
   prm.mb = (int)mb; prm.nb = (int)nb; prm.row0 = (int)(row0 - rsh); prm.col0 = (int)(col0 - csh);
   prm.rsh = rsh; prm.csh = csh;
   prm.tiles_m = (int)((mb + rsh + kBM - 1) / kBM);
@@ -574,11 +607,76 @@ qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t
   prm.ldy = sy;
   prm.ldw = c.n;
   prm.status = reinterpret_cast<int32_t*>(h.ws + h.off_status);
-  const int ntiles = prm.tiles_m * prm.tiles_n;
+  return QS_OK;
+}
+
+template <int MAXB>
+qs_status launch_fused(const TcBatch<MAXB>& bt, cudaStream_t st) {
+  static_assert(sizeof(TcBatch<MAXB>) <= 32764, "kernel parameters above the 32764-byte limit");
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(fused_sketch_kernel<MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes()) != cudaSuccess)
+      return QS_ERR_CUDA;
+    attr_set = true;
+  }
+  const int ntiles = bt.tile_start[bt.count];
+  if (ntiles <= 0) return QS_OK;
   const int grid = std::min(ntiles, kNumSMs);
-  fused_sketch_kernel<<<grid, kThreads, smem_bytes(), st>>>(tA[0], tA[1], tA[2], tA[3], tOm, tPsi, prm);
+  fused_sketch_kernel<MAXB><<<grid, kThreads, smem_bytes(), st>>>(bt);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
+}
+
+// Y and W of every item set to zero (the batched update replaces the sketches): item i's
+// planes are mb x ldy and l x ldw floats from Y[q], W[q].
+__global__ void batch_zero_kernel(const __grid_constant__ TcBatch<kMaxBatch> bt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int i = 0; i < bt.count; ++i) {
+    const TcParams& p = bt.prm[i];
+    const int64_t ny = (int64_t)p.mb * p.ldy, nw = (int64_t)p.l * p.ldw;
+    for (int q = 0; q < 4; ++q) {
+      for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ny; e += stride) p.Y[q][e] = 0.f;
+      for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nw; e += stride) p.W[q][e] = 0.f;
+    }
+  }
+}
+
+}  // namespace
+
+qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t lda, int64_t row0,
+                           int64_t col0, int64_t mb, int64_t nb, double eta, cudaStream_t st) {
+  TcBatch<1> bt;
+  const qs_status r = tc_prepare(h, A, lda, row0, col0, mb, nb, eta, bt.prm[0], bt.maps[0]);
+  if (r != QS_OK) return r;
+  bt.count = 1;
+  bt.tile_start[0] = 0;
+  bt.tile_start[1] = bt.prm[0].tiles_m * bt.prm[0].tiles_n;
+  return launch_fused(bt, st);
+}
+
+qs_status tc_sketch_replace_batched(int count, const qs_handle_s* const* hs, const void* const* A,
+                                    const int64_t* lda, cudaStream_t st) {
+  for (int i0 = 0; i0 < count; i0 += kMaxBatch) {
+    TcBatch<kMaxBatch> bt;
+    bt.count = std::min(kMaxBatch, count - i0);
+    bt.tile_start[0] = 0;
+    for (int j = 0; j < bt.count; ++j) {
+      const qs_handle_s& h = *hs[i0 + j];
+      const qs_status r = tc_prepare(h, A + 4 * (int64_t)(i0 + j), lda[i0 + j], 0, 0, h.cfg.m, h.cfg.n, 1.0,
+                                     bt.prm[j], bt.maps[j]);
+      if (r != QS_OK) return r;
+      const int64_t tiles = (int64_t)bt.prm[j].tiles_m * bt.prm[j].tiles_n;
+      if (bt.tile_start[j] + tiles > INT32_MAX) return QS_ERR_UNSUPPORTED;
+      bt.tile_start[j + 1] = bt.tile_start[j] + (int)tiles;
+    }
+    batch_zero_kernel<<<2 * kNumSMs, 256, 0, st>>>(bt);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return QS_ERR_CUDA;
+    const qs_status r = launch_fused(bt, st);
+    if (r != QS_OK) return r;
+  }
+  return QS_OK;
 }
 
 }  // namespace qs

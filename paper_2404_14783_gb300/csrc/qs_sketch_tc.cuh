@@ -11,6 +11,12 @@ cudaError_t tc_pack_embeddings(const qs_handle_s& h, cudaStream_t st);
 // fused one-read sketch of a block of A
 qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t lda, int64_t row0,
                            int64_t col0, int64_t mb, int64_t nb, double eta, cudaStream_t st);
+// Y_i = A_i Omega_i, W_i = Psi_i A_i (the sketches replaced) for count handles in the
+// tensor-core modes, whole matrices: up to 32 matrices share one persistent launch (after one
+// launch that zeroes their Y and W).  Arguments are checked by the caller except the
+// tensor-core rules, which fail the call before that chunk's launches.
+qs_status tc_sketch_replace_batched(int count, const qs_handle_s* const* hs, const void* const* A,
+                                    const int64_t* lda, cudaStream_t st);
 // pseudo-SVD small stage (Alg. 2 on chi_R): Z (s x s quaternion) from R (s x s upper)
 size_t psvd_work_bytes(int64_t s);
 cudaError_t launch_psvd_small(const double* R, int64_t ldr, int64_t psr, int s, void* work,

@@ -2,7 +2,8 @@
 of different shapes in one call, as in the batch workload (m, n in [256, 4096], k in [8, 64],
 s = 2k + 1, l = 2s + 1, Rademacher test matrices, split-BF16).  Each result matches the
 oracle's sketch of its own matrix (1e-5 relative, the split-BF16 tolerance) and the
-single-matrix entry point on the same inputs.
+single-matrix entry point on the same inputs.  The tensor-core items of a call share
+persistent launches of up to 32 matrices; the call replays from a captured CUDA graph.
 """
 import numpy as np
 import pytest
@@ -74,3 +75,86 @@ def test_batched_rejects_before_enqueueing(pkg):
     with pytest.raises(pkg.QSError):
         pkg.update_batched([q1, q2], [good, bad])
     assert pkg.launch_count() == before
+
+
+def _batch(pkg, count, seed):
+    """count small matrices of mixed shapes, embeddings, precisions and purity."""
+    rng = np.random.default_rng(seed)
+    sk, sk1, mats, host, meta = [], [], [], [], []
+    for i in range(count):
+        m, n = (int(v) for v in rng.integers(64, 400, size=2))
+        k = int(rng.integers(2, 9))
+        s = 2 * k + 1
+        l = min(2 * s + 1, m, n)
+        emb = "rademacher" if i % 3 else "gaussian"
+        prec = ("bf16x3", "bf16x3", "bf16", "fp32")[i % 4]
+        pure = i % 5 == 4
+        A = WL.make_decay(m, n, seed=seed + i, rank_cap=min(m, n, 64), dtype=np.float32)
+        if pure:
+            A[0] = 0.0
+        host.append(A)
+        d = _dev(A)
+        mats.append([None, d[1], d[2], d[3]] if pure else d)
+        kw = dict(emb=emb, prec=prec, seed=1000 + i, pure=pure)
+        sk.append(pkg.QSketch(m, n, s, l, **kw))
+        sk1.append(pkg.QSketch(m, n, s, l, **kw))
+        meta.append((m, n, s, l, emb, prec))
+    return sk, sk1, mats, host, meta
+
+
+def _check_batch(sk, sk1, host, meta, tol_single):
+    for i, (A, (m, n, s, l, emb, prec)) in enumerate(zip(host, meta)):
+        assert sk[i].device_status() == 0
+        Y, W = sk[i].get("Y").cpu().numpy(), sk[i].get("W").cpu().numpy()
+        assert rel(Y, sk1[i].get("Y").cpu().numpy()) < tol_single, i
+        assert rel(W, sk1[i].get("W").cpu().numpy()) < tol_single, i
+        if i % 7 == 0:       # a sample against the oracle
+            kind = O.EMB_RADEMACHER if emb == "rademacher" else O.EMB_GAUSSIAN
+            Om = O.draw_embedding(n, s, kind, O.STREAM_OMEGA, 1000 + i)
+            Psi = O.draw_embedding(l, m, kind, O.STREAM_PSI, 1000 + i)
+            Yr, Wr = O.sketch(A.astype(np.float64), Om, Psi)
+            tol = 8e-3 if prec == "bf16" else 1e-5
+            assert rel(Y, Yr) < tol and rel(W, Wr) < tol, i
+
+
+def test_batched_persistent_launches_over_chunks(pkg):
+    """48 items: the 36 in the tensor-core modes run as two persistent launches (32 + 4
+    items, each after one zeroing launch), the FP32 ones one update each.  Each item equals
+    its single update (1e-6: only the order of the L2 reductions differs) and, on a sample,
+    the oracle (1e-5 split-BF16, 8e-3 BF16)."""
+    sk, sk1, mats, host, meta = _batch(pkg, 48, seed=50)
+    n_tc = sum(1 for mt in meta if mt[5] != "fp32")
+    before = pkg.launch_count()
+    pkg.update_batched(sk, mats)
+    launched = pkg.launch_count() - before
+    n_fp32 = len(meta) - n_tc
+    chunks = (n_tc + 31) // 32
+    assert chunks == 2
+    assert launched <= 2 * chunks + n_fp32 * 8, launched    # zero + fused per chunk
+    for q, A in zip(sk1, mats):
+        q.update(A, theta=0.0)
+    torch.cuda.synchronize()
+    _check_batch(sk, sk1, host, meta, 1e-6)
+
+
+def test_batched_update_replays_from_a_cuda_graph(pkg):
+    """The batched call captured once in a CUDA graph and replayed (the sketches cleared in
+    between) gives the eager results."""
+    sk, sk1, mats, host, meta = _batch(pkg, 12, seed=90)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        pkg.update_batched(sk, mats)          # eager run on a side stream (first-call set-up)
+    torch.cuda.current_stream().wait_stream(side)
+    for q, A in zip(sk1, mats):
+        q.update(A, theta=0.0)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        pkg.update_batched(sk, mats)
+    for rep in range(2):
+        for q in sk:
+            q.get("Y").fill_(float("nan"))
+            q.get("W").fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        _check_batch(sk, sk1, host, meta, 1e-6)

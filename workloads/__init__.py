@@ -16,10 +16,23 @@ that are not available):
   c2  8192 x 8192, FP32: A = U diag(i^-2) V* with random quaternion-orthonormal U, V;
       the spectrum is truncated at R = 1024 (sigma_R = 9.5e-7; the dropped tail is
       1.7e-5 of ||A||_F); k=50, s=101, l=203; Gaussian embeddings.
+  c4  a batch of 256 matrices, m, n ~ U[256, 4096] independently, k ~ U{8..64},
+      s = 2k + 1, l = 2s + 1, sigma_j = exp(-j/8) on R = min(m, n, 320) columns (sigma_320 is
+      4e-18, below FP32 resolution), FP32 data, Rademacher embeddings (make_c4_batch, built
+      on the device: it is a throughput workload, its parity cases are smaller).
+  ex51-{lrn,pds,eds}  the synthetic family of Sec. 5 (Example "syntheticData"): A = U Sigma V*,
+      2000 x 1600, with Sigma = diag(1 (R times), 0, ...) + (xi / n) E (low rank plus noise,
+      E a standard quaternion Gaussian), diag(1 (R times), 2^-p, 3^-p, ...) (polynomial
+      decay) or diag(1 (R times), 10^-q, 10^-2q, ...) (exponential decay); the paper plots
+      xi = 0.01, p = 2, q = 0.25 and does not state R (R = 10 here, the count of leading
+      ones in the practical-sketching test matrices the example follows).
 Random quaternion-orthonormal factors are built as U = D Q W: Q real orthonormal (QR of a
 real Gaussian), W the unitary polar factor of an R x R quaternion Gaussian (from the
 eigendecomposition of its Hermitian complex form), D a diagonal of random unit
-quaternions.  Each factor is unitary, hence so is the product.
+quaternions.  Each factor is unitary, hence so is the product.  For the large square
+factors of the Sec. 5 family the polar factor is replaced by a second real orthogonal
+factor and unit-quaternion diagonal, U = D1 Q1 D2 Q2 (also unitary; the eigendecomposition
+of a 3200 x 3200 complex matrix would take most of a minute).
 """
 import numpy as np
 
@@ -27,6 +40,10 @@ WORKLOADS = {
     "c1": dict(m=512, n=384, k=10, s=21, l=43, precision="fp64", emb="gaussian", seed=0),
     "c2": dict(m=8192, n=8192, k=50, s=101, l=203, precision="bf16x3", emb="gaussian",
                seed=0, rank_cap=1024),
+    # batch: m, n ~ U[256, 4096], k ~ U{8..64}, s = 2k + 1, l = 2s + 1, sigma_j = exp(-j/8)
+    # on R = min(m, n, 320) columns, Rademacher embeddings, split-BF16 sketch
+    "c4": dict(count=256, lo=256, hi=4096, k_lo=8, k_hi=64, rank_cap=320, precision="bf16x3",
+               emb="rademacher", seed=0),
 }
 
 
@@ -62,6 +79,51 @@ def random_orthonormal(rng, m, R):
     d = rng.standard_normal((4, m, 1))
     d /= np.sqrt(np.sum(d * d, axis=0, keepdims=True))
     return _qmul_planes(d, QW)
+
+
+def _unit_diag(rng, m):
+    d = rng.standard_normal((4, m, 1))
+    return d / np.sqrt(np.sum(d * d, axis=0, keepdims=True))
+
+
+def random_orthonormal_fast(rng, m, R):
+    """Random m x R quaternion matrix with orthonormal columns, U = D1 Q1 D2 Q2 (Q1 m x R
+    real orthonormal, Q2 R x R real orthogonal, D1, D2 diagonals of unit quaternions)."""
+    Q1, _ = np.linalg.qr(rng.standard_normal((m, R)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((R, R)))
+    D1Q1 = _qmul_planes(_unit_diag(rng, m), np.broadcast_to(Q1, (4, m, R)) * np.array([1.0, 0, 0, 0])[:, None, None])
+    T = _qmul_planes(D1Q1, _unit_diag(rng, R).transpose(0, 2, 1))     # D1 Q1 D2 (column scaling)
+    return np.stack([T[p] @ Q2 for p in range(4)])
+
+
+def _qprod(P, Q):
+    """Quaternion matrix product P Q (plane form), for building inputs."""
+    return np.stack([P[0] @ Q[0] - P[1] @ Q[1] - P[2] @ Q[2] - P[3] @ Q[3],
+                     P[0] @ Q[1] + P[1] @ Q[0] + P[2] @ Q[3] - P[3] @ Q[2],
+                     P[0] @ Q[2] - P[1] @ Q[3] + P[2] @ Q[0] + P[3] @ Q[1],
+                     P[0] @ Q[3] + P[1] @ Q[2] - P[2] @ Q[1] + P[3] @ Q[0]])
+
+
+def make_ex51(kind, m=2000, n=1600, R=10, xi=0.01, p=2.0, q=0.25, seed=0, dtype=np.float64):
+    """The Sec. 5 synthetic family (m >= n): kind "lrn" (low rank plus noise), "pds"
+    (polynomial decay) or "eds" (exponential decay); A = U Sigma V* with U (m x n), V (n x n)
+    random quaternion-orthonormal."""
+    rng = np.random.default_rng(seed)
+    U = random_orthonormal_fast(rng, m, n)
+    V = random_orthonormal_fast(rng, n, n)
+    tail = np.arange(1, n - R + 1, dtype=np.float64)
+    if kind == "lrn":
+        Sig = (xi / n) * rng.standard_normal((4, n, n))
+        Sig[0, np.arange(R), np.arange(R)] += 1.0
+        Vt = np.stack([V[0].T, -V[1].T, -V[2].T, -V[3].T])
+        return _qprod(_qprod(U, Sig), Vt).astype(dtype)
+    if kind == "pds":
+        sigma = np.concatenate([np.ones(R), (tail + 1.0) ** (-p)])
+    elif kind == "eds":
+        sigma = np.concatenate([np.ones(R), 10.0 ** (-q * tail)])
+    else:
+        raise ValueError(kind)
+    return _assemble(U, sigma, V, dtype=dtype)
 
 
 def _assemble(U, sigma, V, device=None, dtype=np.float64):
@@ -119,3 +181,51 @@ def make_lowrank(m, n, rank, seed=0, dtype=np.float64):
 def make_gaussian(m, n, seed=0, dtype=np.float64):
     """Quaternion Gaussian with N(0,1) planes."""
     return np.random.default_rng(seed).standard_normal((4, m, n)).astype(dtype)
+
+
+def make_c4_batch(device, spec=None):
+    """The c4 batch on a torch device: list of (m, n, k, A) with A a (4, m, n) FP32 tensor
+    (leading dimension padded to a multiple of 4), A = U diag(exp(-j/8)) V* with
+    U = D1 Q1 D2 Q2-type quaternion-orthonormal factors drawn with torch on the device."""
+    import torch
+    spec = dict(WORKLOADS["c4"], **(spec or {}))
+    rng = np.random.default_rng(spec["seed"])
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(spec["seed"]))
+    dt = torch.float64
+
+    def unit(shape):
+        d = torch.randn((4,) + shape, generator=gen, device=device, dtype=dt)
+        return d / torch.sqrt((d * d).sum(0, keepdim=True))
+
+    def qm(a, b):   # entrywise Hamilton product with broadcasting (diagonal scalings)
+        return torch.stack([a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3],
+                            a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2],
+                            a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1],
+                            a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0]])
+
+    def orth(rows, R):
+        Q1 = torch.linalg.qr(torch.randn((rows, R), generator=gen, device=device, dtype=dt)).Q
+        Q2 = torch.linalg.qr(torch.randn((R, R), generator=gen, device=device, dtype=dt)).Q
+        real = torch.stack([Q1, torch.zeros_like(Q1), torch.zeros_like(Q1), torch.zeros_like(Q1)])
+        T = qm(qm(unit((rows, 1)), real), unit((1, R)))       # D1 Q1 D2
+        return torch.stack([T[p] @ Q2 for p in range(4)])
+
+    out = []
+    for _ in range(spec["count"]):
+        m, n = (int(v) for v in rng.integers(spec["lo"], spec["hi"] + 1, size=2))
+        k = int(rng.integers(spec["k_lo"], spec["k_hi"] + 1))
+        R = min(m, n, spec["rank_cap"])
+        # factors in FP64, the product in FP32 (the data's precision; FP64 matrix products
+        # would dominate the set-up on a GPU whose FP64 rate is low)
+        U = (orth(m, R) * torch.exp(-torch.arange(1, R + 1, device=device, dtype=dt) / 8.0)).float()
+        V = orth(n, R).float()
+        Vt = torch.stack([V[0].T, -V[1].T, -V[2].T, -V[3].T])
+        w = U[0] @ Vt[0] - U[1] @ Vt[1] - U[2] @ Vt[2] - U[3] @ Vt[3]
+        x = U[0] @ Vt[1] + U[1] @ Vt[0] + U[2] @ Vt[3] - U[3] @ Vt[2]
+        y = U[0] @ Vt[2] - U[1] @ Vt[3] + U[2] @ Vt[0] + U[3] @ Vt[1]
+        z = U[0] @ Vt[3] + U[1] @ Vt[2] - U[2] @ Vt[1] + U[3] @ Vt[0]
+        buf = torch.zeros((4, m, (n + 3) // 4 * 4), dtype=torch.float32, device=device)
+        buf[:, :, :n] = torch.stack([w, x, y, z])
+        out.append((m, n, k, buf[:, :, :n]))
+    return out
