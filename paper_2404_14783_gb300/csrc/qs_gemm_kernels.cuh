@@ -18,18 +18,33 @@ __device__ __forceinline__ T ld_elem(const void* base, int64_t idx) {
   return static_cast<const T*>(base)[idx];
 }
 
+// c += a * b (Hamilton product) with A, B and accumulator types that may differ (an FP32 A
+// against a double-float B and accumulator uses the cheaper mixed fma).
+template <typename TA_, typename TB_, typename TC_>
+__device__ __forceinline__ void qmacx(TC_& cw, TC_& cx, TC_& cy, TC_& cz, TA_ aw, TA_ ax, TA_ ay, TA_ az,
+                                      TB_ bw, TB_ bx, TB_ by, TB_ bz) {
+  cw = fma(aw, bw, cw); cw = fma(-ax, bx, cw); cw = fma(-ay, by, cw); cw = fma(-az, bz, cw);
+  cx = fma(aw, bx, cx); cx = fma(ax, bw, cx); cx = fma(ay, bz, cx); cx = fma(-az, by, cx);
+  cy = fma(aw, by, cy); cy = fma(-ax, bz, cy); cy = fma(ay, bw, cy); cy = fma(az, bx, cy);
+  cz = fma(aw, bz, cz); cz = fma(ax, by, cz); cz = fma(-ay, bx, cz); cz = fma(az, bw, cz);
+}
+
 // BCPLX: B has only its w and x planes (a complex matrix); the y and z products are skipped.
 // PARTIAL (error epilogue only): each CTA stores its two tile sums at err[2t], err[2t+1]
 // (t = its linear tile index) instead of adding them atomically into err[0], err[1].
-// TN: output columns per thread (4, or 2 for the double-float tall products: 4 x 2 outputs
-// per thread need about half the registers, so two CTAs share an SM, and the 32-column
-// tile wastes less of an N = s that is not a multiple of 64).
+// TN: output columns per thread (4, or 2 / 1 for the double-float tall products: 4 x 2 or
+// 4 x 1 outputs per thread need fewer registers, so several CTAs share an SM, and the 32- or
+// 16-column tile wastes less of an N = s that is not a multiple of 64).
+// AS: type of the staged A tile -- FP32 when A is FP32 and the accumulator double-float (the
+// low part of an FP32 value is zero, so it is neither stored nor multiplied).
 template <typename ACC, typename TA, typename TB, typename TC, bool CONJ, bool BCPLX = false,
           bool PARTIAL = false, int TN = 4>
-__global__ void __launch_bounds__(256, (sizeof(ACC) == 4 || TN == 2) ? 2 : 1) qgemm_kernel(GemmDesc g) {
+__global__ void __launch_bounds__(256, TN == 1 ? 3 : ((sizeof(ACC) == 4 || TN == 2) ? 2 : 1)) qgemm_kernel(GemmDesc g) {
+  using AS = typename std::conditional<std::is_same<ACC, df64>::value && std::is_same<TA, float>::value,
+                                       float, ACC>::type;
   constexpr int BM = 64, BN = 16 * TN;
   constexpr int BK = sizeof(ACC) == 8 ? 4 : 8;
-  __shared__ __align__(16) ACC As[2][4][BK][BM];
+  __shared__ __align__(16) AS As[2][4][BK][BM];
   __shared__ __align__(16) ACC Bs[2][4][BK][BN];
 
   if (g.gate && *g.gate == g.gate_skip) return;
@@ -49,20 +64,22 @@ __global__ void __launch_bounds__(256, (sizeof(ACC) == 4 || TN == 2) ? 2 : 1) qg
   const TB* B = static_cast<const TB*>(g.b[lp]);
   const bool a_zero = (A == nullptr);   // a NULL plane is identically zero (pure quaternion)
   const bool b_zero = (B == nullptr);
-  const ACC a_sign = (CONJ && lp != 0) ? ACC(-1) : ACC(1);
+  const AS a_sign = (CONJ && lp != 0) ? AS(-1) : AS(1);
 
-  ACC ra[BK], rb[BK];
+  AS ra[BK];
+  ACC rb[BK];
   auto load_regs = [&](int64_t k0) {
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       const int64_t k = k0 + kk;
-      ACC va = ACC(0), vb = ACC(0);
+      AS va = AS(0);
+      ACC vb = ACC(0);
       if (CONJ) {
         const int64_t mm = m0 + lr;
-        if (!a_zero && k < kend && mm < g.M) va = a_sign * ACC(A[k * g.lda + mm]);
+        if (!a_zero && k < kend && mm < g.M) va = a_sign * AS(A[k * g.lda + mm]);
       } else {
         const int64_t mm = m0 + lr;
-        if (!a_zero && k < kend && mm < g.M) va = ACC(A[mm * g.lda + k]);
+        if (!a_zero && k < kend && mm < g.M) va = AS(A[mm * g.lda + k]);
       }
       const int64_t nn = n0 + lr;
       if (!b_zero && lr < BN && k < kend && nn < g.N) vb = ACC(B[k * g.ldb + nn]);
@@ -97,7 +114,8 @@ __global__ void __launch_bounds__(256, (sizeof(ACC) == 4 || TN == 2) ? 2 : 1) qg
     if (has_next) load_regs(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      ACC a[4][4], b[4][TN];
+      AS a[4][4];
+      ACC b[4][TN];
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
 #pragma unroll
@@ -120,8 +138,8 @@ __global__ void __launch_bounds__(256, (sizeof(ACC) == 4 || TN == 2) ? 2 : 1) qg
             acc[3][i][j] = fma(a[3][i], b[0][j], acc[3][i][j]);
             acc[3][i][j] = fma(-a[2][i], b[1][j], acc[3][i][j]);
           } else {
-            qmac(acc[0][i][j], acc[1][i][j], acc[2][i][j], acc[3][i][j], a[0][i], a[1][i], a[2][i],
-                 a[3][i], b[0][j], b[1][j], b[2][j], b[3][j]);
+            qmacx(acc[0][i][j], acc[1][i][j], acc[2][i][j], acc[3][i][j], a[0][i], a[1][i], a[2][i],
+                  a[3][i], b[0][j], b[1][j], b[2][j], b[3][j]);
           }
         }
     }
@@ -203,11 +221,15 @@ __global__ void __launch_bounds__(256, (sizeof(ACC) == 4 || TN == 2) ? 2 : 1) qg
 // Small products (M, N <= 512, e.g. the s x s factors of the rangefinders): one quaternion
 // output per thread, 16 x 16 outputs per CTA, K staged 16 deep, split-K over grid z.
 // COUT: only the complex part (planes w, x) of C is formed; planes y, z are left zero.
+// AS, BS: staged operand types -- FP32 for an FP32 operand under a double-float accumulator.
 template <typename ACC, typename TA, typename TB, typename TC, bool CONJ, bool COUT = false>
 __global__ void __launch_bounds__(256) qgemm_small_kernel(GemmDesc g) {
+  constexpr bool DF = std::is_same<ACC, df64>::value;
+  using AS = typename std::conditional<DF && std::is_same<TA, float>::value, float, ACC>::type;
+  using BS = typename std::conditional<DF && std::is_same<TB, float>::value, float, ACC>::type;
   constexpr int T = 16, BK = 16;
-  __shared__ ACC As[4][BK][T + 1];
-  __shared__ ACC Bs[4][BK][T + 1];
+  __shared__ AS As[4][BK][T + 1];
+  __shared__ BS Bs[4][BK][T + 1];
   if (g.gate && *g.gate == g.gate_skip) return;
   if (g.herm && blockIdx.y < blockIdx.x) return;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -226,18 +248,19 @@ __global__ void __launch_bounds__(256) qgemm_small_kernel(GemmDesc g) {
       const TA* A = static_cast<const TA*>(g.a[pl]);
       const TB* B = static_cast<const TB*>(g.b[pl]);
       // A tile element (m = m0 + r, k = k0 + c); B tile element (k = k0 + r, n = n0 + c)
-      ACC va = ACC(0), vb = ACC(0);
+      AS va = AS(0);
+      BS vb = BS(0);
       const int64_t ka = k0 + c, ma = m0 + r;
       if (A && ka < kend && ma < g.M) {
         if (CONJ) {
-          va = ACC(A[ka * g.lda + ma]);
+          va = AS(A[ka * g.lda + ma]);
           if (pl) va = -va;
         } else {
-          va = ACC(A[ma * g.lda + ka]);
+          va = AS(A[ma * g.lda + ka]);
         }
       }
       const int64_t kb = k0 + r, nb = n0 + c;
-      if (B && kb < kend && nb < g.N) vb = ACC(B[kb * g.ldb + nb]);
+      if (B && kb < kend && nb < g.N) vb = BS(B[kb * g.ldb + nb]);
       As[pl][c][r] = va;
       Bs[pl][r][c] = vb;
     }
@@ -245,13 +268,13 @@ __global__ void __launch_bounds__(256) qgemm_small_kernel(GemmDesc g) {
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       if (COUT) {  // (a b)_w and (a b)_x of the Hamilton product
-        const ACC aw = As[0][kk][ty], ax = As[1][kk][ty], ay = As[2][kk][ty], az = As[3][kk][ty];
-        const ACC bw = Bs[0][kk][tx], bx = Bs[1][kk][tx], by = Bs[2][kk][tx], bz = Bs[3][kk][tx];
+        const AS aw = As[0][kk][ty], ax = As[1][kk][ty], ay = As[2][kk][ty], az = As[3][kk][ty];
+        const BS bw = Bs[0][kk][tx], bx = Bs[1][kk][tx], by = Bs[2][kk][tx], bz = Bs[3][kk][tx];
         cw = fma(aw, bw, fma(-ax, bx, fma(-ay, by, fma(-az, bz, cw))));
         cx = fma(aw, bx, fma(ax, bw, fma(ay, bz, fma(-az, by, cx))));
       } else {
-        qmac(cw, cx, cy, cz, As[0][kk][ty], As[1][kk][ty], As[2][kk][ty], As[3][kk][ty],
-             Bs[0][kk][tx], Bs[1][kk][tx], Bs[2][kk][tx], Bs[3][kk][tx]);
+        qmacx(cw, cx, cy, cz, As[0][kk][ty], As[1][kk][ty], As[2][kk][ty], As[3][kk][ty],
+              Bs[0][kk][tx], Bs[1][kk][tx], Bs[2][kk][tx], Bs[3][kk][tx]);
       }
     }
     __syncthreads();
@@ -288,11 +311,18 @@ cudaError_t launch_t(const GemmDesc& d, cudaStream_t st) {
   }
   dim3 grid((unsigned)((d.M + 63) / 64), (unsigned)((d.N + 63) / 64), (unsigned)d.splits);
   const bool bcplx = !d.b[2] && !d.b[3] && d.b[0] && d.b[1];
-  // double-float tall products with a narrow N: 64 x 32 tiles (4 x 2 outputs per thread)
+  // double-float tall products with a narrow N: 64 x 32 tiles (4 x 2 outputs per thread), or
+  // 64 x 16 (4 x 1) when that pads N by at least N/8 less (s = 101: 112 columns, not 128)
   const bool narrow = std::is_same<ACC, df64>::value && !d.conj_a && d.epi == 0;
+  const bool tn1 = narrow && ((d.N + 31) / 32 * 32 - (d.N + 15) / 16 * 16) * 8 >= d.N;
   dim3 grid2((unsigned)((d.M + 63) / 64), (unsigned)((d.N + 31) / 32), (unsigned)d.splits);
+  dim3 grid1((unsigned)((d.M + 63) / 64), (unsigned)((d.N + 15) / 16), (unsigned)d.splits);
   if (d.conj_a)
     qgemm_kernel<ACC, TA, TB, TC, true><<<grid, 256, 0, st>>>(d);
+  else if (tn1 && bcplx)
+    qgemm_kernel<ACC, TA, TB, TC, false, true, false, 1><<<grid1, 256, 0, st>>>(d);
+  else if (tn1)
+    qgemm_kernel<ACC, TA, TB, TC, false, false, false, 1><<<grid1, 256, 0, st>>>(d);
   else if (narrow && bcplx)
     qgemm_kernel<ACC, TA, TB, TC, false, true, false, 2><<<grid2, 256, 0, st>>>(d);
   else if (narrow)
