@@ -7,9 +7,11 @@
 // P = Psi H, and the core products of Alg. 3.
 //
 // Tiling: a CTA of 256 threads computes a 64 x 64 quaternion tile; each thread owns a
-// 4 x 4 quaternion sub-tile (64 accumulators).  K is staged through shared memory in
-// double-buffered slices (8 deep in FP32, 4 in FP64) with a register prefetch of the next
-// slice.  split-K (grid z) accumulates with atomics into a pre-scaled C.
+// 4 x 4 quaternion sub-tile (64 accumulators) -- 64 x 32 or 64 x 16 tiles (4 x 2, 4 x 1 per
+// thread) for the double-float tall products, whichever pads N less.  K is staged through
+// shared memory in double-buffered slices (8 deep in FP32, 4 in FP64 / double-float) with a
+// register prefetch of the next slice.  split-K (grid z) accumulates with atomics into a
+// pre-scaled C.  The templates live in qs_gemm_kernels.cuh.
 #include <algorithm>
 #include <type_traits>
 
