@@ -178,7 +178,9 @@ QS_API qs_status qsketch_update_host(qs_handle_t h, const void* const A_host[4],
  * for a tensor-core handle with s > 256.  Items in the tensor-core modes (QS_PREC_BF16,
  * QS_PREC_BF16X3) are processed 32 at a time by one launch that zeroes their sketches and
  * one persistent fused-sketch launch over all their tiles; the other items run one update
- * each.  Everything is enqueued on `stream` with no host synchronisation and no allocation,
+ * each.  Only a failure of the driver's tensor-map encoding (QS_ERR_CUDA, which the
+ * argument checks leave no known cause for) is found after earlier groups of 32 were
+ * enqueued.  Everything is enqueued on `stream` with no host synchronisation and no allocation,
  * so the call can be captured in a CUDA graph (the handles' workspaces and the A planes
  * must then stay in place for every replay). */
 QS_API qs_status qsketch_update_batched(int32_t count, const qs_handle_t* handles,
