@@ -397,6 +397,45 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def batch_reference(args):
+    """The oracle's sketch (Sec. 4.1, FP64 on the host cores) on a bounded sample of the c4
+    batch: its first two matrices (same sizes and spectra as the GPU run's; the host's torch
+    generator draws other factor values), the metric scaled to A GB/s."""
+    import numpy as np
+    import oracle as O
+    import workloads as WL
+    spec = dict(WL.WORKLOADS["c4"])
+    sample = WL.make_c4_batch("cpu", dict(count=2))
+    vals = []
+    for it in range(args.warmup + args.steps):
+        t, abytes = 0.0, 0
+        for i, (m, n, k, A) in enumerate(sample):
+            s = 2 * k + 1
+            l = min(2 * s + 1, m, n)
+            A64 = A.double().numpy()
+            Om = O.draw_embedding(n, s, O.EMB_RADEMACHER, O.STREAM_OMEGA, spec["seed"] + i)
+            Psi = O.draw_embedding(l, m, O.EMB_RADEMACHER, O.STREAM_PSI, spec["seed"] + i)
+            t0 = time.perf_counter()
+            O.sketch(A64, Om, Psi)
+            t += time.perf_counter() - t0
+            abytes += 16 * m * n
+        if it >= args.warmup:
+            vals.append((abytes / t / 1e9, t))
+    v = statistics.median([g for g, _ in vals])
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample_desc = "first 2 matrices of the c4 batch: " + ", ".join(
+        f"{m}x{n} k={k}" for m, n, k, _ in sample)
+    out = {"impl": "reference", "metric": "one-pass quaternion approx: A GB/s & TFLOPS, split-BF16 vs FP32 at equal error",
+           "value": v, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": statistics.median([t for _, t in vals]) * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "c4: batch of quaternion matrices, sketch only (oracle sample)"},
+           "cpu_baseline": {"value": v, "unit": "GB/s", "cores": threads, "kind": "oracle",
+                            "sample": sample_desc},
+           "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
 def cpu_baseline(w, rows, reps=1):
     """The FP64 oracle on the host cores on a bounded sample: the first ``rows`` rows of the
     workload's matrix with the same s and l.  Returns (A GB/s, seconds, threads)."""
@@ -443,9 +482,9 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
-    if args.workload == "c4" and args.impl == "ours":
-        if rank == 0:      # the batch workload runs on one GPU
-            run_batch(args)
+    if args.workload == "c4":
+        if rank == 0:      # the batch workload runs on one GPU / on the host cores
+            run_batch(args) if args.impl == "ours" else batch_reference(args)
         return
     w = workload(args.workload)
     metric = "one-pass quaternion approx: A GB/s & TFLOPS, split-BF16 vs FP32 at equal error"
