@@ -1,7 +1,7 @@
 """Plain FP64 CPU oracle for the one-pass randomized quaternion low-rank approximation.
 
 This package is TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` may import it.  The CUDA product path never imports,
+CPU-baseline leg and the reference arm (``--impl reference``) of ``bench.py`` may import it.  The CUDA product path never imports,
 links or executes anything here, and nothing here imports the CUDA path: the two share
 no code.  The only common dependency is ``workloads`` (seeded synthetic inputs, which
 holds none of the method's arithmetic).
