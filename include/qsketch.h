@@ -188,18 +188,22 @@ QS_API qs_status qsketch_update_batched(int32_t count, const qs_handle_t* handle
                                         void* stream);
 
 /* Rangefinder H = F(Y) with R(H) = R(Y) (Sec. 3).
- *   QS_RF_PSEUDO_QR : Alg. 1.  Thin complex QR of Y_c (Cholesky-QR on the Gram of Y, with a
- *                     shift on breakdown), H from the Q factor, then n_correction steps
- *                     H <- (1-eps) H + eps (H^dagger)* (eq. CondNumReductionIter), eps from
- *                     three power iterates (Sec. 3.1).  n_correction in [0, 3]; 3 is the
- *                     paper's default.
- *   QS_RF_PSEUDO_SVD: Alg. 2.  Complex SVD of chi_Y, one left vector per duplicated pair,
- *                     SVD repair of the bad pairs.  n_correction is ignored.
+ *   QS_RF_PSEUDO_QR : Alg. 1.  Thin complex QR of Y_c (Cholesky-QR twice on the Gram of
+ *                     Y_c, with a shift on breakdown), H from the Q factor, then
+ *                     n_correction steps H <- (1-eps) H + eps (H^dagger)*
+ *                     (eq. CondNumReductionIter), eps from three power iterates (Sec. 3.1);
+ *                     the steps are accumulated as right factors and H = Y D is formed
+ *                     once.  n_correction in [0, 3]; 3 is the paper's default.
+ *   QS_RF_PSEUDO_SVD: Alg. 2.  Complex SVD of chi_Y -- computed as a quaternion
+ *                     Cholesky-QR (three passes) Y = Q R and the SVD of the 2s x 2s chi_R,
+ *                     since chi_Y = chi_Q chi_R -- one left vector per duplicated pair, SVD
+ *                     repair of the bad pairs.  n_correction is ignored.
  * Returns QS_OK, or an argument error; numerical rank warnings are sticky (see header). */
 QS_API qs_status qrangefinder(qs_handle_t h, int32_t kind, int32_t n_correction, void* stream);
 
-/* QB stage (Alg. 3): P = Psi H, then X = P^dagger W through the complex representation
- * (Alg. QLEQ) with a Householder QR of chi_P. */
+/* QB stage (Alg. 3): P = Psi H, then X = P^dagger W, the least-squares solution of
+ * Alg. QLEQ on chi_P, through a quaternion Cholesky-QR (twice) P = Q R: chi_P = chi_Q chi_R is
+ * a QR factorisation of chi_P that keeps its structure, and X = R^{-1} Q* W. */
 QS_API qs_status qonepass_core(qs_handle_t h, void* stream);
 
 /* Truncation stage (Alg. 4): the rank-r approximation A ~= H_r Sigma_r V_r* from the QSVD of
