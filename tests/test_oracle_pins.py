@@ -477,3 +477,23 @@ def test_truncation_planted_mistake_fails():
     r = 5
     Xbad = O.qmatmul(U[:, :, -r:], O.truncated_core(S[-r:], V[:, :, -r:]))
     assert abs(O.qnorm(X - Xbad) - np.sqrt(np.sum(S[r:] ** 2))) > 1e-3 * O.qnorm(X)
+
+
+def test_epsilon_rule_closed_form():
+    """Reading of Sec. 3.1's "two or three power iterates": three iterates v <- A^{-1} v / |.|
+    on A = chi_G from the normalised all-ones vector v0, eps = 1/sqrt(rho) of the last
+    Rayleigh quotient.  In the eigenbasis A = V diag(lam) V*, with c = V* v0, that quotient is
+    rho = sum |c_i|^2 lam_i^-5 / sum |c_i|^2 lam_i^-4 (a textbook identity, computed here by
+    a Hermitian eigendecomposition instead of linear solves).  Two iterates (rho with
+    exponents -3 / -2) must not match."""
+    rng = np.random.default_rng(17)
+    for s in (3, 6):
+        H = rng.standard_normal((4, 3 * s, s))   # no isolated small eigenvalue: the
+        A = O.chi(O.qmatmul(O.qconjT(H), H))      # iterate counts give different eps
+        lam, V = np.linalg.eigh(A)
+        v0 = np.ones(2 * s) / np.sqrt(2 * s)
+        c2 = np.abs(V.conj().T @ v0) ** 2
+        want = 1.0 / np.sqrt(np.sum(c2 * lam ** -5.0) / np.sum(c2 * lam ** -4.0))
+        assert abs(O.epsilon_rule(A) - want) <= 1e-10 * want
+        two = 1.0 / np.sqrt(np.sum(c2 * lam ** -3.0) / np.sum(c2 * lam ** -2.0))
+        assert abs(two - want) > 1e-3 * want
