@@ -497,3 +497,30 @@ def test_epsilon_rule_closed_form():
         assert abs(O.epsilon_rule(A) - want) <= 1e-10 * want
         two = 1.0 / np.sqrt(np.sum(c2 * lam ** -3.0) / np.sum(c2 * lam ** -2.0))
         assert abs(two - want) > 1e-3 * want
+
+
+def test_pair_classification_reading():
+    """Reading of Sec. 3.2's "good" pairs (singular values of chi_Y that still appear exactly
+    twice; the paper gives no tolerance): pair i = (S[2i], S[2i+1]) is good when its two
+    values agree within tau S[0] and it is separated by more than tau S[0] from both
+    neighbours; the bad part starts at the first failing pair.  Hand-built sequences with
+    tau = 1e-6 and their known counts of leading good pairs."""
+    tau = 1e-6
+    cases = [
+        ([5, 5, 3, 3, 1, 1], 3),                      # all pairs clean
+        ([5, 5, 3, 2.9, 1, 1], 1),                    # pair 1 split by 0.1 > tau * 5
+        ([5, 5, 3, 3 - 1e-7, 1, 1], 3),               # split below tau * 5: still a pair
+        ([5, 5, 5, 5, 1, 1], 0),                      # a repeated quaternion value: four equal
+        ([5, 5, 2, 2, 2, 2], 1),                      # repetition at the end
+        ([5, 5, 2, 2, 0, 0, 0, 0], 2),                # two zero quaternion values (rank loss)
+        ([5, 5, 2, 2, 0, 0], 3),                      # one zero value: an exact pair
+        ([5, 5, 1 + 4e-6, 1 + 4e-6, 1, 1], 1),        # neighbours 4e-6 apart < tau * 5
+    ]
+    for S, g in cases:
+        S = np.asarray(S, dtype=float)
+        assert O.classify_pairs(S, len(S) // 2, tau=tau) == g, (S, g)
+    # the default tau = 2 s 1e3 u: pairs closer than that relative to S[0] are not separated
+    s = 4
+    t0 = 2 * s * 1e3 * U64
+    S = np.array([1, 1, 0.5, 0.5, 0.5 - 0.5 * t0, 0.5 - 0.5 * t0, 0.1, 0.1])
+    assert O.classify_pairs(S, s) == 1
