@@ -524,3 +524,15 @@ def test_pair_classification_reading():
     t0 = 2 * s * 1e3 * U64
     S = np.array([1, 1, 0.5, 0.5, 0.5 - 0.5 * t0, 0.5 - 0.5 * t0, 0.1, 0.1])
     assert O.classify_pairs(S, s) == 1
+
+
+def test_philox_known_answers():
+    """The counter-based generator both sides implement, against the known-answer vectors
+    published with its definition (tests/golden/philox4x32_10_kat.txt)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        w = [int(x, 16) for x in r]
+        out = O.philox4x32_10(*(np.array([v], dtype=np.uint64) for v in w[:4]), w[4], w[5])
+        assert [int(np.asarray(x).ravel()[0]) for x in out] == w[6:10]
