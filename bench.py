@@ -167,7 +167,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     qs = pkg.QSketch(cfg["m"], cfg["n"], cfg["s"], cfg["l"], emb=cfg["emb"], prec=args.prec,
-                     seed=w["seed"] + rank)
+                     seed=w["seed"] + rank, rf_prec=args.rf_prec)
     err_out = torch.zeros(1, dtype=torch.float64, device=dev)
     E = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
 
@@ -283,22 +283,57 @@ def run_ours(args, rank, world, local_rank):
                   cfg=cfg, w=w, e2e_gbs=world * abytes / (e2e_ms * 1e-3) / 1e9,
                   h2d=A.numel() * A.element_size(), d2h=8, truncate_ms=truncate_ms, trunc_rank=k,
                   e2e_modes=e2e, e2e_err=e2e_err, e2e_status=e2e_status)
-    # FP32 SIMT comparison path at equal error (rank 0 only, device resident)
+    # the stages after the sketch in the other arithmetics, on this step's Y and W (rank 0,
+    # informational): native FP64, and the mixed mode with its device-chosen FP32 steps
+    if rank == 0 and args.prec != "fp64" and not args.no_compare:
+        result["rf_variants"] = {}
+        for rf in ("fp64", "mixed"):
+            if rf == args.rf_prec:
+                continue
+            qv = pkg.QSketch(cfg["m"], cfg["n"], cfg["s"], cfg["l"], emb=cfg["emb"], prec=args.prec,
+                             seed=w["seed"], rf_prec=rf)
+            qv.get("Y").copy_(qs.get("Y"))
+            qv.get("W").copy_(qs.get("W"))
+            for _ in range(2):
+                qv.rangefinder(args.rangefinder, 3)
+                qv.core()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            reps = 3
+            ev[0].record(stream)
+            for _ in range(reps):
+                qv.rangefinder(args.rangefinder, 3)
+            ev[1].record(stream)
+            for _ in range(reps):
+                qv.core()
+            ev[2].record(stream)
+            err_v = float(qv.error(A).item())
+            torch.cuda.synchronize()
+            result["rf_variants"][rf] = dict(
+                rangefinder_ms=ev[0].elapsed_time(ev[1]) / reps,
+                core_ms=ev[1].elapsed_time(ev[2]) / reps,
+                final_rel_error=err_v, device_status=int(qv.device_status()))
+            qv.close()
+    # FP32 SIMT comparison path at equal error (rank 0 only, device resident): the sketch
+    # timed over 20 repetitions after warm-up, the whole path once for its final error
     if rank == 0 and args.prec != "fp32" and not args.no_compare:
         qs32 = pkg.QSketch(cfg["m"], cfg["n"], cfg["s"], cfg["l"], emb=cfg["emb"], prec="fp32",
-                           seed=w["seed"])
+                           seed=w["seed"], rf_prec=args.rf_prec)
+        for _ in range(args.warmup):
+            qs32.update(A, theta=0.0)
+        reps32 = 20
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
-        for it in range(2):
-            s0.record(stream)
-            qs32.reset(seed=w["seed"])
+        s0.record(stream)
+        for _ in range(reps32):
             qs32.update(A, theta=0.0)
-            s1.record(stream)
-            qs32.rangefinder(args.rangefinder, 3)
-            qs32.core()
-            e32 = float(qs32.error(A).item())
+        s1.record(stream)
+        qs32.reset(seed=w["seed"])
+        qs32.update(A, theta=0.0)
+        qs32.rangefinder(args.rangefinder, 3)
+        qs32.core()
+        e32 = float(qs32.error(A).item())
         torch.cuda.synchronize()
-        result["fp32"] = dict(sketch_ms=s0.elapsed_time(s1), err=e32)
+        result["fp32"] = dict(sketch_ms=s0.elapsed_time(s1) / reps32, reps=reps32, err=e32)
         qs32.close()
     qs.close()
     return result
@@ -469,6 +504,8 @@ def main():
     ap.add_argument("--workload", default="c2",
                     help="c2 (default: the one-pass step) or c4 (the batched sketch, one GPU)")
     ap.add_argument("--rangefinder", default="pseudo_qr")
+    ap.add_argument("--rf-prec", default="df64", choices=["df64", "fp64", "mixed"],
+                    help="arithmetic of the rangefinder, core and truncation stages")
     ap.add_argument("--cpu-rows", type=int, default=4096)
     ap.add_argument("--stream-rows", type=int, default=1024,
                     help="row-block height of the streamed host update in the e2e loop")
@@ -489,7 +526,7 @@ def main():
     config = {"workload": f"{w['name']}: quaternion A {w['m']}x{w['n']} FP32 planes, "
                           f"sigma_i=i^-2, k={w['k']}, s={w['s']}, l={w['l']}, Gaussian Omega/Psi",
               "m": w["m"], "n": w["n"], "s": w["s"], "l": w["l"], "prec": args.prec,
-              "rangefinder": args.rangefinder, "n_correction": 3,
+              "rangefinder": args.rangefinder, "n_correction": 3, "rf_prec": args.rf_prec,
               "l2": "inputs larger than L2 (A is 1.07 GB per step)", "parallelism": "replicas"}
 
     if args.impl == "reference":
@@ -544,8 +581,8 @@ def main():
     out = {"metric": metric, "value": res["gbs"], "unit": "GB/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": {"bf16x3": "bf16x3+f64", "bf16": "bf16+f64", "fp32": "f32+f64",
-                     "fp64": "f64"}[args.prec],
+           "dtype": "f64" if args.prec == "fp64" else args.prec.replace("fp32", "f32") + "+" + {
+               "df64": "df64", "fp64": "f64", "mixed": "df64/f32"}[args.rf_prec],
            "data": "synthetic", "config": config, "roofline": roof,
            "tflops": {"useful_step": world * flops / (res["ms"] * 1e-3) / 1e12,
                       "useful_sketch": flops / (sk_ms * 1e-3) / 1e12,
@@ -564,8 +601,15 @@ def main():
                    "final_err": res["e2e_err"], "device_status": res["e2e_status"]},
            "gpu_launches": res["launches"], "gpu_launches_per_step": res["launches"] / args.steps,
            "clocks": res["clocks"]}
+    if "rf_variants" in res:
+        out["stages_after_sketch_variants"] = res["rf_variants"]
     if "fp32" in res:
-        out["fp32_path"] = {"sketch_ms": res["fp32"]["sketch_ms"],
+        clk = (res["clocks"] or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        fp32_peak = N_SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+        out["fp32_path"] = {"sketch_ms": res["fp32"]["sketch_ms"], "reps": res["fp32"]["reps"],
+                            "sketch_tflops": flops / (res["fp32"]["sketch_ms"] * 1e-3) / 1e12,
+                            "fp32_alu_peak_tflops": fp32_peak,
+                            "frac_of_fp32_peak": flops / (res["fp32"]["sketch_ms"] * 1e-3) / 1e12 / fp32_peak,
                             "final_rel_error": res["fp32"]["err"],
                             "sketch_speedup_vs_fp32": res["fp32"]["sketch_ms"] / sk_ms,
                             "error_ratio": res["final_err"] / res["fp32"]["err"]}

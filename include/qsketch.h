@@ -81,14 +81,34 @@ typedef enum { QS_PREC_FP64 = 0, QS_PREC_FP32 = 1, QS_PREC_BF16 = 2, QS_PREC_BF1
 
 typedef enum { QS_RF_PSEUDO_QR = 0, QS_RF_PSEUDO_SVD = 1 } qs_rangefinder_kind;
 
+/* Arithmetic of the stages after the sketch: the rangefinders (Alg. 1, Alg. 2), the QB stage
+ * (Alg. 3 with Alg. QLEQ) and the truncation stage (Alg. 4).  The paper runs all of them in
+ * FP64 (Sec. 5); their stability depends on kappa(Y) and kappa(Psi H).  With
+ * QS_PREC_FP64 every stage is native FP64 whatever this field says.  For the FP32-storage
+ * modes (FP32, BF16, BF16X3; Y and W are FP32):
+ *   DF64  : every Gram matrix, every s x s factorisation and product, H = Y D, P = Psi H and
+ *           X = P^dagger W accumulate in double-float (an unevaluated sum of two FP32
+ *           numbers, about 48 significant bits, on the FP32 pipes); H, X and the
+ *           truncation factors are stored in FP64.  Agrees with FP64 to a few units of
+ *           2^-48 times the conditioning of the step.
+ *   FP64  : the same steps in native FP64 arithmetic (FP32 inputs widened exactly);
+ *           H and X stored in FP64.  GB300 runs FP64 at about 1/60 of its FP32 rate.
+ *   MIXED : double-float by default, but a factorisation runs in FP32 when a kappa estimate
+ *           made on the device shows FP32 suffices (later corrections when
+ *           kappa(H_{k-1}) < 1e3, the core's factorisations when kappa(H) < 30), P = Psi H
+ *           and X = P^dagger W accumulate in FP32 after the corrections, and H and X are
+ *           stored in FP32. */
+typedef enum { QS_RF_PREC_DF64 = 0, QS_RF_PREC_FP64 = 1, QS_RF_PREC_MIXED = 2 } qs_rf_precision;
+
 /* Objects readable through qsketch_get. */
 typedef enum {
   QS_OBJ_Y = 0,      /* m x s sketch Y = A Omega                               */
   QS_OBJ_W = 1,      /* l x n sketch W = Psi A                                 */
   QS_OBJ_OMEGA = 2,  /* n x s test matrix                                      */
   QS_OBJ_PSI = 3,    /* l x m test matrix                                      */
-  QS_OBJ_H = 4,      /* m x s rangefinder (after qrangefinder)                 */
-  QS_OBJ_X = 5,      /* s x n core factor (after qonepass_core)                */
+  QS_OBJ_H = 4,      /* m x s rangefinder (after qrangefinder); FP64 unless
+                        rf_prec is QS_RF_PREC_MIXED in an FP32-storage mode     */
+  QS_OBJ_X = 5,      /* s x n core factor (after qonepass_core); stored like H  */
   QS_OBJ_PSIH = 6,   /* l x s product Psi H (after qonepass_core)              */
   QS_OBJ_SCALARS = 7, /* 16 doubles: [0] last relative error, [1] kappa estimate of H,
                         [2..4] correction parameters eps_1..eps_3, [5] pseudo-SVD bad
@@ -109,6 +129,8 @@ typedef struct {
   uint64_t seed;    /* key of the counter-based generator                         */
   int32_t pure;     /* 1: A_w == 0 (pure quaternion); plane w is never read        */
   int32_t flags;    /* 0, or QS_FLAG_TEST_WITHHOLD_COPY (tensor-core precisions)  */
+  int32_t rf_prec;  /* qs_rf_precision of the stages after the sketch (0: DF64)   */
+  int32_t reserved; /* must be 0                                                  */
 } qs_config;
 
 /* qs_config.flags.  QS_FLAG_TEST_WITHHOLD_COPY is a test aid for the failure path of the

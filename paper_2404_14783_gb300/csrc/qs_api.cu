@@ -47,12 +47,20 @@ bool valid_cfg(const qs_config* c) {
   if (c->pure != 0 && c->pure != 1) return false;
   if (c->flags & ~QS_FLAG_TEST_WITHHOLD_COPY) return false;
   if (c->flags && c->prec != QS_PREC_BF16 && c->prec != QS_PREC_BF16X3) return false;
+  if (c->rf_prec < QS_RF_PREC_DF64 || c->rf_prec > QS_RF_PREC_MIXED || c->reserved != 0) return false;
   return true;
+}
+
+// H, X and the truncation factors are FP64 unless the stages after the sketch run mixed
+// (FP32-storage modes with QS_RF_PREC_MIXED).
+inline bool hx_f64(const qs_config& c) {
+  return c.prec == QS_PREC_FP64 || c.rf_prec != QS_RF_PREC_MIXED;
 }
 
 // Workspace layout; fills offsets of h (if non-null) and returns total bytes.
 size_t plan(const qs_config& c, qs_handle_s* h) {
   const size_t es = c.prec == QS_PREC_FP64 ? 8 : 4;
+  const size_t ehx = hx_f64(c) ? 8 : 4;   // H, X, H_r, X_r
   const size_t m = c.m, n = c.n, s = c.s, l = c.l;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -67,8 +75,8 @@ size_t plan(const qs_config& c, qs_handle_s* h) {
   const size_t sy = (s + 3) / 4 * 4;   // Y rows padded to 16 bytes (vector reductions)
   size_t o_y = take(4 * m * sy * es);
   size_t o_w = take(4 * l * n * es);
-  size_t o_h = take(4 * m * s * es);
-  size_t o_x = take(4 * s * n * es);
+  size_t o_h = take(4 * m * s * ehx);
+  size_t o_x = take(4 * s * n * ehx);
   size_t o_gram = take(2 * 4 * m * s * 8);  // two FP64 tall temporaries (m x s)
   const size_t small_bytes = kSmallSlots * align_up(4 * s * s * 8);
   size_t o_small = take(small_bytes);
@@ -80,10 +88,11 @@ size_t plan(const qs_config& c, qs_handle_s* h) {
   size_t o_psvd = take(psvd_work_bytes(c.s));
   size_t o_epack = take(tc_mode(c.prec) ? err_tc_pack_bytes(c.m, c.n, c.s) : 0);
   // truncation stage: X* (n x s, FP64), H_r (m x s), X_r (s x n), sigma (s)
-  size_t o_trunc = take(align_up(4 * n * s * 8) + align_up(4 * m * s * es) + align_up(4 * s * n * es) +
+  size_t o_trunc = take(align_up(4 * n * s * 8) + align_up(4 * m * s * ehx) + align_up(4 * s * n * ehx) +
                         s * 8);
   if (h) {
     h->esize = (int)es;
+    h->hx_esize = (int)ehx;
     h->off_status = o_status; h->off_scalars = o_scal; h->off_omega = o_om; h->off_psi = o_psi;
     h->off_y = o_y; h->off_w = o_w; h->off_h = o_h; h->off_x = o_x; h->off_gram = o_gram;
     h->off_small = o_small; h->off_p = o_p; h->off_core = o_core; h->off_pack = o_pack;
@@ -116,24 +125,28 @@ struct Ctx {
   qs_handle_s* h;
   cudaStream_t st;
   int64_t m, n, s, l;
-  bool f64;
+  bool f64;     // A, Omega, Psi, Y, W are FP64 (QS_PREC_FP64)
+  bool hx64;    // H, X, H_r, X_r are FP64
+  int rf;       // qs_rf_precision of the stages after the sketch
+  bool mixed() const { return !f64 && rf == QS_RF_PREC_MIXED; }
   Mat omega() const { return {h->ws + h->off_omega, s, n * s, f64}; }
   Mat psi() const { return {h->ws + h->off_psi, m, l * m, f64}; }
   int64_t sy() const { return (s + 3) / 4 * 4; }
   Mat Y() const { return {h->ws + h->off_y, sy(), m * sy(), f64}; }
   Mat W() const { return {h->ws + h->off_w, n, l * n, f64}; }
-  Mat H() const { return {h->ws + h->off_h, s, m * s, f64}; }
-  Mat X() const { return {h->ws + h->off_x, n, s * n, f64}; }
+  Mat H() const { return {h->ws + h->off_h, s, m * s, hx64}; }
+  Mat X() const { return {h->ws + h->off_x, n, s * n, hx64}; }
   Mat T() const { return {h->ws + h->off_gram, s, m * s, 1}; }
   // truncation stage: X* (n x s FP64), H_r (m x r, ld r), X_r (r x n), sigma (r doubles)
   Mat XT() const { return {h->ws + h->off_trunc, s, n * s, 1}; }
-  Mat Hr(int64_t r) const { return {h->ws + h->off_trunc + align_up(4 * n * s * 8), r, m * r, f64}; }
+  Mat Hr(int64_t r) const { return {h->ws + h->off_trunc + align_up(4 * n * s * 8), r, m * r, hx64}; }
   Mat Xr(int64_t r) const {
-    return {h->ws + h->off_trunc + align_up(4 * n * s * 8) + align_up(4 * m * s * h->esize), n, r * n, f64};
+    return {h->ws + h->off_trunc + align_up(4 * n * s * 8) + align_up(4 * m * s * h->hx_esize), n, r * n,
+            hx64};
   }
   double* sigma() const {
     return reinterpret_cast<double*>(h->ws + h->off_trunc + align_up(4 * n * s * 8) +
-                                     align_up(4 * m * s * h->esize) + align_up(4 * s * n * h->esize));
+                                     align_up(4 * m * s * h->hx_esize) + align_up(4 * s * n * h->hx_esize));
   }
   Mat T2() const { return {h->ws + h->off_gram + 4 * m * s * 8, s, m * s, 1}; }
   Mat small(int i) const {
@@ -145,11 +158,17 @@ struct Ctx {
     if (i < 3) return {base + i * align_up(4 * l * s * 8), s, l * s, 1};
     return {base + 3 * align_up(4 * l * s * 8), l, s * l, 1};
   }
-  // FP64-class accumulation: native FP64 in the FP64 mode, double-float otherwise
-  int acc_hi() const { return f64 ? 1 : 2; }
+  // FP64-class accumulation: native FP64 in the FP64 mode and with QS_RF_PREC_FP64,
+  // double-float otherwise
+  int acc_hi() const { return (f64 || rf == QS_RF_PREC_FP64) ? 1 : 2; }
   int32_t* status() const { return h->d_status(); }
   double* scalars() const { return h->d_scalars(); }
 };
+
+Ctx make_ctx(qs_handle_s* h, cudaStream_t st) {
+  const qs_config& c = h->cfg;
+  return Ctx{h, st, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64, hx_f64(c), c.rf_prec};
+}
 
 inline bool is_small(int64_t M, int64_t N) { return M <= 512 && N <= 512; }
 
@@ -225,8 +244,9 @@ cudaError_t chol_inv(const Ctx& x, const Mat& G, const Mat& L, const Mat& Li, in
   double* sc = x.scalars();
   if (s <= qchol_inv_max_n())
     return launch_qchol_inv((const double*)G.p, G.ld, G.ps, (double*)Li.p, Li.ld, Li.ps, s,
-                            complex_only, allow_shift, shift_rows, slot, kKappaStop, !x.f64, st, sc,
-                            fail_bits, (double*)L.p, x.st, fp32_gate, fp32_below);
+                            complex_only, allow_shift, shift_rows, slot, kKappaStop, x.acc_hi() == 2,
+                            st, sc, fail_bits, (double*)L.p, x.st, x.mixed() ? fp32_gate : nullptr,
+                            fp32_below);
   cudaError_t e = launch_qchol((const double*)G.p, G.ld, G.ps, (double*)L.p, L.ld, L.ps, s,
                                complex_only, allow_shift, shift_rows, st, sc, fail_bits, x.st);
   if (e == cudaSuccess && slot >= 0)
@@ -262,7 +282,7 @@ qs_status pseudo_qr(const Ctx& x, int ncorr) {
   // (Alg. 1 step 4) corrections H <- (1-eps) H + eps (H^dagger)* = H ((1-eps) I + eps G^{-1})
   for (int k = 0; k < ncorr; ++k) {
     const double* lo = nullptr;
-    if (!x.f64 && k > 0) {   // snapshot: the factorisation itself rewrites the kappa estimate
+    if (x.mixed() && k > 0) {   // snapshot: the factorisation itself rewrites the kappa estimate
       QS_CU(cudaMemcpyAsync(sc + kScFp32Gate, sc + kScKappa, sizeof(double), cudaMemcpyDeviceToDevice,
                             x.st));
       lo = sc + kScFp32Gate;
@@ -304,21 +324,19 @@ qs_status core_solve(const Ctx& x) {
             R2 = x.small(5), S = x.small(6);
   int32_t* st = x.status();
   double* sc = x.scalars();
-  // (Alg. 3 step 2) P = Psi H.  FP32 modes: after corrections (or pseudo-SVD) kappa(P) is
-  // small and an FP32 product, widened for the small solve, loses nothing; an uncorrected
-  // pseudo-QR H has kappa(Y), which would amplify the FP32 rounding of P into X, so that
-  // product accumulates in double-float.
-  if (x.f64) {
-    QS_CU(gemm(x, x.psi(), false, x.H(), P, l, s, x.m, 1.0, 0.0, 1, true));
-  } else if (!x.h->h_well_conditioned) {
-    QS_CU(gemm(x, x.psi(), false, x.H(), P, l, s, x.m, 1.0, 0.0, 2, true));
+  // (Alg. 3 step 2) P = Psi H in the FP64 class.  Mixed FP32 modes: after corrections (or
+  // pseudo-SVD) kappa(P) is small and an FP32 product, widened for the small solve, keeps
+  // the FP32 level of the sketch; an uncorrected pseudo-QR H has kappa(Y), which would
+  // amplify the FP32 rounding of P into X, so that product accumulates in double-float.
+  if (!x.mixed() || !x.h->h_well_conditioned) {
+    QS_CU(gemm(x, x.psi(), false, x.H(), P, l, s, x.m, 1.0, 0.0, x.acc_hi(), true));
   } else {
     const Mat P32{x.core(0).p, s, l * s, 0};
     QS_CU(gemm(x, x.psi(), false, x.H(), P32, l, s, x.m, 1.0, 0.0, 0, true));
     QS_CU(launch_qcopy(P32.p, 0, P32.ld, P32.ps, P.p, 1, P.ld, P.ps, l, s, x.st));
   }
   // Alg. QLEQ on chi_P: QR of P (quaternion Cholesky-QR, twice), X = R^{-1} Q* W
-  const double* lo = (!x.f64 && x.h->h_well_conditioned) ? sc + kScKappa : nullptr;
+  const double* lo = (x.mixed() && x.h->h_well_conditioned) ? sc + kScKappa : nullptr;
   QS_CU(gram(x, P, l, s, G));
   QS_CU(chol_inv(x, G, L, L1i, 0, 1, 4.0 * l, -1, kDevRank, false, lo));
   QS_CU(launch_qconjT(L1i.p, 1, L1i.ld, L1i.ps, R1.p, 1, R1.ld, R1.ps, s, s, x.st));
@@ -331,13 +349,13 @@ qs_status core_solve(const Ctx& x) {
   QS_CU(gemm(x, Qp, false, S, ZT, l, s, s, 1.0, 0.0, x.acc_hi(), false));        // (P^dagger)* = Q R^{-*}
   // P^dagger (s x l), in the working precision of W; with an uncorrected H the norm of
   // P^dagger is kappa(H) times that of P, so it stays FP64 and X accumulates in double-float
-  const bool wide = x.f64 || !x.h->h_well_conditioned;
+  const bool wide = !x.mixed() || !x.h->h_well_conditioned;
   const Mat Zw{Z.p, Z.ld, Z.ps, wide ? 1 : 0};
   QS_CU(launch_qconjT(ZT.p, 1, ZT.ld, ZT.ps, Zw.p, Zw.f64, Zw.ld, Zw.ps, (int)l, s, x.st));
-  // X = P^dagger W (s x n)
-  // (split-K partial sums would meet in an FP32 output, so the double-float case runs unsplit)
-  QS_CU(gemm(x, Zw, false, x.W(), x.X(), s, x.n, l, 1.0, 0.0, x.f64 ? 1 : (wide ? 2 : 0),
-             x.f64 || !wide));
+  // X = P^dagger W (s x n).  Split-K partial sums are added with atomics into X; an FP32 X
+  // (mixed modes) would round every partial, so the double-float case there runs unsplit.
+  const int acc_x = wide ? x.acc_hi() : 0;
+  QS_CU(gemm(x, Zw, false, x.W(), x.X(), s, x.n, l, 1.0, 0.0, acc_x, x.X().f64 || acc_x == 0));
   return QS_OK;
 }
 
@@ -409,7 +427,7 @@ qs_status qsketch_create(const qs_config* cfg, void* workspace, size_t bytes, vo
   h->ws = static_cast<char*>(workspace);
   h->ws_bytes = bytes;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Ctx x{h, st, cfg->m, cfg->n, cfg->s, cfg->l, cfg->prec == QS_PREC_FP64};
+  Ctx x = make_ctx(h, st);
   const bool f64 = x.f64;
   cudaError_t e = cudaMemsetAsync(h->ws, 0, h->off_omega, st);
   if (e == cudaSuccess) e = launch_draw(x.omega().p, f64, cfg->n, cfg->s, cfg->emb, kStreamOmega, cfg->seed, st);
@@ -434,7 +452,7 @@ qs_status qsketch_update(qs_handle_t h, const void* const A_planes[4], int64_t l
     return QS_ERR_INVALID;
   if (lda < nb || !std::isfinite(theta) || !std::isfinite(eta)) return QS_ERR_INVALID;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Ctx x{h, st, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64};
+  Ctx x = make_ctx(h, st);
   if (theta != 1.0) {
     QS_CU(launch_scale(x.Y().p, x.f64, c.m, c.s, x.Y().ld, x.Y().ps, theta, st));
     QS_CU(launch_scale(x.W().p, x.f64, c.l, c.n, c.n, c.l * c.n, theta, st));
@@ -518,7 +536,7 @@ qs_status qrangefinder(qs_handle_t h, int32_t kind, int32_t n_correction, void* 
   if (n_correction < 0 || n_correction > 3) return QS_ERR_INVALID;
   const qs_config& c = h->cfg;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Ctx x{h, st, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64};
+  Ctx x = make_ctx(h, st);
   QS_CU(launch_clear_stop(x.status(), st));
   QS_CU(cudaMemsetAsync(x.scalars() + kScKappa, 0, sizeof(double) * 6, st));
   QS_CU(cudaMemsetAsync(x.scalars() + kScGate, 0, sizeof(double), st));
@@ -531,7 +549,7 @@ qs_status qonepass_core(qs_handle_t h, void* stream) {
   if (!h) return QS_ERR_INVALID;
   const qs_config& c = h->cfg;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Ctx x{h, st, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64};
+  Ctx x = make_ctx(h, st);
   return core_solve(x);
 }
 
@@ -544,7 +562,7 @@ qs_status qtruncate(qs_handle_t h, int64_t r, void* stream) {
   const qs_config& c = h->cfg;
   if (r < 1 || r > c.s) return QS_ERR_INVALID;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Ctx x{h, st, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64};
+  Ctx x = make_ctx(h, st);
   const int s = (int)c.s;
   const Mat XT = x.XT(), G = x.small(0), L = x.small(1), Li = x.small(2), U = x.small(3);
   const Mat X = x.X(), H = x.H(), Hr = x.Hr(r), Xr = x.Xr(r);
@@ -565,26 +583,27 @@ qs_status qreconstruct_error(qs_handle_t h, const void* const A_planes[4], int64
   const qs_config& c = h->cfg;
   if (lda < c.n) return QS_ERR_INVALID;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Ctx x{h, st, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64};
+  Ctx x = make_ctx(h, st);
   double* sc = x.scalars();
   QS_CU(cudaMemsetAsync(sc + kScErrNum, 0, 2 * sizeof(double), st));
   const void* Ap[4] = {A_planes[0], A_planes[1], A_planes[2], A_planes[3]};
   if (c.pure) Ap[0] = nullptr;
   if (tc_mode(c.prec) && err_tc_supported(Ap, lda)) {
     // tensor-core modes: H X on the tensor cores (split BF16), residual in FP32
-    QS_CU(launch_err_tc(Ap, lda, static_cast<const float*>(x.H().p), static_cast<const float*>(x.X().p),
-                        c.m, c.n, c.s, h->ws + h->off_epack, sc + kScErrNum, x.status(), st));
+    QS_CU(launch_err_tc(Ap, lda, x.H().p, x.X().p, x.hx64, c.m, c.n, c.s, h->ws + h->off_epack,
+                        sc + kScErrNum, x.status(), st));
     QS_CU(launch_finalize_err(sc, rel_err_dev, st));
     return QS_OK;
   }
   GemmDesc d{};
   d.M = c.m; d.N = c.n; d.K = c.s;
-  x.H().cplanes(d.a); d.lda = c.s; d.a_f64 = x.f64;
-  x.X().cplanes(d.b); d.ldb = c.n; d.b_f64 = x.f64;
+  x.H().cplanes(d.a); d.lda = c.s; d.a_f64 = x.hx64;
+  x.X().cplanes(d.b); d.ldb = c.n; d.b_f64 = x.hx64;
   for (int p = 0; p < 4; ++p) d.c[p] = const_cast<void*>(A_planes[p]);
   if (c.pure) d.c[0] = nullptr;
   d.ldc = lda; d.c_f64 = x.f64;
-  d.alpha = 1.0; d.beta = 0.0; d.acc_f64 = x.f64; d.splits = 1;
+  // FP64 mode: FP64; FP32 A with FP64 factors: double-float; mixed FP32 mode: FP32
+  d.alpha = 1.0; d.beta = 0.0; d.acc_f64 = x.f64 ? 1 : (x.hx64 ? 2 : 0); d.splits = 1;
   d.epi = 1; d.err = sc + kScErrNum;
   QS_CU(launch_qgemm(d, st));
   QS_CU(launch_finalize_err(sc, rel_err_dev, st));
@@ -595,7 +614,7 @@ qs_status qsketch_get(qs_handle_t h, int32_t which, void** dev_ptr, int64_t* ld,
                       int64_t* plane_stride, int32_t* dtype) {
   if (!h || !dev_ptr) return QS_ERR_INVALID;
   const qs_config& c = h->cfg;
-  Ctx x{h, nullptr, c.m, c.n, c.s, c.l, c.prec == QS_PREC_FP64};
+  Ctx x = make_ctx(h, nullptr);
   Mat v{};
   switch (which) {
     case QS_OBJ_Y: v = x.Y(); break;

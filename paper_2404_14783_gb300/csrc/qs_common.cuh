@@ -81,7 +81,8 @@ enum : uint32_t { kStreamOmega = 1, kStreamPsi = 2, kStreamPsvdF = 3 };
 // ------------------------------------------------------------------ host-side handle
 struct qs_handle_s {
   qs_config cfg;
-  int esize;            // bytes per element of A, Omega, Psi, Y, W, H, X (8 or 4)
+  int esize;            // bytes per element of A, Omega, Psi, Y, W (8 or 4)
+  int hx_esize;         // bytes per element of H, X, H_r, X_r (8 or 4)
   char* ws;             // workspace base (device)
   size_t ws_bytes;
   // slab offsets (bytes) into ws

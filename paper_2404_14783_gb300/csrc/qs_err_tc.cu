@@ -303,7 +303,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 // FP32 planes (rows x cols, leading dimension ld, plane stride ps) -> BF16 hi/lo pairs
 // dst[(2 plane + hl) * drows + r][k] with K = cols (or rows when transposed) padded to dld
 // (zeros), the K-major operand layout of err_tc_kernel.
-__global__ void pack_hl_kernel(const float* __restrict__ src, int64_t rows, int64_t cols,
+template <typename TS>
+__global__ void pack_hl_kernel(const TS* __restrict__ src, int64_t rows, int64_t cols,
                                int64_t ld, int64_t ps, int transpose, __nv_bfloat16* __restrict__ dst,
                                int64_t drows, int64_t dld) {
   const int64_t per_plane = drows * dld;
@@ -312,14 +313,17 @@ __global__ void pack_hl_kernel(const float* __restrict__ src, int64_t rows, int6
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t pl = e / per_plane, rc = e % per_plane;
     const int64_t r = rc / dld, k = rc % dld;
-    float v = 0.f;
+    TS v = TS(0);
     if (transpose) {  // dst row r = src column r, k = src row
       if (k < rows && r < cols) v = src[pl * ps + k * ld + r];
     } else {
       if (r < rows && k < cols) v = src[pl * ps + r * ld + k];
     }
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(h));
+    // hi = v rounded to BF16; lo = the rest rounded to BF16 (an FP64 v is first rounded to
+    // FP32, whose rounding error, 2^-24 relative, is far below the lo part's 2^-16)
+    const float vf = (float)v;
+    const __nv_bfloat16 h = __float2bfloat16_rn(vf);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(vf - __bfloat162float(h));
     dst[(2 * pl + 0) * per_plane + r * dld + k] = h;
     dst[(2 * pl + 1) * per_plane + r * dld + k] = lo;
   }
@@ -341,16 +345,26 @@ bool err_tc_supported(const void* const A[4], int64_t lda) {
   return true;
 }
 
-cudaError_t launch_err_tc(const void* const A[4], int64_t lda, const float* H, const float* X,
-                          int64_t m, int64_t n, int64_t s, void* pack, double* err, int32_t* status,
-                          cudaStream_t st) {
+cudaError_t launch_err_tc(const void* const A[4], int64_t lda, const void* H, const void* X,
+                          int hx_f64, int64_t m, int64_t n, int64_t s, void* pack, double* err,
+                          int32_t* status, cudaStream_t st) {
   const int64_t ks = (s + 15) / 16 * 16;
   __nv_bfloat16* hp = static_cast<__nv_bfloat16*>(pack);
   __nv_bfloat16* xp = hp + 8 * m * ks;
   auto blocks = [](int64_t tot) { return (int)std::min<int64_t>((tot + 255) / 256, 16 * kNumSMs); };
-  pack_hl_kernel<<<blocks(4 * m * ks), 256, 0, st>>>(H, m, s, s, m * s, 0, hp, m, ks);
-  count_launch();
-  pack_hl_kernel<<<blocks(4 * n * ks), 256, 0, st>>>(X, s, n, n, s * n, 1, xp, n, ks);
+  if (hx_f64) {
+    pack_hl_kernel<double><<<blocks(4 * m * ks), 256, 0, st>>>(static_cast<const double*>(H), m, s, s,
+                                                              m * s, 0, hp, m, ks);
+    count_launch();
+    pack_hl_kernel<double><<<blocks(4 * n * ks), 256, 0, st>>>(static_cast<const double*>(X), s, n, n,
+                                                              s * n, 1, xp, n, ks);
+  } else {
+    pack_hl_kernel<float><<<blocks(4 * m * ks), 256, 0, st>>>(static_cast<const float*>(H), m, s, s,
+                                                             m * s, 0, hp, m, ks);
+    count_launch();
+    pack_hl_kernel<float><<<blocks(4 * n * ks), 256, 0, st>>>(static_cast<const float*>(X), s, n, n,
+                                                             s * n, 1, xp, n, ks);
+  }
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

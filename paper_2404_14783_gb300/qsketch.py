@@ -17,6 +17,7 @@ QS_OK, QS_ERR_INVALID, QS_ERR_NOMEM, QS_ERR_CUDA, QS_ERR_RANK, QS_ERR_NUMERIC, \
 QS_EMB_GAUSSIAN, QS_EMB_RADEMACHER = 0, 1
 QS_PREC_FP64, QS_PREC_FP32, QS_PREC_BF16, QS_PREC_BF16X3 = 0, 1, 2, 3
 QS_RF_PSEUDO_QR, QS_RF_PSEUDO_SVD = 0, 1
+QS_RF_PREC_DF64, QS_RF_PREC_FP64, QS_RF_PREC_MIXED = 0, 1, 2
 QS_OBJ_Y, QS_OBJ_W, QS_OBJ_OMEGA, QS_OBJ_PSI, QS_OBJ_H, QS_OBJ_X, QS_OBJ_PSIH, \
     QS_OBJ_SCALARS, QS_OBJ_HR, QS_OBJ_XR, QS_OBJ_SIGMA = range(11)
 QS_DT_F64, QS_DT_F32 = 0, 1
@@ -26,6 +27,7 @@ PRECISIONS = {"fp64": QS_PREC_FP64, "fp32": QS_PREC_FP32, "bf16": QS_PREC_BF16,
               "bf16x3": QS_PREC_BF16X3}
 EMBEDDINGS = {"gaussian": QS_EMB_GAUSSIAN, "rademacher": QS_EMB_RADEMACHER}
 RANGEFINDERS = {"pseudo_qr": QS_RF_PSEUDO_QR, "pseudo_svd": QS_RF_PSEUDO_SVD}
+RF_PRECISIONS = {"df64": QS_RF_PREC_DF64, "fp64": QS_RF_PREC_FP64, "mixed": QS_RF_PREC_MIXED}
 
 ABI_SYMBOLS = ("qsketch_workspace_bytes", "qsketch_create", "qsketch_update", "qrangefinder",
                "qonepass_core", "qreconstruct_error", "qsketch_get", "qs_last_device_error",
@@ -37,7 +39,8 @@ ABI_SYMBOLS = ("qsketch_workspace_bytes", "qsketch_create", "qsketch_update", "q
 class QSConfig(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("s", ctypes.c_int64),
                 ("l", ctypes.c_int64), ("emb", ctypes.c_int32), ("prec", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("pure", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("pure", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("rf_prec", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class QSError(RuntimeError):
@@ -186,10 +189,10 @@ class QSketch:
     """One sketch state (Omega, Psi, Y, W and the results) in a caller-owned workspace."""
 
     def __init__(self, m, n, s, l, emb="gaussian", prec="fp64", seed=0, pure=False,
-                 device="cuda", stream=None, flags=0):
+                 device="cuda", stream=None, flags=0, rf_prec="df64"):
         self.lib = load_library()
         self.cfg = QSConfig(m, n, s, l, EMBEDDINGS.get(emb, emb), PRECISIONS.get(prec, prec),
-                            seed, int(bool(pure)), int(flags))
+                            seed, int(bool(pure)), int(flags), RF_PRECISIONS.get(rf_prec, rf_prec), 0)
         self.f64 = self.cfg.prec == QS_PREC_FP64
         nbytes = self.lib.qsketch_workspace_bytes(ctypes.byref(self.cfg))
         if nbytes == 0:
