@@ -244,7 +244,7 @@ QS_API qs_status qreconstruct_error(qs_handle_t h, const void* const A_planes[4]
                              double* rel_err_dev, void* stream);
 
 /* Allocation-free relative error (a service entry point; the paper has no counterpart).
- * Computes ||A - H X||_F / ||A||_F, the error measure of Sec. 5, for factors the caller
+ * Computes ||A - H X||_F / ||A||_F for factors the caller
  * holds itself, with no handle and no workspace: for callers that did not build the
  * factors through a handle (stored factors, another library) and cannot allocate one,
  * since a device allocation synchronises the device and fails once the process's memory
@@ -253,19 +253,22 @@ QS_API qs_status qreconstruct_error(qs_handle_t h, const void* const A_planes[4]
  *   dtype     : QS_DT_F64 (all planes FP64, FP64 accumulation) or QS_DT_F32 (all planes
  *               FP32, FP32 accumulation of H X, FP64 sums of squares).
  *   *_planes  : four device planes each, row-major with leading dimensions lda >= n,
- *               ldh >= s, ldx >= n.  A_planes[0] may be NULL (pure quaternion A); H and X
- *               planes may not.  Read only.
+ *               ldh >= s, ldx >= n.  A_planes[0] may be NULL (pure quaternion A); no other
+ *               plane of A, H or X may be.  Read only.
  *   rel_err_dev: device pointer to one double, written on `stream`.
  * Scratch: a library-owned static device array of 2 doubles per 64 x 64 tile of A, at
  * most QS_STATIC_ERR_MAX_TILES tiles (1 MiB); nothing in it has to start at zero, every
  * slot read is written earlier by the same call.  The sums are reduced in a fixed order,
  * so the result is deterministic.
  * Returns QS_ERR_INVALID for bad sizes, dtypes or pointers, QS_ERR_UNSUPPORTED when
- * ceil(m/64) * ceil(n/64) > QS_STATIC_ERR_MAX_TILES (both before any CUDA call), and
- * QS_ERR_CUDA when the scratch lookup or a launch fails.
- * The first call on a device looks up the scratch address on the current device (once per
- * device, cached); a caller that captures streams into graphs makes that first call before
- * any capture.  The scratch is shared by every call on a device: two calls whose work may
+ * ceil(m/64) * ceil(n/64) > QS_STATIC_ERR_MAX_TILES or ceil(n/64) > 65535 (both before any
+ * CUDA call), and QS_ERR_CUDA when the scratch lookup or a launch fails.
+ * The first call on a device looks up the scratch address on the current device, and caches
+ * it with the context that was current (a call under another context looks it up again); a
+ * caller that captures streams into graphs makes that first call before any capture.  A
+ * context destroyed by cudaDeviceReset whose successor the driver gives the same handle is
+ * not told apart: after a reset, make the first call of the new context before any capture
+ * as well, and do not reset while calls may be in flight.  The scratch is shared by every call on a device: two calls whose work may
  * overlap in time (different streams without ordering, or several host threads) race on
  * it; order them (one stream, or events). */
 #define QS_STATIC_ERR_MAX_TILES 65536

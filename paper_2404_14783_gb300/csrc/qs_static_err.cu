@@ -1,5 +1,5 @@
-// Allocation-free relative error ||A - H X||_F / ||A||_F (the error measure of Sec. 5) for
-// factors H, X that the caller holds in its own buffers, without a qsketch handle.
+// Allocation-free relative error ||A - H X||_F / ||A||_F for factors H, X that the caller
+// holds in its own buffers, without a qsketch handle.
 //
 // Who needs it: a caller that checks an approximation it did not build through a handle
 // (factors loaded from storage or produced by another library) and has no workspace to
@@ -13,6 +13,9 @@
 // adding them atomically; a second launch adds the slots in a fixed order.  So the result
 // is deterministic, and no slot has to start at zero: every slot the reduction reads is
 // written earlier by the same call.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "qs_common.cuh"
@@ -26,18 +29,42 @@ __device__ __align__(256) double g_err_scratch[2 * QS_STATIC_ERR_MAX_TILES];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
+// per device: the context the address was looked up in, and the address
+CUcontext g_scratch_ctx[kMaxDevices] = {};
 double* g_scratch_addr[kMaxDevices] = {};
 
-// Address of g_err_scratch on the current device; looked up once per device.
+// The CUDA context current on this thread (driver entry point through the runtime, so the
+// library needs no link to the driver library); nullptr when it cannot be queried.
+CUcontext current_context() {
+  static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &ptr, 4000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(ptr);
+  });
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
+
+// Address of g_err_scratch on the current device, looked up once per device and context
+// (a context other than the one of the cached lookup -- e.g. a non-primary driver context --
+// triggers a fresh lookup).
 qs_status scratch_for_current_device(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return QS_ERR_CUDA;
   if (dev >= kMaxDevices) return QS_ERR_UNSUPPORTED;
+  const CUcontext ctx = current_context();
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  if (!g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_err_scratch) != cudaSuccess || !p) return QS_ERR_CUDA;
     g_scratch_addr[dev] = static_cast<double*>(p);
+    // the lookup makes the device's primary context current when no context was
+    g_scratch_ctx[dev] = current_context();
   }
   *out = g_scratch_addr[dev];
   return QS_OK;
@@ -53,14 +80,13 @@ extern "C" QS_API qs_status qs_reconstruct_error_static(
   if (dtype != QS_DT_F64 && dtype != QS_DT_F32) return QS_ERR_INVALID;
   if (!A_planes || !H_planes || !X_planes || !rel_err_dev) return QS_ERR_INVALID;
   if (lda < n || ldh < s || ldx < n) return QS_ERR_INVALID;
-  bool any_a = false;
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < 4; ++p)
     if (!H_planes[p] || !X_planes[p]) return QS_ERR_INVALID;
-    any_a = any_a || A_planes[p] != nullptr;
-  }
-  if (!any_a) return QS_ERR_INVALID;
-  const int64_t tiles = ((m + 63) / 64) * ((n + 63) / 64);
-  if (tiles > QS_STATIC_ERR_MAX_TILES) return QS_ERR_UNSUPPORTED;
+  for (int p = 1; p < 4; ++p)           // only plane w of A may be NULL (pure quaternion)
+    if (!A_planes[p]) return QS_ERR_INVALID;
+  const int64_t tiles_m = (m + 63) / 64, tiles_n = (n + 63) / 64;
+  // one CTA per 64 x 64 tile: column tiles go on grid.y (at most 65535)
+  if (tiles_m * tiles_n > QS_STATIC_ERR_MAX_TILES || tiles_n > 65535) return QS_ERR_UNSUPPORTED;
 
   double* scratch = nullptr;
   const qs_status ss = scratch_for_current_device(&scratch);

@@ -99,16 +99,43 @@ def reconstruct_error_static(A, H, X, out, stream=None):
     """||A - H X||_F / ||A||_F through qs_reconstruct_error_static (no handle, no workspace).
 
     A (m x n), H (m x s), X (s x n): (4, rows, cols) CUDA tensors or lists of four planes
-    (A's first plane may be None), all float64 or all float32, row-major planes.  `out` is a
-    1-element CUDA float64 tensor the result is written to on `stream`; the caller provides
-    it so that the call itself allocates nothing."""
+    (A's first plane may be None), all float64 or all float32, row-major planes, the planes
+    of one operand with one row stride.  `out` is a 1-element CUDA float64 tensor the result
+    is written to on `stream`; the caller provides it so that the call itself allocates
+    nothing.  Shapes, dtypes, devices and strides are checked here, before the C call, so
+    that no launch reads past a caller's buffer (ValueError otherwise)."""
     lib = load_library()
-    f64 = out.dtype == torch.float64 and _dtype_of(H) == torch.float64
+    f64 = _dtype_of(H) == torch.float64
+    m, s = _shape_of(H)
+    s2, n = _shape_of(X)
+    if s2 != s:
+        raise ValueError(f"X has {s2} rows, H has {s} columns")
+    for name, M_, shape, may_skip_w in (("A", A, (m, n), True), ("H", H, (m, s), False),
+                                        ("X", X, (s, n), False)):
+        mats = [M_[p] for p in range(4)] if isinstance(M_, torch.Tensor) else list(M_)
+        if len(mats) != 4:
+            raise ValueError(f"{name} must have four planes")
+        strides = set()
+        for p, t in enumerate(mats):
+            if t is None:
+                if p == 0 and may_skip_w:
+                    continue
+                raise ValueError(f"plane {p} of {name} is missing")
+            if tuple(t.shape) != shape:
+                raise ValueError(f"plane {p} of {name} is {tuple(t.shape)}, expected {shape}")
+            strides.add(t.stride(0) if t.shape[0] > 1 else t.shape[1])
+        if len(strides) != 1:
+            raise ValueError(f"the planes of {name} have different row strides {sorted(strides)}")
+    if (not isinstance(out, torch.Tensor) or not out.is_cuda or out.dtype != torch.float64
+            or out.numel() < 1):
+        raise ValueError("out must be a CUDA float64 tensor with at least one element")
+    for M_ in (A, H, X):
+        for t in ([M_[p] for p in range(4)] if isinstance(M_, torch.Tensor) else list(M_)):
+            if t is not None and t.device != out.device:
+                raise ValueError(f"every plane must be on {out.device}")
     a_ptrs, lda = _planes(A, f64)
     h_ptrs, ldh = _planes(H, f64)
     x_ptrs, ldx = _planes(X, f64)
-    m, s = _shape_of(H)
-    n = _shape_of(X)[1]
     _check(lib.qs_reconstruct_error_static(m, n, s, QS_DT_F64 if f64 else QS_DT_F32, a_ptrs, lda,
                                            h_ptrs, ldh, x_ptrs, ldx,
                                            ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),

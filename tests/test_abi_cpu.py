@@ -56,7 +56,8 @@ def test_workspace_bytes_and_validation(lib):
     # FP32 modes store half-size objects
     assert lib.qsketch_workspace_bytes(ctypes.byref(_cfg(prec=1))) < good
     for bad in (dict(s=0), dict(l=4), dict(l=81), dict(m=0), dict(emb=2), dict(prec=9),
-                dict(flags=1), dict(pure=3), dict(s=2000, l=2000, m=5000, n=5000)):
+                dict(flags=1), dict(pure=3), dict(s=2000, l=2000, m=5000, n=5000),
+                dict(rf_prec=3), dict(rf_prec=-1), dict(reserved=1)):
         assert lib.qsketch_workspace_bytes(ctypes.byref(_cfg(**bad))) == 0, bad
 
 
@@ -101,3 +102,36 @@ def test_test_flag_only_in_tensor_core_modes(lib):
     assert lib.qsketch_workspace_bytes(ctypes.byref(_cfg(flags=1, prec=3))) > 0
     assert lib.qsketch_workspace_bytes(ctypes.byref(_cfg(flags=1, prec=1))) == 0
     assert lib.qsketch_workspace_bytes(ctypes.byref(_cfg(flags=2, prec=3))) == 0
+
+
+def test_rf_precision_sets_the_storage_of_h_and_x(lib):
+    """FP32-storage modes keep H and X in FP64 unless the stages after the sketch run mixed."""
+    fp32_df = lib.qsketch_workspace_bytes(ctypes.byref(_cfg(prec=1, rf_prec=0)))
+    fp32_64 = lib.qsketch_workspace_bytes(ctypes.byref(_cfg(prec=1, rf_prec=1)))
+    fp32_mx = lib.qsketch_workspace_bytes(ctypes.byref(_cfg(prec=1, rf_prec=2)))
+    assert fp32_df == fp32_64 > fp32_mx > 0
+
+
+def test_static_error_binding_checks_shapes_before_any_launch(lib):
+    """reconstruct_error_static refuses operands of the wrong shape, mixed row strides or a
+    bad output before it reaches the C ABI (nothing launched)."""
+    import torch
+    import paper_2404_14783_gb300 as pkg
+    m, n, s = 40, 30, 5
+    A = torch.zeros(4, m, n, dtype=torch.float64)
+    H = torch.zeros(4, m, s, dtype=torch.float64)
+    X = torch.zeros(4, s, n, dtype=torch.float64)
+    out = torch.zeros(1, dtype=torch.float64)
+    before = pkg.launch_count()
+    bad_cases = [
+        (torch.zeros(4, m, n - 1, dtype=torch.float64), H, X, out),     # A too narrow
+        (torch.zeros(4, m - 1, n, dtype=torch.float64), H, X, out),     # A too short
+        (A, H, torch.zeros(4, s - 1, n, dtype=torch.float64), out),     # X too short for H
+        (A, [H[0], H[1], H[2], None], X, out),                           # H plane missing
+        ([A[0], A[1], A[2], torch.zeros(m, n + 3, dtype=torch.float64)[:, :n]], H, X, out),
+        (A, H, X, out),                                                  # out on the host
+    ]
+    for a, h, x, o in bad_cases:
+        with pytest.raises(ValueError):
+            pkg.reconstruct_error_static(a, h, x, o)
+    assert pkg.launch_count() == before

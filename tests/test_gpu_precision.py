@@ -14,12 +14,16 @@ are an unevaluated sum of two FP32 numbers):
     to ~u kappa(Y), and the corrections are smooth in H, so H carries that error; eps_k is
     a Rayleigh quotient of G_k^{-1}, sensitive as u kappa(G_k) = u kappa(H_k)^2.
   * kappa(Y) = 1e3: the same quantities at the bars that this conditioning allows: H at
-    30 u kappa(Y), eps_1 at 30 u kappa(Y)^2 (eps_2, eps_3 see the corrected H, kappa < 10).
+    30 u kappa(Y), the eps_k at 30 u kappa(Y)^2 (eps_1 has that sensitivity, and the later
+    corrections inherit its error through H_1).
   * QB stage: P = Psi H against the oracle's product, 1e-12; X = P^dagger W against the
     oracle's least-squares solution with the same H, W, Psi, 1e-12 (kappa(P) ~ 6 here).
   * The stop path of the corrections (kappa estimate above 1e8, the range of use the paper
     gives for pseudo-QR): QS_ERR_RANK, all eps_k = 0, H = the uncorrected H_0, whose range
-    is Y's to 100 u kappa(Y) (H_0 = Y D with kappa(D) = kappa(Y)).
+    is Y's to 100 u kappa(Y) (H_0 = Y D with kappa(D) = kappa(Y)).  FP64 storage: kappa(Y)
+    = 1e10.  FP32 storage cannot hold such a Y (rounding Y to FP32 alone lifts its smallest
+    singular values to ~1e-7 of the largest), so there Y has two equal columns (exactly
+    rank deficient).
 """
 import numpy as np
 import pytest
@@ -99,7 +103,7 @@ def test_pseudo_qr_with_corrections_elementwise(pkg, prec, rf, kappa):
     else:
         u = _unit(prec, rf)
         bar_h = max(1e-12, 30 * u * kappa)
-        bar_e = [max(1e-12, 30 * u * kappa ** 2), 1e-12 * 30, 1e-12 * 30]
+        bar_e = [max(1e-12, 30 * u * kappa ** 2)] * 3
     assert relmax(H, Href) <= bar_h, (relmax(H, Href), bar_h)
     for k in range(3):
         assert abs(eps[k] - info["eps"][k]) <= bar_e[k] * info["eps"][k], (k, eps[k], info["eps"][k])
@@ -134,12 +138,15 @@ def test_qb_stage_on_the_gpus_own_h(pkg, prec, rf):
 
 @pytest.mark.parametrize("prec,rf", [("fp64", "df64"), ("bf16x3", "df64")])
 def test_corrections_stop_beyond_their_range(pkg, prec, rf):
-    """kappa(Y) = 1e10: the kappa estimate of H_0 exceeds 1e8, so the corrections are skipped
-    (QS_ERR_RANK as a warning, all eps_k = 0) and H is the uncorrected H_0, which still
-    spans R(Y)."""
+    """The kappa estimate of H_0 exceeds 1e8, so the corrections are skipped (QS_ERR_RANK as
+    a warning, all eps_k = 0) and H is the uncorrected H_0, which still spans R(Y)."""
+    f64 = prec == "fp64"
     kappa = 1e10
+    Y = _make_y(kappa, 21)
+    if not f64:
+        Y[:, :, S - 1] = Y[:, :, 0]
     qs = pkg.QSketch(M, N, S, L, emb="gaussian", prec=prec, rf_prec=rf, seed=3)
-    Y = _put(qs, "Y", _make_y(kappa, 21), prec == "fp64")
+    Y = _put(qs, "Y", Y, f64)
     qs.rangefinder("pseudo_qr", 3)
     torch.cuda.synchronize()
     assert qs.device_status() == QS_ERR_RANK
@@ -150,7 +157,9 @@ def test_corrections_stop_beyond_their_range(pkg, prec, rf):
     Qh, _ = np.linalg.qr(CH)
     u = _unit(prec, rf)
     resid = np.linalg.norm(CY - Qh @ (Qh.conj().T @ CY)) / np.linalg.norm(CY)
-    assert resid <= 100 * u * kappa, resid
+    assert resid <= (100 * u * kappa if f64 else 1e-6), resid
+    if not f64:
+        return
     # the oracle's Alg. 1 without corrections spans the same space
     H0 = O.pseudo_qr(Y, 0)
     Q0, _ = np.linalg.qr(O.chi(H0))

@@ -64,7 +64,9 @@ def test_truncation_matches_oracle(pkg, case):
     assert rel(O.qmatmul(Hr, Xr), ref_prod) < tol_p
     # the truncated approximation's error, through the allocation-free error entry point
     out = torch.empty(1, dtype=torch.float64, device="cuda")
-    err_r = float(pkg.reconstruct_error_static(Ad, qs.get("Hr"), qs.get("Xr"), out).item())
+    # the entry point takes all planes in A's type: the factors rounded to it
+    Hr_t, Xr_t = qs.get("Hr").to(Ad.dtype), qs.get("Xr").to(Ad.dtype)
+    err_r = float(pkg.reconstruct_error_static(Ad, Hr_t, Xr_t, out).item())
     A64 = Ad.double().cpu().numpy()
     ref_err = O.qnorm(A64 - ref_prod) / O.qnorm(A64)
     assert abs(err_r - ref_err) <= 1e-4 * ref_err + 1e-12, (err_r, ref_err)

@@ -6,9 +6,14 @@ epilogue; only the order in which the tile sums are added differs (atomics versu
 fixed-order reduction), so the two agree to FP64 summation rounding: 1e-12 relative.  In the
 split-BF16 mode the handle's pass runs on the tensor cores (H X from BF16 hi/lo pairs), which
 moves the error by at most 2^-15 ||M||_F / ||A||_F, M = |H| |X| over the Hamilton terms.
-The static path is deterministic, so two calls in a row return the same bits; the second
-call also shows that no state left in the static scratch by the first one leaks into the
-result.
+The handles run with rf_prec = mixed in the FP32-storage modes, which keeps H and X in FP32,
+so that both entry points see the same factor values.  Both are also compared with the
+oracle's error of those factors (FP64): 1e-12 relative in FP64; in FP32 the product H X is
+accumulated in FP32, which moves the error by at most 2 s 2^-24 ||M||_F / ||A||_F.
+
+The static path is deterministic, so two calls in a row return the same bits.  A large call
+followed by a smaller one shows that what the first leaves in the static scratch does not
+leak into the second, and the device's free memory is the same before and after a call.
 """
 import ctypes
 
@@ -18,6 +23,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+import oracle as O
 import workloads as WL
 
 
@@ -36,7 +42,8 @@ def _pipeline(pkg, m, n, s, l, prec, pure=False, seed=5):
     A = WL.make_decay(m, n, seed=seed, rank_cap=min(m, n), dtype=np.float32)
     if pure:
         A[0] = 0.0
-    qs = pkg.QSketch(m, n, s, l, prec=prec, seed=seed, pure=pure)
+    qs = pkg.QSketch(m, n, s, l, prec=prec, seed=seed, pure=pure,
+                     rf_prec="df64" if prec == "fp64" else "mixed")
     dt = torch.float64 if prec == "fp64" else torch.float32
     Ad = torch.as_tensor(A, dtype=dt, device="cuda")
     planes = [None, Ad[1], Ad[2], Ad[3]] if pure else Ad
@@ -50,13 +57,23 @@ def _pipeline(pkg, m, n, s, l, prec, pure=False, seed=5):
 _PLANE = [[0, 1, 2, 3], [1, 0, 3, 2], [2, 3, 0, 1], [3, 2, 1, 0]]
 
 
-def _split_bf16_bound(planes, H, X):
+def _np_planes(planes, H, X):
     Hn = H.double().cpu().numpy()
     Xn = X.double().cpu().numpy()
     An = np.stack([np.zeros(Hn.shape[1:2] + Xn.shape[2:]) if p is None else p.double().cpu().numpy()
                    for p in planes])
+    return An, Hn, Xn
+
+
+def _abs_product_bound(planes, H, X, unit):
+    """unit * ||M||_F / ||A||_F, M = |H| |X| summed over the Hamilton terms."""
+    An, Hn, Xn = _np_planes(planes, H, X)
     M = np.stack([sum(np.abs(Hn[_PLANE[q][b]]) @ np.abs(Xn[b]) for b in range(4)) for q in range(4)])
-    return 2.0 ** -15 * np.linalg.norm(M) / np.linalg.norm(An)
+    return unit * np.linalg.norm(M) / np.linalg.norm(An)
+
+
+def _split_bf16_bound(planes, H, X):
+    return _abs_product_bound(planes, H, X, 2.0 ** -15)
 
 
 def _static_twice(pkg, planes, H, X):
@@ -78,6 +95,30 @@ def test_static_error_matches_handle_error(pkg, m, n, s, l, prec):
         tol += _split_bf16_bound(planes, qs.get("H"), qs.get("X"))
     assert abs(r1 - ref) <= tol, (r1, ref, tol)
     assert r2 == r1
+    # against the oracle's error of the same factors
+    An, Hn, Xn = _np_planes(planes, qs.get("H"), qs.get("X"))
+    exact = O.rel_error(An, Hn, Xn)
+    tol_o = 1e-12 * exact if prec == "fp64" else _abs_product_bound(planes, qs.get("H"), qs.get("X"),
+                                                                    2 * s * 2.0 ** -24)
+    assert abs(r1 - exact) <= tol_o, (r1, exact, tol_o)
+
+
+def test_static_error_large_then_small_call_and_no_allocation(pkg):
+    """A 1000 x 700 call, then a 64 x 64 one: the second equals its own handle's error (the
+    first call's scratch contents do not leak); the device's free memory does not move."""
+    big, bplanes, _ = _pipeline(pkg, 1000, 700, 37, 75, "fp64", seed=8)
+    small, splanes, sref = _pipeline(pkg, 64, 64, 5, 11, "fp64", seed=9)
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    pkg.reconstruct_error_static(bplanes, big.get("H"), big.get("X"), out)   # warm-up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    reserved0 = torch.cuda.memory_reserved()
+    pkg.reconstruct_error_static(bplanes, big.get("H"), big.get("X"), out)
+    r = float(pkg.reconstruct_error_static(splanes, small.get("H"), small.get("X"), out).item())
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_reserved() == reserved0
+    assert abs(r - sref) <= 1e-12 * sref, (r, sref)
 
 
 def test_static_error_pure_quaternion_and_strided_factors(pkg):
