@@ -34,4 +34,13 @@ cudaError_t launch_qchol_inv(const double* G, int64_t ldg, int64_t psg, double* 
                              int power_slot, double kappa_stop, int use_df64, int32_t* status,
                              double* scalars, int fail_bits, double* Lg, cudaStream_t st,
                              const double* fp32_gate = nullptr, double fp32_below = 0.0);
+// The same factorisation, inverse and power iterates on one cluster of 8 CTAs (one launch;
+// df64 or double arithmetic); n <= qchol_cluster_max_n(complex_only).  Gate semantics as above
+// (gate_mode 0: always run).
+int qchol_cluster_max_n(int complex_only);
+cudaError_t launch_qchol_cluster(const double* G, int64_t ldg, int64_t psg, double* Li, int64_t ldl,
+                                 int64_t psl, int n, int complex_only, int allow_shift,
+                                 double shift_rows, int power_slot, double kappa_stop, int use_df64,
+                                 int32_t* status, double* scalars, int fail_bits, double* Lg,
+                                 cudaStream_t st, const double* gate, double thr, int gate_mode);
 }  // namespace qs

@@ -14,8 +14,9 @@ are an unevaluated sum of two FP32 numbers):
     to ~u kappa(Y), and the corrections are smooth in H, so H carries that error; eps_k is
     a Rayleigh quotient of G_k^{-1}, sensitive as u kappa(G_k) = u kappa(H_k)^2.
   * kappa(Y) = 1e3: the same quantities at the bars that this conditioning allows: H at
-    30 u kappa(Y), the eps_k at 30 u kappa(Y)^2 (eps_1 has that sensitivity, and the later
-    corrections inherit its error through H_1).
+    100 u kappa(Y), the eps_k at 100 u kappa(Y)^2 (eps_1 has that sensitivity, and the later
+    corrections inherit its error through H_1); the factor 100 stands for the dimension-
+    dependent constants (s = 24) of the forward-error bounds of the QR and the solves.
   * QB stage: P = Psi H against the oracle's product, 1e-12; X = P^dagger W against the
     oracle's least-squares solution with the same H, W, Psi, 1e-12 (kappa(P) ~ 6 here).
   * The stop path of the corrections (kappa estimate above 1e8, the range of use the paper
@@ -102,8 +103,8 @@ def test_pseudo_qr_with_corrections_elementwise(pkg, prec, rf, kappa):
         bar_h, bar_e = 1e-12, [1e-12] * 3
     else:
         u = _unit(prec, rf)
-        bar_h = max(1e-12, 30 * u * kappa)
-        bar_e = [max(1e-12, 30 * u * kappa ** 2)] * 3
+        bar_h = max(1e-12, 100 * u * kappa)
+        bar_e = [max(1e-12, 100 * u * kappa ** 2)] * 3
     assert relmax(H, Href) <= bar_h, (relmax(H, Href), bar_h)
     for k in range(3):
         assert abs(eps[k] - info["eps"][k]) <= bar_e[k] * info["eps"][k], (k, eps[k], info["eps"][k])
