@@ -142,16 +142,31 @@ def algorithmic(cfg):
 
 
 def make_A(w, device, prec):
+    """The workload's matrix on the device: a (4, m, n) tensor, or for a pure quaternion
+    workload the list [None, A_x, A_y, A_z] of its three stored planes."""
     import numpy as np
     import torch
     import workloads as WL
     dt = np.float64 if prec == "fp64" else np.float32
     if w["name"] == "c1":
-        A = torch.as_tensor(WL.make_c1(seed=w["seed"]).astype(dt), device=device)
-    else:
-        A = WL.make_decay(w["m"], w["n"], seed=w["seed"], rank_cap=w.get("rank_cap", 1024),
-                          device=device, dtype=dt)
-    return A.contiguous()
+        return torch.as_tensor(WL.make_c1(seed=w["seed"]).astype(dt), device=device).contiguous()
+    if w["name"] == "c3":
+        P = WL.make_c3(device)
+        return [None, P[0], P[1], P[2]]
+    if w["name"] == "c5":
+        P = WL.make_c5(device)
+        return [None, P[0], P[1], P[2]]
+    return WL.make_decay(w["m"], w["n"], seed=w["seed"], rank_cap=w.get("rank_cap", 1024),
+                         device=device, dtype=dt).contiguous()
+
+
+def planes_of(A):
+    """The stored planes of a (4, m, n) tensor or a plane list (None for a zero plane)."""
+    return [A[p] for p in range(4)] if not isinstance(A, list) else A
+
+
+def a_nbytes(A):
+    return sum(p.numel() * p.element_size() for p in planes_of(A) if p is not None)
 
 
 def run_ours(args, rank, world, local_rank):
@@ -161,13 +176,14 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     w = workload(args.workload)
+    pure = bool(w.get("pure", False))
     cfg = dict(m=w["m"], n=w["n"], s=w["s"], l=w["l"], prec=args.prec, emb=w["emb"],
-               pure=False)
+               pure=pure)
     A = make_A(w, dev, args.prec)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     qs = pkg.QSketch(cfg["m"], cfg["n"], cfg["s"], cfg["l"], emb=cfg["emb"], prec=args.prec,
-                     seed=w["seed"] + rank, rf_prec=args.rf_prec)
+                     seed=w["seed"] + rank, rf_prec=args.rf_prec, pure=pure)
     err_out = torch.zeros(1, dtype=torch.float64, device=dev)
     E = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
 
@@ -233,9 +249,13 @@ def run_ours(args, rank, world, local_rank):
     # error pass that last read it, so one step's copies overlap the previous step's
     # rangefinder, core and error pass.  One staging buffer (copies wait for the previous
     # step) and the plain copy-then-step loop are timed beside it.
-    A_host = A.cpu().pin_memory()
+    A_host = [None if p is None else p.cpu().pin_memory() for p in planes_of(A)]
     n = cfg["n"]
-    staging = [torch.empty(qs.staging_shape(), dtype=A.dtype, device=dev) for _ in range(2)]
+    a_dtype = next(p for p in A_host if p is not None).dtype
+    staging = [torch.empty(qs.staging_shape(), dtype=a_dtype, device=dev) for _ in range(2)]
+
+    def stg_planes(stg):
+        return [None if A_host[p] is None else stg[p, :, :n] for p in range(4)]
     freed = [torch.cuda.Event(), torch.cuda.Event()]
     err_host = torch.zeros(1, dtype=torch.float64).pin_memory()
 
@@ -245,14 +265,16 @@ def run_ours(args, rank, world, local_rank):
             stg = staging[j]
             qs.reset(seed=w["seed"] + rank)
             if mode == "copy":
-                stg[:, :, :n].copy_(A_host, non_blocking=True)
-                qs.update(stg[:, :, :n], theta=0.0)
+                for p in range(4):
+                    if A_host[p] is not None:
+                        stg[p, :, :n].copy_(A_host[p], non_blocking=True)
+                qs.update(stg_planes(stg), theta=0.0)
             else:
                 qs.update_host(A_host, stg, block_rows=args.stream_rows, theta=0.0,
                                staging_free=freed[j] if mode == "pipelined" and used[j] else None)
             qs.rangefinder(args.rangefinder, 3)
             qs.core()
-            qs.error(stg[:, :, :n], out=err_out)
+            qs.error(stg_planes(stg), out=err_out)
             freed[j].record(stream)
             used[j] = True
             err_host.copy_(err_out, non_blocking=True)
@@ -281,7 +303,7 @@ def run_ours(args, rank, world, local_rank):
     result = dict(ms=ms, gbs=gbs, stage_ms=stage_ms, clocks=clocks, launches=launches,
                   final_err=final_err, status=status, e2e_ms=e2e_ms, flops=flops, abytes=abytes,
                   cfg=cfg, w=w, e2e_gbs=world * abytes / (e2e_ms * 1e-3) / 1e9,
-                  h2d=A.numel() * A.element_size(), d2h=8, truncate_ms=truncate_ms, trunc_rank=k,
+                  h2d=a_nbytes(A), d2h=8, truncate_ms=truncate_ms, trunc_rank=k,
                   e2e_modes=e2e, e2e_err=e2e_err, e2e_status=e2e_status)
     # the stages after the sketch in the other arithmetics, on this step's Y and W (rank 0,
     # informational): native FP64, and the mixed mode with its device-chosen FP32 steps
@@ -291,7 +313,7 @@ def run_ours(args, rank, world, local_rank):
             if rf == args.rf_prec:
                 continue
             qv = pkg.QSketch(cfg["m"], cfg["n"], cfg["s"], cfg["l"], emb=cfg["emb"], prec=args.prec,
-                             seed=w["seed"], rf_prec=rf)
+                             seed=w["seed"], rf_prec=rf, pure=pure)
             qv.get("Y").copy_(qs.get("Y"))
             qv.get("W").copy_(qs.get("W"))
             for _ in range(2):
@@ -317,10 +339,10 @@ def run_ours(args, rank, world, local_rank):
     # timed over 20 repetitions after warm-up, the whole path once for its final error
     if rank == 0 and args.prec != "fp32" and not args.no_compare:
         qs32 = pkg.QSketch(cfg["m"], cfg["n"], cfg["s"], cfg["l"], emb=cfg["emb"], prec="fp32",
-                           seed=w["seed"], rf_prec=args.rf_prec)
+                           seed=w["seed"], rf_prec=args.rf_prec, pure=pure)
         for _ in range(args.warmup):
             qs32.update(A, theta=0.0)
-        reps32 = 20
+        reps32 = 20 if cfg["m"] * cfg["n"] <= 8192 * 8192 else 5
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
         s0.record(stream)
@@ -469,29 +491,60 @@ def batch_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def cpu_baseline(w, rows, reps=1):
-    """The FP64 oracle on the host cores on a bounded sample: the first ``rows`` rows of the
-    workload's matrix with the same s and l.  Returns (A GB/s, seconds, threads)."""
+def cpu_sample(w, rows):
+    """A bounded sample of the workload for the oracle on the host cores, as FP64 numpy
+    (4, rows', n') planes, and its description: c1/c2 the first rows of the matrix; c3 the
+    first rows and columns of the same image (same generator); c5 a 32^3 grid with the same
+    time steps.  The oracle's rate on the sample is reported as A GB/s of the sample."""
     import numpy as np
-    import oracle as O
     import workloads as WL
     if w["name"] == "c1":
         A = WL.make_c1(seed=w["seed"])[:, :rows]
-    else:
-        A = WL.make_decay(w["m"], w["n"], seed=w["seed"], rank_cap=w.get("rank_cap", 1024),
-                          dtype=np.float64)[:, :rows]
+        return A, f"first {A.shape[1]} rows x {A.shape[2]} cols of c1"
+    if w["name"] == "c3":
+        cols = 8192      # the oracle's least-squares solve costs ~2.5 ms per column of A
+        P = WL.make_c3("cpu", m=w["m"], n=w["n"], rows=rows)[:, :, :cols].double().numpy()
+        A = np.concatenate([np.zeros((1,) + P.shape[1:]), P])
+        return A, f"first {rows} rows x first {cols} cols of the c3 image (pure)"
+    if w["name"] == "c5":
+        P = WL.make_c5("cpu", grid=32).double().numpy()
+        A = np.concatenate([np.zeros((1,) + P.shape[1:]), P])
+        return A, f"32^3-grid c5 snapshots ({A.shape[1]} rows x {A.shape[2]} cols, pure)"
+    A = WL.make_decay(w["m"], w["n"], seed=w["seed"], rank_cap=w.get("rank_cap", 1024),
+                      dtype=np.float64)[:, :rows]
+    return A, f"first {A.shape[1]} rows x {A.shape[2]} cols of {w['name']}"
+
+
+def cpu_baseline(w, rows, reps=1, sample=None):
+    """The FP64 oracle's whole one-pass path on the host cores on a bounded sample of the
+    workload (cpu_sample).  Returns (A GB/s, seconds, threads, description); the bytes are
+    those of the sample as the GPU workload stores it (FP32, 3 planes when pure)."""
+    import oracle as O
+    A, desc = sample if sample is not None else cpu_sample(w, rows)
     m, n = A.shape[1], A.shape[2]
-    Om = O.draw_embedding(n, w["s"], O.EMB_GAUSSIAN, O.STREAM_OMEGA, w["seed"])
-    Psi = O.draw_embedding(w["l"], m, O.EMB_GAUSSIAN, O.STREAM_PSI, w["seed"])
+    kind = O.EMB_GAUSSIAN if w["emb"] == "gaussian" else O.EMB_RADEMACHER
+    l = min(w["l"], m, n)
+    Om = O.draw_embedding(n, w["s"], kind, O.STREAM_OMEGA, w["seed"])
+    Psi = O.draw_embedding(l, m, kind, O.STREAM_PSI, w["seed"])
     times = []
     for _ in range(reps):
         t = time.perf_counter()
         O.onepass(A, Om, Psi, "pseudo_qr", 3)
         times.append(time.perf_counter() - t)
     sec = min(times)
-    abytes = 4 * m * n * 4      # A bytes as stored in the FP32 workload
+    abytes = (3 if w.get("pure") else 4) * m * n * 4      # A bytes as stored in the FP32 workload
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return abytes / sec / 1e9, sec, threads, f"first {m} rows x {n} cols of {w['name']}"
+    return abytes / sec / 1e9, sec, threads, desc
+
+
+WORKLOAD_TEXT = {
+    "c1": "quaternion A 512x384 FP64 planes, U diag(0.5^i) V* + 1e-6 noise, k=10, s=21, l=43, Gaussian Omega/Psi",
+    "c2": "quaternion A 8192x8192 FP32 planes, sigma_i=i^-2, k=50, s=101, l=203, Gaussian Omega/Psi",
+    "c3": "pure-quaternion image-like A 31365x27125 FP32 (3 channels of 64 random Fourier modes in [0,0.98] "
+          "+ U(0,0.02)), k=100, s=201, l=403, Rademacher Omega/Psi (exact in BF16)",
+    "c5": "pure-quaternion flow snapshots A 2097152x256 FP32 (128^3 grid x 256 steps, 32 divergence-free "
+          "Taylor-Green-type modes + 1e-4 noise), k=20, s=41, l=83, Gaussian Omega/Psi",
+}
 
 
 def main():
@@ -506,13 +559,16 @@ def main():
     ap.add_argument("--rangefinder", default="pseudo_qr")
     ap.add_argument("--rf-prec", default="df64", choices=["df64", "fp64", "mixed"],
                     help="arithmetic of the rangefinder, core and truncation stages")
-    ap.add_argument("--cpu-rows", type=int, default=4096)
+    ap.add_argument("--cpu-rows", type=int, default=None,
+                    help="rows of the oracle's sample (default: 4096 for c2, 256 for c3)")
     ap.add_argument("--stream-rows", type=int, default=1024,
                     help="row-block height of the streamed host update in the e2e loop")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.cpu_rows is None:
+        args.cpu_rows = {"c3": 256}.get(args.workload, 4096)
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -523,18 +579,20 @@ def main():
         return
     w = workload(args.workload)
     metric = "one-pass quaternion approx: A GB/s & TFLOPS, split-BF16 vs FP32 at equal error"
-    config = {"workload": f"{w['name']}: quaternion A {w['m']}x{w['n']} FP32 planes, "
-                          f"sigma_i=i^-2, k={w['k']}, s={w['s']}, l={w['l']}, Gaussian Omega/Psi",
+    abytes_w = (3 if w.get("pure") else 4) * w["m"] * w["n"] * (8 if args.prec == "fp64" else 4)
+    config = {"workload": f"{w['name']}: {WORKLOAD_TEXT[w['name']]}",
               "m": w["m"], "n": w["n"], "s": w["s"], "l": w["l"], "prec": args.prec,
               "rangefinder": args.rangefinder, "n_correction": 3, "rf_prec": args.rf_prec,
-              "l2": "inputs larger than L2 (A is 1.07 GB per step)", "parallelism": "replicas"}
+              "l2": "inputs larger than L2 (A is %.2f GB per step)" % (abytes_w / 1e9),
+              "parallelism": "replicas"}
 
     if args.impl == "reference":
         if rank != 0:
             return
         vals = []
+        smp = cpu_sample(w, args.cpu_rows)
         for i in range(args.warmup + args.steps):
-            gbs, sec, thr, sample = cpu_baseline(w, args.cpu_rows)
+            gbs, sec, thr, sample = cpu_baseline(w, args.cpu_rows, sample=smp)
             if i >= args.warmup:
                 vals.append((gbs, sec))
         v = statistics.median([g for g, _ in vals])

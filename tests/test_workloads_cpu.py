@@ -48,3 +48,31 @@ def test_c4_batch_generator_on_cpu():
         R = min(m, n, 12)
         np.testing.assert_allclose(sv[:R], np.exp(-np.arange(1, R + 1) / 8.0), rtol=1e-5)
         assert sv[R:].max(initial=0.0) < 1e-5
+
+
+def test_c3_generator_range_and_rank_structure():
+    """c3: every channel lies in [0, 1] (rescaled to [0, 0.98] plus U(0, 0.02) noise), and
+    without the noise each channel is a sum of 64 cosine modes, i.e. rank <= 128."""
+    import torch
+    A = WL.make_c3("cpu", m=300, n=257)
+    assert A.shape == (3, 300, 257)
+    assert float(A.min()) >= 0.0 and float(A.max()) <= 1.0
+    sv = torch.linalg.svdvals(A[0].double())
+    assert float(sv[128] / sv[0]) < 0.05       # the smooth part: 128 real directions
+
+
+def test_c5_generator_is_divergence_free():
+    """c5: every snapshot is a divergence-free velocity field on the periodic grid (spectral
+    divergence, up to the 1e-4 noise), and its columns span at most 32 modes."""
+    import torch
+    g, steps = 16, 12
+    A = WL.make_c5("cpu", grid=g, steps=steps, modes=6, seed=3).double().numpy()
+    k = np.fft.fftfreq(g) * g
+    K = np.meshgrid(k, k, k, indexing="ij")
+    for t in range(steps):
+        v = A[:, :, t].reshape(3, g, g, g)
+        div = sum(np.fft.ifftn(1j * K[d] * np.fft.fftn(v[d])).real for d in range(3))
+        # noise 1e-4 per entry, amplified by at most |k| <= 8 per axis
+        assert np.abs(div).max() <= 3 * 8 * 4 * 1e-4 + 1e-6 * np.abs(v).max()
+    sv = np.linalg.svd(np.concatenate([A[0], A[1], A[2]], 0), compute_uv=False)
+    assert sv[6] / sv[0] < 1e-3                    # 6 modes plus the noise floor

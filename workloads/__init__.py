@@ -26,6 +26,19 @@ that are not available):
       decay) or diag(1 (R times), 10^-q, 10^-2q, ...) (exponential decay); the paper plots
       xi = 0.01, p = 2, q = 0.25 and does not state R (R = 10 here, the count of leading
       ones in the practical-sketching test matrices the example follows).
+  c3  31365 x 27125 pure quaternion (real part 0), FP32, image-like: per channel (i, j, k)
+      f(p, q) = sum_{t<64} a_t cos(2 pi (u_t p / m + v_t q / n) + phi_t) with integer
+      frequencies u_t, v_t ~ U{0..8}, a_t ~ N(0, 1), phi_t ~ U[0, 2 pi), min-max rescaled to
+      [0, 0.98], plus U(0, 0.02) noise; k=100, s=201, l=403; Rademacher embeddings
+      (make_c3, built on the device).
+  c5  2,097,152 x 256 pure quaternion (a 128^3 grid times 256 time steps; the velocity
+      components are the i, j, k parts), FP32: 32 divergence-free Taylor-Green-type modes
+      (A_x cos(a x) sin(b y) sin(c z), A_y sin(a x) cos(b y) sin(c z), 0) with integer
+      wavenumbers a, b, c in 1..4 and A_x a + A_y b = 0, each turned by a random signed
+      permutation of the axes (an orthogonal map of the periodic grid onto itself, which
+      keeps the field divergence free), times a time-periodic amplitude
+      alpha_t sin(2 pi tau / T_t + phi_t), plus 1e-4 Gaussian noise; k=20, s=41, l=83;
+      Gaussian embeddings (make_c5, built on the device).
 Random quaternion-orthonormal factors are built as U = D Q W: Q real orthonormal (QR of a
 real Gaussian), W the unitary polar factor of an R x R quaternion Gaussian (from the
 eigendecomposition of its Hermitian complex form), D a diagonal of random unit
@@ -44,6 +57,12 @@ WORKLOADS = {
     # on R = min(m, n, 320) columns, Rademacher embeddings, split-BF16 sketch
     "c4": dict(count=256, lo=256, hi=4096, k_lo=8, k_hi=64, rank_cap=320, precision="bf16x3",
                emb="rademacher", seed=0),
+    # image-like pure quaternion (the colour-image experiment's shape), Rademacher embeddings
+    "c3": dict(m=31365, n=27125, k=100, s=201, l=403, precision="bf16x3", emb="rademacher",
+               seed=0, pure=True, modes=64),
+    # tall flow-snapshot pure quaternion (128^3 grid x 256 time steps), Gaussian embeddings
+    "c5": dict(m=128 ** 3, n=256, k=20, s=41, l=83, precision="bf16x3", emb="gaussian", seed=0,
+               pure=True, grid=128, modes=32),
 }
 
 
@@ -229,3 +248,94 @@ def make_c4_batch(device, spec=None):
         buf[:, :, :n] = torch.stack([w, x, y, z])
         out.append((m, n, k, buf[:, :, :n]))
     return out
+
+
+def _pad4(n):
+    return (n + 3) // 4 * 4
+
+
+def make_c3(device, m=None, n=None, seed=None, modes=None, rows=None):
+    """c3 (image-like pure quaternion) on a torch device: a (3, m, ldd) FP32 tensor holding the
+    i, j, k planes (ldd = n rounded up to a multiple of 4), viewed as (3, m, n); the real
+    plane is zero and not stored.  Smaller m, n give shape classes with the same structure;
+    ``rows`` keeps only the first rows of the m-row image (rescaled on those rows)."""
+    import torch
+    spec = WORKLOADS["c3"]
+    m = spec["m"] if m is None else m
+    n = spec["n"] if n is None else n
+    seed = spec["seed"] if seed is None else seed
+    modes = spec["modes"] if modes is None else modes
+    rng = np.random.default_rng(seed)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) + 1)
+    mr = m if rows is None else min(rows, m)
+    buf = torch.empty((3, mr, _pad4(n)), dtype=torch.float32, device=device)
+    p = torch.arange(mr, device=device, dtype=torch.float64) / m
+    q = torch.arange(n, device=device, dtype=torch.float64) / n
+    for ch in range(3):
+        u = torch.as_tensor(rng.integers(0, 9, modes), device=device, dtype=torch.float64)
+        v = torch.as_tensor(rng.integers(0, 9, modes), device=device, dtype=torch.float64)
+        a = torch.as_tensor(rng.standard_normal(modes), device=device)
+        phi = torch.as_tensor(rng.uniform(0.0, 2.0 * np.pi, modes), device=device)
+        alpha = 2.0 * np.pi * p[:, None] * u[None, :] + phi[None, :]       # m x modes
+        beta = 2.0 * np.pi * q[:, None] * v[None, :]                       # n x modes
+        # cos(alpha + beta) = cos alpha cos beta - sin alpha sin beta: a rank-2 modes product
+        L = torch.cat([a * torch.cos(alpha), -a * torch.sin(alpha)], 1).float()
+        Rt = torch.cat([torch.cos(beta), torch.sin(beta)], 1).float()
+        f = buf[ch, :, :n]
+        torch.matmul(L, Rt.T, out=f) if f.is_contiguous() else f.copy_(L @ Rt.T)
+        lo, hi = f.min(), f.max()
+        f.sub_(lo).mul_(0.98 / (hi - lo))
+        f.add_(torch.rand((mr, n), generator=gen, device=device, dtype=torch.float32).mul_(0.02))
+    return buf[:, :, :n]
+
+
+def make_c5(device, grid=None, steps=None, seed=None, modes=None):
+    """c5 (tall flow snapshots, pure quaternion) on a torch device: a (3, grid^3, steps) FP32
+    tensor with the i, j, k planes (velocity components); rows are grid points (x slowest),
+    columns are time steps.  The real plane is zero and not stored."""
+    import torch
+    spec = WORKLOADS["c5"]
+    grid = spec["grid"] if grid is None else grid
+    steps = spec["n"] if steps is None else steps
+    seed = spec["seed"] if seed is None else seed
+    modes = spec["modes"] if modes is None else modes
+    rng = np.random.default_rng(seed)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) + 1)
+    x = 2.0 * np.pi * torch.arange(grid, device=device, dtype=torch.float64) / grid
+    m = grid ** 3
+    U = torch.empty((3, m, modes), dtype=torch.float32, device=device)
+    for t in range(modes):
+        a, b, c = (int(v) for v in rng.integers(1, 5, 3))
+        nrm = np.hypot(a, b)
+        ax, ay = b / nrm, -a / nrm                       # ax a + ay b = 0: divergence free
+        fx = [torch.cos(a * x), torch.sin(b * x), torch.sin(c * x)]
+        fy = [torch.sin(a * x), torch.cos(b * x), torch.sin(c * x)]
+        comp = [ax * fx[0][:, None, None] * fx[1][None, :, None] * fx[2][None, None, :],
+                ay * fy[0][:, None, None] * fy[1][None, :, None] * fy[2][None, None, :],
+                torch.zeros((grid, grid, grid), device=device, dtype=torch.float64)]
+        # random signed permutation P of the axes: v(x) = P u(P^T x)
+        perm = rng.permutation(3)
+        sign = rng.choice([-1.0, 1.0], 3)
+        field = torch.stack(comp)                         # (3, gx, gy, gz), u(x)
+        for d in range(3):                                # u(P^T x): reflect, then permute axes
+            if sign[d] < 0:
+                field = torch.roll(torch.flip(field, dims=[1 + d]), shifts=1, dims=1 + d)
+        field = field.permute(0, *(1 + int(np.argsort(perm)[e]) for e in range(3)))
+        newf = torch.empty_like(field)
+        for d in range(3):                                # components: (P u)_perm[d] = sign[d] u_d
+            newf[int(perm[d])] = sign[d] * field[d]
+        U[:, :, t] = newf.reshape(3, m).float()
+    tau = torch.arange(steps, device=device, dtype=torch.float64)
+    amp = torch.empty((modes, steps), device=device, dtype=torch.float64)
+    for t in range(modes):
+        alpha = (0.5 + rng.uniform()) * 0.85 ** t
+        period = rng.uniform(16.0, 256.0)
+        amp[t] = alpha * torch.sin(2.0 * np.pi * tau / period + rng.uniform(0.0, 2.0 * np.pi))
+    A = torch.empty((3, m, steps), dtype=torch.float32, device=device)
+    ampf = amp.float()
+    for ch in range(3):
+        torch.matmul(U[ch], ampf, out=A[ch])
+        A[ch].add_(torch.randn((m, steps), generator=gen, device=device, dtype=torch.float32).mul_(1e-4))
+    return A
