@@ -18,6 +18,16 @@ __device__ __forceinline__ T ld_elem(const void* base, int64_t idx) {
   return static_cast<const T*>(base)[idx];
 }
 
+// Double-float accumulators are renormalised (lo folded into hi by TwoSum) every kRenorm
+// k-steps: the compensated multiply-add collects every rounding error in lo with plain FP32
+// additions, whose own rounding grows with |lo|; kept at |lo| <= ulp(hi)/2, the accumulated
+// error of a K-term sum stays near sqrt(K) u_fp32^2 of the sum instead of K u_fp32^2.
+constexpr int kRenorm = 32;
+template <typename ACC>
+__device__ __forceinline__ void renorm(ACC& a) {
+  if constexpr (std::is_same<ACC, df64>::value) a = df_norm(a);
+}
+
 // c += a * b (Hamilton product) with A, B and accumulator types that may differ (an FP32 A
 // against a double-float B and accumulator uses the cheaper mixed fma).
 template <typename TA_, typename TB_, typename TC_>
@@ -142,6 +152,16 @@ __global__ void __launch_bounds__(256, TN == 1 ? 3 : ((sizeof(ACC) == 4 || TN ==
                   a[3][i], b[0][j], b[1][j], b[2][j], b[3][j]);
           }
         }
+    }
+    if constexpr (std::is_same<ACC, df64>::value) {
+      if (((k0 - kbeg) / BK) % (kRenorm / BK) == kRenorm / BK - 1) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) renorm(acc[q][i][j]);
+      }
     }
     if (has_next) {
       store_regs(buf ^ 1);
@@ -276,6 +296,9 @@ __global__ void __launch_bounds__(256) qgemm_small_kernel(GemmDesc g) {
         qmacx(cw, cx, cy, cz, As[0][kk][ty], As[1][kk][ty], As[2][kk][ty], As[3][kk][ty],
               Bs[0][kk][tx], Bs[1][kk][tx], Bs[2][kk][tx], Bs[3][kk][tx]);
       }
+    }
+    if constexpr (DF) {   // every BK = 16 k-steps (kRenorm >= BK)
+      renorm(cw); renorm(cx); renorm(cy); renorm(cz);
     }
     __syncthreads();
   }

@@ -15,8 +15,8 @@ these sizes, so it checks what it can compute exactly -- 256 sampled rows of Y a
 columns of W (rows of Y and columns of W are independent: 1e-5), the rangefinder on the
 GPU's own Y (H element by element at 100 u_df kappa(Y)^2, the sensitivity of the correction
 parameters; H X on sampled rows, which depends only on the range of H, at 100 u_df kappa(Y)),
-X = (Psi H)^dagger W on the GPU's own
-H, W and exported Psi (1e-12), and the error pass against the oracle's error of the same
+X = (Psi H)^dagger W on the GPU's own H, W and exported Psi (10 sqrt(m) u_df kappa(Psi H):
+Psi H sums m terms), and the error pass against the oracle's error of the same
 factors (c5: all rows; c3: a 2048-row block through the allocation-free entry point, and the
 whole matrix against an FP64 torch evaluation, within the split-BF16 bound of the error pass).
 
@@ -179,7 +179,10 @@ def _tall_whole_path_checks(pkg, name, planes, chunk):
         Pref += O.qmatmul(Pc, Href[:, r0:r1])
     X = qs.get("X").cpu().numpy()
     Xref = O.qls_solve(P, W)
-    assert rel(X, Xref) <= 1e-12, rel(X, Xref)
+    # P = Psi H sums m terms per entry: rounding ~ sqrt(m) u_df relative, which X carries
+    # times kappa(P)
+    bar_x = max(1e-12, 10 * np.sqrt(m) * UDF * _kappa(P))
+    assert rel(X, Xref) <= bar_x, (rel(X, Xref), bar_x)
     HXr = O.qmatmul(H[:, rows], X)
     HXr_ref = O.qmatmul(Href[:, rows], O.qls_solve(Pref, W))
     assert rel(HXr, HXr_ref) <= max(1e-12, 100 * UDF * kap), (rel(HXr, HXr_ref), kap)
