@@ -79,7 +79,16 @@ typedef enum { QS_EMB_GAUSSIAN = 0, QS_EMB_RADEMACHER = 1 } qs_embedding;
  *            Rademacher test matrices are exact in BF16, so only hi*hi + lo*hi is formed. */
 typedef enum { QS_PREC_FP64 = 0, QS_PREC_FP32 = 1, QS_PREC_BF16 = 2, QS_PREC_BF16X3 = 3 } qs_precision;
 
-typedef enum { QS_RF_PSEUDO_QR = 0, QS_RF_PSEUDO_SVD = 1 } qs_rangefinder_kind;
+/* Rangefinders (Sec. 3).  The two plain kinds take their thin QR by Cholesky-QR (fast; Q
+ * orthonormal to working precision while kappa(Y) stays below ~1e8); the _HOUSEHOLDER kinds
+ * take it by Householder reflections (one cooperative launch, more passes over Y; Q
+ * orthonormal to working precision for any kappa(Y)). */
+typedef enum {
+  QS_RF_PSEUDO_QR = 0,
+  QS_RF_PSEUDO_SVD = 1,
+  QS_RF_PSEUDO_QR_HOUSEHOLDER = 2,
+  QS_RF_PSEUDO_SVD_HOUSEHOLDER = 3
+} qs_rangefinder_kind;
 
 /* Arithmetic of the stages after the sketch: the rangefinders (Alg. 1, Alg. 2), the QB stage
  * (Alg. 3 with Alg. QLEQ) and the truncation stage (Alg. 4).  The paper runs all of them in
@@ -211,13 +220,15 @@ QS_API qs_status qsketch_update_batched(int32_t count, const qs_handle_t* handle
 
 /* Rangefinder H = F(Y) with R(H) = R(Y) (Sec. 3).
  *   QS_RF_PSEUDO_QR : Alg. 1.  Thin complex QR of Y_c (Cholesky-QR twice on the Gram of
- *                     Y_c, with a shift on breakdown), H from the Q factor, then
+ *                     Y_c, with a shift on breakdown; QS_RF_PSEUDO_QR_HOUSEHOLDER: by complex
+ *                     Householder reflections), H from the Q factor, then
  *                     n_correction steps H <- (1-eps) H + eps (H^dagger)*
  *                     (eq. CondNumReductionIter), eps from three power iterates (Sec. 3.1);
  *                     the steps are accumulated as right factors and H = Y D is formed
  *                     once.  n_correction in [0, 3]; 3 is the paper's default.
  *   QS_RF_PSEUDO_SVD: Alg. 2.  Complex SVD of chi_Y -- computed as a quaternion
- *                     Cholesky-QR (three passes) Y = Q R and the SVD of the 2s x 2s chi_R,
+ *                     Cholesky-QR (three passes; QS_RF_PSEUDO_SVD_HOUSEHOLDER: quaternion
+ *                     Householder reflections) Y = Q R and the SVD of the 2s x 2s chi_R,
  *                     since chi_Y = chi_Q chi_R -- one left vector per duplicated pair, SVD
  *                     repair of the bad pairs.  n_correction is ignored.
  * Returns QS_OK, or an argument error; numerical rank warnings are sticky (see header). */

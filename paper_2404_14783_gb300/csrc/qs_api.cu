@@ -13,6 +13,7 @@
 #include "qs_common.cuh"
 #include "qs_small.cuh"
 #include "qs_err_tc.cuh"
+#include "qs_householder.cuh"
 #include "qs_sketch_tc.cuh"
 
 using namespace qs;
@@ -86,6 +87,7 @@ size_t plan(const qs_config& c, qs_handle_s* h) {
   const size_t pack_bytes = tc_pack_bytes(c);
   size_t o_pack = take(pack_bytes);
   size_t o_psvd = take(psvd_work_bytes(c.s));
+  size_t o_hh = take(qhh_scratch_bytes((int)c.s));
   size_t o_epack = take(tc_mode(c.prec) ? err_tc_pack_bytes(c.m, c.n, c.s) : 0);
   // truncation stage: X* (n x s, FP64), H_r (m x s), X_r (s x n), sigma (s)
   size_t o_trunc = take(align_up(4 * n * s * 8) + align_up(4 * m * s * ehx) + align_up(4 * s * n * ehx) +
@@ -96,7 +98,7 @@ size_t plan(const qs_config& c, qs_handle_s* h) {
     h->off_status = o_status; h->off_scalars = o_scal; h->off_omega = o_om; h->off_psi = o_psi;
     h->off_y = o_y; h->off_w = o_w; h->off_h = o_h; h->off_x = o_x; h->off_gram = o_gram;
     h->off_small = o_small; h->off_p = o_p; h->off_core = o_core; h->off_pack = o_pack;
-    h->off_psvd = o_psvd; h->off_epack = o_epack; h->off_trunc = o_trunc;
+    h->off_psvd = o_psvd; h->off_epack = o_epack; h->off_trunc = o_trunc; h->off_hh = o_hh;
     h->off_tail = off; h->small_bytes = small_bytes; h->core_bytes = core_bytes;
     h->pack_bytes = pack_bytes;
   }
@@ -256,6 +258,8 @@ cudaError_t chol_inv(const Ctx& x, const Mat& G, const Mat& L, const Mat& Li, in
   return e;
 }
 
+qs_status corrections(const Ctx& x, int ncorr, const Mat& B, Mat Dcur, Mat Dnext, const Mat& G0);
+
 qs_status pseudo_qr(const Ctx& x, int ncorr) {
   const int s = (int)x.s;
   const Mat G = x.small(0), L = x.small(1), Li = x.small(2), D = x.small(3), D2 = x.small(4),
@@ -277,7 +281,31 @@ qs_status pseudo_qr(const Ctx& x, int ncorr) {
   // (Alg. 1 step 3) H_0 = Y D2; its quaternion Gram G_0 = R2^{-*} (T*T) R2^{-1}
   QS_CU(gemm(x, Li, false, G, Tm, s, s, s, 1.0, 0.0, x.acc_hi(), false));
   QS_CU(gemm(x, Tm, false, R2, G0, s, s, s, 1.0, 0.0, x.acc_hi(), false));
-  Mat Dcur = D2, Dnext = D;
+  return corrections(x, ncorr, Y, D2, D, G0);
+}
+
+// Thin complex QR of Y_c by Householder reflections (any kappa(Y)): H_0 = the relabelled Q
+// factor, explicit in the second tall temporary, and G_0 = H_0* H_0.
+qs_status pseudo_qr_householder(const Ctx& x, int ncorr) {
+  const int s = (int)x.s;
+  const Mat Rq = x.small(5), D = x.small(3), D2 = x.small(4), G0 = x.small(7);
+  const Mat Y = x.Y(), T = x.T(), H0 = x.T2();
+  const void* yp[4];
+  Y.cplanes(yp);
+  QS_CU(launch_qhh(x.m, s, 1, yp, Y.f64, Y.ld, (double*)T.p, (double*)H0.p, (double*)Rq.p,
+                   x.h->ws + x.h->off_hh, x.acc_hi() == 2, x.st));
+  QS_CU(gram(x, H0, x.m, s, G0));
+  QS_CU(launch_qeye((double*)D2.p, D2.ld, D2.ps, s, x.st));
+  return corrections(x, ncorr, H0, D2, D, G0);
+}
+
+// (Alg. 1 step 4) on H_0 = B D0 with quaternion Gram G0: the corrections as right factors
+// and H = B D.
+qs_status corrections(const Ctx& x, int ncorr, const Mat& B, Mat Dcur, Mat Dnext, const Mat& G0) {
+  const int s = (int)x.s;
+  const Mat G = x.small(0), L = x.small(1), Li = x.small(2), Gi = x.small(8), M = x.small(9);
+  const Mat T = x.T();
+  double* sc = x.scalars();
   Mat Gk = G0;
   // (Alg. 1 step 4) corrections H <- (1-eps) H + eps (H^dagger)* = H ((1-eps) I + eps G^{-1})
   for (int k = 0; k < ncorr; ++k) {
@@ -301,18 +329,18 @@ qs_status pseudo_qr(const Ctx& x, int ncorr) {
       if (x.h->cfg.s <= qchol_inv_max_n()) {
         QS_CU(launch_qgram_update((const double*)Gk.p, (double*)G.p, (const double*)Gi.p, G.ld, G.ps,
                                   s, sc, kScEps0 + k, x.st));
-        QS_CU(gemm(x, Y, false, Dcur, T, x.m, s, s, 1.0, 0.0, x.acc_hi(), false, gate, 1.0));
+        QS_CU(gemm(x, B, false, Dcur, T, x.m, s, s, 1.0, 0.0, x.acc_hi(), false, gate, 1.0));
         QS_CU(gram(x, T, x.m, s, G, gate, 1.0));
       } else {
-        QS_CU(gemm(x, Y, false, Dcur, T, x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
+        QS_CU(gemm(x, B, false, Dcur, T, x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
         QS_CU(gram(x, T, x.m, s, G));
       }
       Gk = G;
     }
   }
-  // H = Y D in the FP64 class: D carries the correction factors, whose norm times ||Y||
+  // H = B D in the FP64 class: D carries the correction factors, whose norm times ||Y||
   // is far above 1/u32, so an FP32 product would tilt the range of H away from that of Y
-  QS_CU(gemm(x, Y, false, Dcur, x.H(), x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
+  QS_CU(gemm(x, B, false, Dcur, x.H(), x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
   return QS_OK;
 }
 
@@ -390,6 +418,22 @@ qs_status pseudo_svd(const Ctx& x) {
   // H = Q Z = T2 R3^{-1} Z: R3 is close to I, so this product adds no kappa(Y)-sized rounding
   QS_CU(gemm(x, R3i, false, Z, D, s, s, s, 1.0, 0.0, x.acc_hi(), false));
   QS_CU(gemm(x, T2, false, D, x.H(), x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
+  return QS_OK;
+}
+
+// Pseudo-SVD (Alg. 2) with the quaternion QR Y = Q R by Householder reflections (any
+// kappa(Y)): the small SVD stage on chi_R gives Z, and H = Q Z.
+qs_status pseudo_svd_householder(const Ctx& x) {
+  const int s = (int)x.s;
+  const Mat R = x.small(12), Z = x.small(13);
+  const Mat Y = x.Y(), T = x.T(), Q = x.T2();
+  const void* yp[4];
+  Y.cplanes(yp);
+  QS_CU(launch_qhh(x.m, s, 0, yp, Y.f64, Y.ld, (double*)T.p, (double*)Q.p, (double*)R.p,
+                   x.h->ws + x.h->off_hh, x.acc_hi() == 2, x.st));
+  QS_CU(launch_psvd_small((const double*)R.p, R.ld, R.ps, s, x.h->ws + x.h->off_psvd, (double*)Z.p,
+                          Z.ld, Z.ps, x.h->cfg.seed, x.scalars(), x.status(), x.st));
+  QS_CU(gemm(x, Q, false, Z, x.H(), x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
   return QS_OK;
 }
 
@@ -532,7 +576,7 @@ qs_status qsketch_update_batched(int32_t count, const qs_handle_t* handles,
 
 qs_status qrangefinder(qs_handle_t h, int32_t kind, int32_t n_correction, void* stream) {
   if (!h) return QS_ERR_INVALID;
-  if (kind != QS_RF_PSEUDO_QR && kind != QS_RF_PSEUDO_SVD) return QS_ERR_INVALID;
+  if (kind < QS_RF_PSEUDO_QR || kind > QS_RF_PSEUDO_SVD_HOUSEHOLDER) return QS_ERR_INVALID;
   if (n_correction < 0 || n_correction > 3) return QS_ERR_INVALID;
   const qs_config& c = h->cfg;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -540,8 +584,11 @@ qs_status qrangefinder(qs_handle_t h, int32_t kind, int32_t n_correction, void* 
   QS_CU(launch_clear_stop(x.status(), st));
   QS_CU(cudaMemsetAsync(x.scalars() + kScKappa, 0, sizeof(double) * 6, st));
   QS_CU(cudaMemsetAsync(x.scalars() + kScGate, 0, sizeof(double), st));
-  h->h_well_conditioned = kind == QS_RF_PSEUDO_SVD || n_correction > 0;
+  h->h_well_conditioned = kind == QS_RF_PSEUDO_SVD || kind == QS_RF_PSEUDO_SVD_HOUSEHOLDER ||
+                          n_correction > 0;
   if (kind == QS_RF_PSEUDO_QR) return pseudo_qr(x, n_correction);
+  if (kind == QS_RF_PSEUDO_QR_HOUSEHOLDER) return pseudo_qr_householder(x, n_correction);
+  if (kind == QS_RF_PSEUDO_SVD_HOUSEHOLDER) return pseudo_svd_householder(x);
   return pseudo_svd(x);
 }
 

@@ -357,6 +357,13 @@ __global__ void qcopy_kernel(const TS* S, int64_t lds, int64_t pss, TD* D, int64
   }
 }
 
+__global__ void qeye_kernel(double* M, int64_t ld, int64_t ps, int n) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 4 * n * n; e += gridDim.x * blockDim.x) {
+    const int p = e / (n * n), i = (e / n) % n, j = e % n;
+    M[p * ps + (int64_t)i * ld + j] = (p == 0 && i == j) ? 1.0 : 0.0;
+  }
+}
+
 __global__ void clear_stop_kernel(int32_t* status) {
   if (threadIdx.x == 0) atomicAnd(status, ~kDevStopCorr);
 }
@@ -440,6 +447,12 @@ cudaError_t launch_qgram_update(const double* G, double* Gn, const double* Gi, i
                                 cudaStream_t st) {
   const int blocks = std::max(1, std::min(64, (n * n + 255) / 256));
   qgram_update_kernel<<<blocks, 256, 0, st>>>(G, Gn, Gi, ld, ps, n, scalars, slot);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qeye(double* M, int64_t ld, int64_t ps, int n, cudaStream_t st) {
+  qeye_kernel<<<std::max(1, std::min(64, (4 * n * n + 255) / 256)), 256, 0, st>>>(M, ld, ps, n);
   count_launch();
   return cudaGetLastError();
 }

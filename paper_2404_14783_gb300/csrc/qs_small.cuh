@@ -19,6 +19,8 @@ cudaError_t launch_qconjT(const void* S, int s_f64, int64_t lds, int64_t pss, vo
 cudaError_t launch_qcopy(const void* S, int s_f64, int64_t lds, int64_t pss, void* D, int d_f64,
                          int64_t ldd, int64_t psd, int64_t r, int64_t c, cudaStream_t st);
 cudaError_t launch_clear_stop(int32_t* status, cudaStream_t st);
+// M = I (n x n quaternion, FP64 planes).
+cudaError_t launch_qeye(double* M, int64_t ld, int64_t ps, int n, cudaStream_t st);
 // Gram of the corrected H in s x s space (gated by scalars[kScGate] == 1).
 cudaError_t launch_qgram_update(const double* G, double* Gn, const double* Gi, int64_t ld,
                                 int64_t ps, int n, const double* scalars, int slot,

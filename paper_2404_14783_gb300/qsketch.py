@@ -26,7 +26,10 @@ QS_FLAG_TEST_WITHHOLD_COPY = 1
 PRECISIONS = {"fp64": QS_PREC_FP64, "fp32": QS_PREC_FP32, "bf16": QS_PREC_BF16,
               "bf16x3": QS_PREC_BF16X3}
 EMBEDDINGS = {"gaussian": QS_EMB_GAUSSIAN, "rademacher": QS_EMB_RADEMACHER}
-RANGEFINDERS = {"pseudo_qr": QS_RF_PSEUDO_QR, "pseudo_svd": QS_RF_PSEUDO_SVD}
+QS_RF_PSEUDO_QR_HOUSEHOLDER, QS_RF_PSEUDO_SVD_HOUSEHOLDER = 2, 3
+RANGEFINDERS = {"pseudo_qr": QS_RF_PSEUDO_QR, "pseudo_svd": QS_RF_PSEUDO_SVD,
+                "pseudo_qr_householder": QS_RF_PSEUDO_QR_HOUSEHOLDER,
+                "pseudo_svd_householder": QS_RF_PSEUDO_SVD_HOUSEHOLDER}
 RF_PRECISIONS = {"df64": QS_RF_PREC_DF64, "fp64": QS_RF_PREC_FP64, "mixed": QS_RF_PREC_MIXED}
 
 ABI_SYMBOLS = ("qsketch_workspace_bytes", "qsketch_create", "qsketch_update", "qrangefinder",

@@ -85,12 +85,15 @@ def _unit(prec, rf):
     return U64 if prec == "fp64" or rf == "fp64" else UDF
 
 
+@pytest.mark.parametrize("kind", ["pseudo_qr", "pseudo_qr_householder"])
 @pytest.mark.parametrize("prec,rf", MODES)
 @pytest.mark.parametrize("kappa", [10.0, 1e3])
-def test_pseudo_qr_with_corrections_elementwise(pkg, prec, rf, kappa):
+def test_pseudo_qr_with_corrections_elementwise(pkg, prec, rf, kappa, kind):
+    """Both thin-QR routes of Alg. 1 step 2 (Cholesky-QR, Householder reflections) give the
+    same canonical Q (R_ii > 0), hence the same H."""
     qs = pkg.QSketch(M, N, S, L, emb="gaussian", prec=prec, rf_prec=rf, seed=3)
     Y = _put(qs, "Y", _make_y(kappa, 11), prec == "fp64")
-    qs.rangefinder("pseudo_qr", 3)
+    qs.rangefinder(kind, 3)
     torch.cuda.synchronize()
     assert qs.device_status() == 0
     H = qs.get("H")

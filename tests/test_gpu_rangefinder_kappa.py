@@ -80,14 +80,15 @@ def _proj(H):
     return C @ np.linalg.pinv(C)
 
 
+@pytest.mark.parametrize("kind", ["pseudo_qr", "pseudo_qr_householder"])
 @pytest.mark.parametrize("prec,kappa,bar", [("fp64", 1e2, 1e-12), ("fp64", 1e5, 1e-9),
                                             ("fp64", 1e7, 1e-7), ("bf16x3", 1e2, 1e-6),
                                             ("bf16x3", 1e5, 1e-6)])
-def test_pseudo_qr_kappa_sweep(pkg, prec, kappa, bar):
+def test_pseudo_qr_kappa_sweep(pkg, prec, kappa, bar, kind):
     Y = _make_y(kappa, seed=int(np.log10(kappa)))
     if prec != "fp64":
         Y = Y.astype(np.float32).astype(np.float64)     # the values the FP32 handle holds
-    qs, H, sc = _run(pkg, Y, "pseudo_qr", prec, seed=1)
+    qs, H, sc = _run(pkg, Y, kind, prec, seed=1)
     info = {}
     Href = O.pseudo_qr(Y, 3, info=info)
     assert qs.device_status() == 0
@@ -99,10 +100,18 @@ def test_pseudo_qr_kappa_sweep(pkg, prec, kappa, bar):
     np.testing.assert_allclose(sc[2:5], info["eps"], rtol=1e-3)
 
 
-@pytest.mark.parametrize("kappa", [1e2, 1e6, 1e10, 1e13])
-def test_pseudo_svd_kappa_sweep(pkg, kappa):
+@pytest.mark.parametrize("kind,kappa", [("pseudo_svd", 1e2), ("pseudo_svd", 1e6), ("pseudo_svd", 1e10),
+                                        ("pseudo_svd", 1e13),
+                                        ("pseudo_svd_householder", 1e2),
+                                        ("pseudo_svd_householder", 1e6),
+                                        ("pseudo_svd_householder", 1e13),
+                                        ("pseudo_svd_householder", 1e15),
+                                        ("pseudo_svd_householder", 1e16)])
+def test_pseudo_svd_kappa_sweep(pkg, kind, kappa):
+    """Householder's Q keeps R(H) containing R(Y) to working precision past kappa = 1e15,
+    where the Gram of Y (kappa^2 > 1/u) no longer determines it."""
     Y = _make_y(kappa, seed=10 + int(np.log10(kappa)))
-    qs, H, sc = _run(pkg, Y, "pseudo_svd", "fp64", seed=2)
+    qs, H, sc = _run(pkg, Y, kind, "fp64", seed=2)
     assert np.all(np.isfinite(H))
     orth = 1e-10 if kappa <= 1e6 else 1e-6
     np.testing.assert_allclose(O.qmatmul(O.qconjT(H), H), O.qeye(S), atol=orth)
