@@ -7,7 +7,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "qs_common.cuh"
@@ -89,6 +91,7 @@ size_t plan(const qs_config& c, qs_handle_s* h) {
   size_t o_psvd = take(psvd_work_bytes(c.s));
   size_t o_hh = take(qhh_scratch_bytes((int)c.s));
   size_t o_epack = take(tc_mode(c.prec) ? err_tc_pack_bytes(c.m, c.n, c.s) : 0);
+  size_t o_desc = take(tc_mode(c.prec) ? tc_item_bytes() : 0);   // batched-launch descriptor
   // truncation stage: X* (n x s, FP64), H_r (m x s), X_r (s x n), sigma (s)
   size_t o_trunc = take(align_up(4 * n * s * 8) + align_up(4 * m * s * ehx) + align_up(4 * s * n * ehx) +
                         s * 8);
@@ -99,6 +102,7 @@ size_t plan(const qs_config& c, qs_handle_s* h) {
     h->off_y = o_y; h->off_w = o_w; h->off_h = o_h; h->off_x = o_x; h->off_gram = o_gram;
     h->off_small = o_small; h->off_p = o_p; h->off_core = o_core; h->off_pack = o_pack;
     h->off_psvd = o_psvd; h->off_epack = o_epack; h->off_trunc = o_trunc; h->off_hh = o_hh;
+    h->off_desc = o_desc;
     h->off_tail = off; h->small_bytes = small_bytes; h->core_bytes = core_bytes;
     h->pack_bytes = pack_bytes;
   }
@@ -437,6 +441,39 @@ qs_status pseudo_svd_householder(const Ctx& x) {
   return QS_OK;
 }
 
+// Tuned plans of the batched sketch, keyed by the batch's signature (per item m, n, s, l,
+// precision, embedding, pureness, in order); process-wide.
+std::mutex g_plan_mu;
+std::unordered_map<uint64_t, TcBatchPlan> g_plans;
+
+uint64_t batch_key(int count, const qs_handle_s* const* hs) {
+  uint64_t k = 1469598103934665603ull;   // FNV-1a over the signature words
+  auto mix = [&](uint64_t v) {
+    for (int b = 0; b < 8; ++b) {
+      k ^= (v >> (8 * b)) & 0xff;
+      k *= 1099511628211ull;
+    }
+  };
+  mix((uint64_t)count);
+  for (int i = 0; i < count; ++i) {
+    const qs_config& c = hs[i]->cfg;
+    mix((uint64_t)c.m); mix((uint64_t)c.n); mix((uint64_t)c.s); mix((uint64_t)c.l);
+    mix((uint64_t)c.prec | ((uint64_t)c.emb << 8) | ((uint64_t)c.pure << 16));
+  }
+  return k;
+}
+bool tuned_plan(uint64_t key, TcBatchPlan* out) {
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  const auto it = g_plans.find(key);
+  if (it == g_plans.end()) return false;
+  *out = it->second;
+  return true;
+}
+void store_plan(uint64_t key, const TcBatchPlan& p) {
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  g_plans[key] = p;
+}
+
 bool planes_ok(const qs_handle_s* h, const void* const A[4]) {
   if (!A) return false;
   for (int p = 1; p < 4; ++p)
@@ -570,8 +607,58 @@ qs_status qsketch_update_batched(int32_t count, const qs_handle_t* handles,
     if (r != QS_OK) return r;
   }
   if (tch.empty()) return QS_OK;
+  TcBatchPlan plan{};
+  const bool tuned = tuned_plan(batch_key((int)tch.size(), tch.data()), &plan);
   return tc_sketch_replace_batched((int)tch.size(), tch.data(), tca.data(), tcl.data(),
-                                   static_cast<cudaStream_t>(stream));
+                                   static_cast<cudaStream_t>(stream), tuned ? &plan : nullptr);
+}
+
+// Autotuner of the batched sketch: times each candidate plan (item order x persistent grid)
+// on the caller's batch and keeps the fastest for batches with the same signature.
+qs_status qsketch_tune_batched(int32_t count, const qs_handle_t* handles, const void* const* A_planes,
+                               const int64_t* lda, int32_t reps, void* stream) {
+  if (count < 1 || reps < 1 || reps > 1000) return QS_ERR_INVALID;
+  std::vector<const qs_handle_s*> hs(handles, handles + count);
+  for (int32_t i = 0; i < count; ++i) {
+    const qs_handle_t h = handles[i];
+    const void* const* A = A_planes + 4 * (int64_t)i;
+    if (!h || !planes_ok(h, A) || lda[i] < h->cfg.n || !tc_mode(h->cfg.prec)) return QS_ERR_INVALID;
+    if (lda[i] % 4) return QS_ERR_INVALID;
+    for (int q = 0; q < 4; ++q)
+      if (A[q] && (reinterpret_cast<uintptr_t>(A[q]) & 15)) return QS_ERR_INVALID;
+    if ((h->cfg.s + 15) / 16 * 16 > 256) return QS_ERR_UNSUPPORTED;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return QS_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return QS_ERR_CUDA; }
+  static const TcBatchPlan cands[] = {{0, kNumSMs}, {1, kNumSMs}, {0, 144}, {1, 144}, {1, 128}};
+  float best = -1.f;
+  TcBatchPlan best_plan = cands[0];
+  qs_status rc = QS_OK;
+  for (const TcBatchPlan& c : cands) {
+    rc = tc_sketch_replace_batched(count, hs.data(), A_planes, lda, st, &c);   // warm-up
+    if (rc != QS_OK) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && rc == QS_OK; ++r)
+      rc = tc_sketch_replace_batched(count, hs.data(), A_planes, lda, st, &c);
+    cudaEventRecord(e1, st);
+    float ms = 0.f;
+    if (rc != QS_OK || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = rc == QS_OK ? QS_ERR_CUDA : rc;
+      break;
+    }
+    if (best < 0.f || ms < best) {
+      best = ms;
+      best_plan = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != QS_OK) return rc;
+  store_plan(batch_key(count, hs.data()), best_plan);
+  return QS_OK;
 }
 
 qs_status qrangefinder(qs_handle_t h, int32_t kind, int32_t n_correction, void* stream) {

@@ -87,7 +87,7 @@ struct qs_handle_s {
   size_t ws_bytes;
   // slab offsets (bytes) into ws
   size_t off_status, off_scalars, off_omega, off_psi, off_y, off_w, off_h, off_x;
-  size_t off_gram, off_small, off_p, off_core, off_pack, off_psvd, off_epack, off_trunc, off_hh, off_tail;
+  size_t off_gram, off_small, off_p, off_core, off_pack, off_psvd, off_epack, off_trunc, off_hh, off_desc, off_tail;
   size_t small_bytes, core_bytes, pack_bytes;
   // 0 after a pseudo-QR without corrections (H inherits kappa(Y)); the core solve then
   // forms Psi H in the FP64 class in the FP32 modes

@@ -36,6 +36,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "qs_sketch_tc.cuh"
 #include "qs_tc_ptx.cuh"
@@ -91,8 +92,48 @@ struct TcBatch {
   TcParams prm[MAXB];
   int tile_start[MAXB + 1];
   int count;
+  static constexpr bool kTable = false;
+  __device__ const TcParams& P(int i) const { return prm[i]; }
+  __device__ const TcMaps& M(int i) const { return maps[i]; }
+  __device__ int ts(int i) const { return tile_start[i]; }
+  __device__ int n() const { return count; }
+  __device__ int item_of(int t) const {
+    if constexpr (MAXB == 1) return 0;   // a compile-time index keeps item 0 in the constant bank
+    int i = 0;
+    while (i + 1 < count && tile_start[i + 1] <= t) ++i;
+    return i;
+  }
 };
 constexpr int kMaxBatch = 32;   // items per batched launch (kernel parameters <= 32764 bytes)
+
+// One work item's descriptor in global memory (the item's handle workspace): the batched
+// update writes it there, so one persistent launch can take any number of items.  Tensor maps
+// in global memory are read by the copy engine through the tensor-map proxy: the writer
+// releases them (fence.proxy.tensormap::generic.release) and the kernel acquires each before
+// its first copy (fence.proxy.tensormap::generic.acquire).
+struct __align__(128) TcItem {
+  TcMaps maps;
+  TcParams prm;
+};
+constexpr int kMaxTable = 1024;  // items per table launch (pointer table in kernel parameters)
+struct TcTable {
+  const TcItem* item[kMaxTable];
+  int tile_start[kMaxTable + 1];
+  int count;
+  static constexpr bool kTable = true;
+  __device__ const TcParams& P(int i) const { return item[i]->prm; }
+  __device__ const TcMaps& M(int i) const { return item[i]->maps; }
+  __device__ int ts(int i) const { return tile_start[i]; }
+  __device__ int n() const { return count; }
+  __device__ int item_of(int t) const {   // last i with tile_start[i] <= t
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  }
+};
 
 struct Shared {
   uint64_t a_full, a_ready, a_free, done;
@@ -125,24 +166,17 @@ __device__ bool wait_bar(uint64_t* bar, uint32_t parity, Shared* sh, int32_t* st
 // ---------------------------------------------------------------- the kernel
 // Every role walks the same sequence of global tiles (t = blockIdx.x, + gridDim.x, ...) and
 // looks up the item a tile belongs to, so the items of a batch share one persistent grid.
-template <int MAXB>
-__global__ void __launch_bounds__(kThreads, 1) fused_sketch_kernel(const __grid_constant__ TcBatch<MAXB> bt) {
+template <class Src>
+__global__ void __launch_bounds__(kThreads, 1) fused_sketch_kernel(const __grid_constant__ Src bt) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sRing = smem + kABytes;
   Shared* sh = reinterpret_cast<Shared*>(smem + kABytes + kStages * kStageBytes);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntiles = bt.tile_start[bt.count];
-  // (a single-item launch indexes item 0 at compile time, so its parameters stay
-  // constant-bank operands; a dynamic index reads them through generic loads, ~5% slower)
-  auto item_of = [&](int t) {
-    if constexpr (MAXB == 1) return 0;
-    int i = 0;
-    while (i + 1 < bt.count && bt.tile_start[i + 1] <= t) ++i;
-    return i;
-  };
-  int32_t* cur_status = bt.prm[0].status;   // status word of the item a role last worked on
+  const int ntiles = bt.ts(bt.n());
+  auto item_of = [&](int t) { return bt.item_of(t); };
+  int32_t* cur_status = bt.P(0).status;   // status word of the item a role last worked on
 
   if (threadIdx.x == 0) {
     mbar_init(&sh->a_full, 1);
@@ -185,12 +219,19 @@ __global__ void __launch_bounds__(kThreads, 1) fused_sketch_kernel(const __grid_
       bool a_outstanding = false;
       uint32_t a_fills = 0;
       bool stop = false;
+      int last_item = -1;
       for (int t = blockIdx.x; t < ntiles && !stop && !sh->abort; t += gridDim.x, ++t_local) {
         const int it = item_of(t);
-        const TcParams& p = bt.prm[it];
-        const TcMaps& mp = bt.maps[it];
+        const TcParams& p = bt.P(it);
+        const TcMaps& mp = bt.M(it);
         cur_status = p.status;
-        const int lt = t - bt.tile_start[it], ti = lt / p.tiles_n, tj = lt % p.tiles_n;
+        if constexpr (Src::kTable) {
+          if (it != last_item) {   // maps written by an earlier kernel: acquire them
+            for (int q = 0; q < 6; ++q) tmap_acquire(&mp.m[q]);
+            last_item = it;
+          }
+        }
+        const int lt = t - bt.ts(it), ti = lt / p.tiles_n, tj = lt % p.tiles_n;
         const int nwaves = nwaves_of(p);
         const uint32_t hl_tx = (p.nprod == 3) ? 2u : 1u;
         if (t_local > 0 && !wait_bar(&sh->a_free, (t_local - 1) & 1, sh, p.status)) break;
@@ -252,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_sketch_kernel(const __grid_
       const uint64_t dA_y = sdesc(a_base, 16, 2048);      // A tile as the Y products' A operand
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok && !sh->abort; t += gridDim.x, ++t_local) {
-        const TcParams& p = bt.prm[item_of(t)];
+        const TcParams& p = bt.P(item_of(t));
         cur_status = p.status;
         // products: hi*hi, then A_lo * (test hi) when nprod >= 2, (test lo) * A_hi when nprod == 3
         const bool alo = p.nprod >= 2, three = p.nprod == 3, pure = p.pure != 0;
@@ -343,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_sketch_kernel(const __grid_
     int t_local = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok && !sh->abort; t += gridDim.x, ++t_local) {
-      const TcParams& p = bt.prm[item_of(t)];
+      const TcParams& p = bt.P(item_of(t));
       if (!wait_bar(&sh->a_full, t_local & 1, sh, p.status)) { ok = false; break; }
       for (int gi = cw; gi < 64; gi += 4) {
         const int plane = gi >> 4, grp = gi & 15;
@@ -383,8 +424,8 @@ __global__ void __launch_bounds__(kThreads, 1) fused_sketch_kernel(const __grid_
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok && !sh->abort; t += gridDim.x) {
       const int it = item_of(t);
-      const TcParams& p = bt.prm[it];
-      const int lt = t - bt.tile_start[it], ti = lt / p.tiles_n, tj = lt % p.tiles_n;
+      const TcParams& p = bt.P(it);
+      const int lt = t - bt.ts(it), ti = lt / p.tiles_n, tj = lt % p.tiles_n;
       const int nwaves = nwaves_of(p);
       const bool wvec = ((p.col0 & 3) == 0) && ((p.ldw & 3) == 0);
       for (int wv = 0; wv < nwaves; ++wv, ++g) {
@@ -610,27 +651,46 @@ qs_status tc_prepare(const qs_handle_s& h, const void* const A[4], int64_t lda, 
   return QS_OK;
 }
 
-template <int MAXB>
-qs_status launch_fused(const TcBatch<MAXB>& bt, cudaStream_t st) {
-  static_assert(sizeof(TcBatch<MAXB>) <= 32764, "kernel parameters above the 32764-byte limit");
+template <class Src>
+qs_status launch_fused(const Src& bt, cudaStream_t st, int grid_max = kNumSMs) {
+  static_assert(sizeof(Src) <= 32764, "kernel parameters above the 32764-byte limit");
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(fused_sketch_kernel<MAXB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(fused_sketch_kernel<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes()) != cudaSuccess)
       return QS_ERR_CUDA;
     attr_set = true;
   }
   const int ntiles = bt.tile_start[bt.count];
   if (ntiles <= 0) return QS_OK;
-  const int grid = std::min(ntiles, kNumSMs);
-  fused_sketch_kernel<MAXB><<<grid, kThreads, smem_bytes(), st>>>(bt);
+  const int grid = std::min(ntiles, std::max(1, std::min(grid_max, kNumSMs)));
+  fused_sketch_kernel<Src><<<grid, kThreads, smem_bytes(), st>>>(bt);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? QS_OK : QS_ERR_CUDA;
 }
 
+// Up to kMaxBatch items of a batched update: their descriptors, and where each goes.
+struct TcPrepare {
+  TcBatch<kMaxBatch> bt;
+  TcItem* dst[kMaxBatch];
+};
+static_assert(sizeof(TcPrepare) <= 32764, "kernel parameters above the 32764-byte limit");
+
 // Y and W of every item set to zero (the batched update replaces the sketches): item i's
-// planes are mb x ldy and l x ldw floats from Y[q], W[q].
-__global__ void batch_zero_kernel(const __grid_constant__ TcBatch<kMaxBatch> bt) {
+// planes are mb x ldy and l x ldw floats from Y[q], W[q]; CTA 0 also writes each item's
+// descriptor to its place in global memory and releases the tensor maps to the copy engine.
+__global__ void batch_prepare_kernel(const __grid_constant__ TcPrepare pr) {
+  const TcBatch<kMaxBatch>& bt = pr.bt;
+  if (blockIdx.x == 0) {
+    for (int i = 0; i < bt.count; ++i) {
+      const uint32_t* src_m = reinterpret_cast<const uint32_t*>(&bt.maps[i]);
+      uint32_t* dm = reinterpret_cast<uint32_t*>(&pr.dst[i]->maps);
+      for (int w = threadIdx.x; w < (int)(sizeof(TcMaps) / 4); w += blockDim.x) dm[w] = src_m[w];
+      if (threadIdx.x == 0) pr.dst[i]->prm = bt.prm[i];
+    }
+    __syncthreads();
+    tmap_release();
+  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int i = 0; i < bt.count; ++i) {
     const TcParams& p = bt.prm[i];
@@ -655,25 +715,53 @@ qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t
   return launch_fused(bt, st);
 }
 
+size_t tc_item_bytes() { return sizeof(TcItem); }
+
 qs_status tc_sketch_replace_batched(int count, const qs_handle_s* const* hs, const void* const* A,
-                                    const int64_t* lda, cudaStream_t st) {
-  for (int i0 = 0; i0 < count; i0 += kMaxBatch) {
-    TcBatch<kMaxBatch> bt;
-    bt.count = std::min(kMaxBatch, count - i0);
-    bt.tile_start[0] = 0;
-    for (int j = 0; j < bt.count; ++j) {
-      const qs_handle_s& h = *hs[i0 + j];
-      const qs_status r = tc_prepare(h, A + 4 * (int64_t)(i0 + j), lda[i0 + j], 0, 0, h.cfg.m, h.cfg.n, 1.0,
-                                     bt.prm[j], bt.maps[j]);
-      if (r != QS_OK) return r;
-      const int64_t tiles = (int64_t)bt.prm[j].tiles_m * bt.prm[j].tiles_n;
-      if (bt.tile_start[j] + tiles > INT32_MAX) return QS_ERR_UNSUPPORTED;
-      bt.tile_start[j + 1] = bt.tile_start[j] + (int)tiles;
+                                    const int64_t* lda, cudaStream_t st, const TcBatchPlan* plan) {
+  // items in the plan's order (default: as given); every descriptor is built and checked
+  // on the host before anything is enqueued
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  if (plan && plan->largest_first)
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return hs[a]->cfg.m * hs[a]->cfg.n > hs[b]->cfg.m * hs[b]->cfg.n;
+    });
+  std::vector<TcItem> items(count);
+  for (int j = 0; j < count; ++j) {
+    const int i = order[j];
+    const qs_handle_s& h = *hs[i];
+    const qs_status r = tc_prepare(h, A + 4 * (int64_t)i, lda[i], 0, 0, h.cfg.m, h.cfg.n, 1.0,
+                                   items[j].prm, items[j].maps);
+    if (r != QS_OK) return r;
+  }
+  for (int c0 = 0; c0 < count; c0 += kMaxTable) {
+    const int cnt = std::min(kMaxTable, count - c0);
+    TcTable tab;
+    tab.count = cnt;
+    tab.tile_start[0] = 0;
+    for (int j = 0; j < cnt; ++j) {
+      const TcItem& it = items[c0 + j];
+      const int64_t tiles = (int64_t)it.prm.tiles_m * it.prm.tiles_n;
+      if (tab.tile_start[j] + tiles > INT32_MAX) return QS_ERR_UNSUPPORTED;
+      tab.tile_start[j + 1] = tab.tile_start[j] + (int)tiles;
+      const qs_handle_s& h = *hs[order[c0 + j]];
+      tab.item[j] = reinterpret_cast<const TcItem*>(h.ws + h.off_desc);
     }
-    batch_zero_kernel<<<2 * kNumSMs, 256, 0, st>>>(bt);
-    count_launch();
-    if (cudaGetLastError() != cudaSuccess) return QS_ERR_CUDA;
-    const qs_status r = launch_fused(bt, st);
+    // descriptors to the handles' workspaces and the sketches zeroed, kMaxBatch items a launch
+    for (int b0 = 0; b0 < cnt; b0 += kMaxBatch) {
+      TcPrepare pr;
+      pr.bt.count = std::min(kMaxBatch, cnt - b0);
+      for (int j = 0; j < pr.bt.count; ++j) {
+        pr.bt.maps[j] = items[c0 + b0 + j].maps;
+        pr.bt.prm[j] = items[c0 + b0 + j].prm;
+        pr.dst[j] = const_cast<TcItem*>(tab.item[b0 + j]);
+      }
+      batch_prepare_kernel<<<2 * kNumSMs, 256, 0, st>>>(pr);
+      count_launch();
+      if (cudaGetLastError() != cudaSuccess) return QS_ERR_CUDA;
+    }
+    const qs_status r = launch_fused(tab, st, plan ? plan->grid : kNumSMs);
     if (r != QS_OK) return r;
   }
   return QS_OK;

@@ -12,11 +12,20 @@ cudaError_t tc_pack_embeddings(const qs_handle_s& h, cudaStream_t st);
 qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t lda, int64_t row0,
                            int64_t col0, int64_t mb, int64_t nb, double eta, cudaStream_t st);
 // Y_i = A_i Omega_i, W_i = Psi_i A_i (the sketches replaced) for count handles in the
-// tensor-core modes, whole matrices: up to 32 matrices share one persistent launch (after one
-// launch that zeroes their Y and W).  Arguments are checked by the caller except the
-// tensor-core rules, which fail the call before that chunk's launches.
+// tensor-core modes, whole matrices: one launch per 32 matrices writes their descriptors and
+// zeroes their Y and W, then one persistent launch covers all their tiles.  Arguments are
+// checked by the caller except the tensor-core rules, which fail the call before any launch.
+// The items' descriptors go to their handles' workspaces (tc_item_bytes() at off_desc), so
+// one persistent launch covers up to 1024 items; a plan (from the autotuner) sets the item
+// order and the number of persistent CTAs.
+struct TcBatchPlan {
+  int largest_first;   // 1: items by decreasing m n (the largest ones start first)
+  int grid;            // persistent CTAs (<= the SM count)
+};
+size_t tc_item_bytes();
 qs_status tc_sketch_replace_batched(int count, const qs_handle_s* const* hs, const void* const* A,
-                                    const int64_t* lda, cudaStream_t st);
+                                    const int64_t* lda, cudaStream_t st,
+                                    const TcBatchPlan* plan = nullptr);
 // pseudo-SVD small stage (Alg. 2 on chi_R): Z (s x s quaternion) from R (s x s upper)
 size_t psvd_work_bytes(int64_t s);
 cudaError_t launch_psvd_small(const double* R, int64_t ldr, int64_t psr, int s, void* work,

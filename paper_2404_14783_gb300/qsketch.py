@@ -36,7 +36,7 @@ ABI_SYMBOLS = ("qsketch_workspace_bytes", "qsketch_create", "qsketch_update", "q
                "qonepass_core", "qreconstruct_error", "qsketch_get", "qs_last_device_error",
                "qsketch_destroy", "qs_status_string", "qs_launch_count", "qs_version",
                "qs_reconstruct_error_static", "qsketch_update_batched", "qtruncate",
-               "qsketch_update_host")
+               "qsketch_update_host", "qsketch_tune_batched")
 
 
 class QSConfig(ctypes.Structure):
@@ -82,12 +82,13 @@ def load_library(path=LIB_PATH):
     lib.qs_reconstruct_error_static.argtypes = [I64, I64, I64, I32, planes, I64, planes, I64,
                                                 planes, I64, VP, VP]
     lib.qsketch_update_batched.argtypes = [I32, P(VP), P(VP), P(I64), VP]
+    lib.qsketch_tune_batched.argtypes = [I32, P(VP), P(VP), P(I64), I32, VP]
     lib.qtruncate.argtypes = [VP, I64, VP]
     lib.qsketch_update_host.argtypes = [VP, planes, I64, I64, VP, ctypes.c_size_t, VP, D, D, VP]
     for name in ("qsketch_create", "qsketch_update", "qrangefinder", "qonepass_core",
                  "qreconstruct_error", "qsketch_get", "qs_last_device_error", "qsketch_destroy",
                  "qs_reconstruct_error_static", "qsketch_update_batched", "qtruncate",
-               "qsketch_update_host"):
+                 "qsketch_update_host", "qsketch_tune_batched"):
         getattr(lib, name).restype = I32
     _lib = lib
     return lib
@@ -144,6 +145,29 @@ def reconstruct_error_static(A, H, X, out, stream=None):
                                            ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
            "qs_reconstruct_error_static")
     return out
+
+
+def _batch_args(sketches, matrices):
+    count = len(sketches)
+    hs = (ctypes.c_void_p * max(count, 1))()
+    ptrs = (ctypes.c_void_p * max(4 * count, 1))()
+    lds = (ctypes.c_int64 * max(count, 1))()
+    for i, (qs, A) in enumerate(zip(sketches, matrices)):
+        p4, ld = _planes(A, qs.f64)
+        hs[i] = qs.handle
+        for q in range(4):
+            ptrs[4 * i + q] = p4[q]
+        lds[i] = ld
+    return count, hs, ptrs, lds
+
+
+def tune_batched(sketches, matrices, reps=3, stream=None):
+    """qsketch_tune_batched: time the candidate plans of the batched sketch on this batch and
+    keep the fastest for batches of the same signature (synchronises the stream)."""
+    lib = load_library()
+    count, hs, ptrs, lds = _batch_args(sketches, matrices)
+    return _check(lib.qsketch_tune_batched(count, hs, ptrs, lds, int(reps), _stream_ptr(stream)),
+                  "qsketch_tune_batched")
 
 
 def update_batched(sketches, matrices, stream=None):
