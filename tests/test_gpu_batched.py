@@ -102,16 +102,17 @@ def _batch(pkg, count, seed):
     return sk, sk1, mats, host, meta
 
 
-def _check_batch(sk, sk1, host, meta, tol_single):
+def _check_batch(sk, sk1, host, meta, tol_single, seeds=None):
     for i, (A, (m, n, s, l, emb, prec)) in enumerate(zip(host, meta)):
+        seed = 1000 + (i if seeds is None else seeds[i])
         assert sk[i].device_status() == 0
         Y, W = sk[i].get("Y").cpu().numpy(), sk[i].get("W").cpu().numpy()
         assert rel(Y, sk1[i].get("Y").cpu().numpy()) < tol_single, i
         assert rel(W, sk1[i].get("W").cpu().numpy()) < tol_single, i
         if i % 7 == 0:       # a sample against the oracle
             kind = O.EMB_RADEMACHER if emb == "rademacher" else O.EMB_GAUSSIAN
-            Om = O.draw_embedding(n, s, kind, O.STREAM_OMEGA, 1000 + i)
-            Psi = O.draw_embedding(l, m, kind, O.STREAM_PSI, 1000 + i)
+            Om = O.draw_embedding(n, s, kind, O.STREAM_OMEGA, seed)
+            Psi = O.draw_embedding(l, m, kind, O.STREAM_PSI, seed)
             Yr, Wr = O.sketch(A.astype(np.float64), Om, Psi)
             tol = 8e-3 if prec == "bf16" else 1e-5
             assert rel(Y, Yr) < tol and rel(W, Wr) < tol, i
@@ -175,4 +176,4 @@ def test_tuned_batched_plan(pkg):
         sk1[i].update(mats[i], theta=0.0)
     torch.cuda.synchronize()
     _check_batch([sk[i] for i in tc], [sk1[i] for i in tc], [host[i] for i in tc],
-                 [meta[i] for i in tc], 1e-6)
+                 [meta[i] for i in tc], 1e-6, seeds=tc)
