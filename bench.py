@@ -156,6 +156,11 @@ def make_A(w, device, prec):
     if w["name"] == "c5":
         P = WL.make_c5(device)
         return [None, P[0], P[1], P[2]]
+    if w["name"] == "lorenz":
+        import paper_2404_14783_gb300 as pkg
+        u0 = torch.as_tensor(WL.lorenz_initial_states(w["n"], seed=w["seed"], radius=w["radius"]),
+                             device=device)
+        return pkg.lorenz4d(u0, w["m"], w["dt"], w["a"], w["b"], w["c"], dtype=torch.float32)
     return WL.make_decay(w["m"], w["n"], seed=w["seed"], rank_cap=w.get("rank_cap", 1024),
                          device=device, dtype=dt).contiguous()
 
@@ -454,6 +459,55 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def run_rf_curve(args):
+    """Rangefinder time against the sketch height m with m = 20 s (the paper's timing of its
+    rangefinders, Sec. 3.4): Y (m x s, quaternion Gaussian, FP32 values in a split-BF16
+    handle, double-float stages) written into a handle; each kind timed with CUDA events over
+    `steps` calls after `warmup` calls."""
+    import numpy as np
+    import torch
+    import paper_2404_14783_gb300 as pkg
+    pkg.load_library()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    kinds = ("pseudo_qr", "pseudo_svd", "pseudo_qr_householder", "pseudo_svd_householder")
+    curve = []
+    sampler = ClockSampler(0)
+    sampler.start()
+    for m in (500, 1000, 2000, 3000, 4000, 5000):
+        s = m // 20
+        l = min(2 * s + 1, m)
+        qs = pkg.QSketch(m, l, s, l, emb="gaussian", prec="bf16x3", seed=1)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(m)
+        qs.get("Y").copy_(torch.randn((4, m, s), generator=gen, device=dev))
+        row = {"m": m, "s": s}
+        for kind in kinds:
+            for _ in range(args.warmup):
+                qs.rangefinder(kind, 3)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                qs.rangefinder(kind, 3)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[kind + "_ms"] = e0.elapsed_time(e1) / args.steps
+        row["device_status"] = int(qs.device_status())
+        curve.append(row)
+        qs.close()
+    clocks = sampler.stop()
+    last = curve[-1]
+    out = {"metric": "rangefinder time vs m (m = 20 s): pseudo-QR with 3 corrections",
+           "value": last["pseudo_qr_ms"], "unit": "ms", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": last["pseudo_qr_ms"], "higher_is_better": False,
+           "scaling": "none", "vs_baseline": None, "dtype": "df64", "data": "synthetic",
+           "config": {"workload": "rangefinders on quaternion Gaussian Y, m in 500..5000, s = m/20",
+                      "l2": "Y is at most 5000 x 250 quaternion (L2-resident): small-matrix latency"},
+           "curve": curve, "clocks": clocks}
+    print(json.dumps(out), flush=True)
+
+
 def batch_reference(args):
     """The oracle's sketch (Sec. 4.1, FP64 on the host cores) on a bounded sample of the c4
     batch: its first two matrices (same sizes and spectra as the GPU run's; the host's torch
@@ -512,6 +566,11 @@ def cpu_sample(w, rows):
         P = WL.make_c5("cpu", grid=32).double().numpy()
         A = np.concatenate([np.zeros((1,) + P.shape[1:]), P])
         return A, f"32^3-grid c5 snapshots ({A.shape[1]} rows x {A.shape[2]} cols, pure)"
+    if w["name"] == "lorenz":
+        import oracle as O
+        u0 = WL.lorenz_initial_states(w["n"], seed=w["seed"], radius=w["radius"])
+        A = O.lorenz4d_snapshots(u0, rows, w["dt"], w["a"], w["b"], w["c"])
+        return A, f"first {rows} time instances x {w['n']} trajectories (the oracle's own RK4)"
     A = WL.make_decay(w["m"], w["n"], seed=w["seed"], rank_cap=w.get("rank_cap", 1024),
                       dtype=np.float64)[:, :rows]
     return A, f"first {A.shape[1]} rows x {A.shape[2]} cols of {w['name']}"
@@ -546,6 +605,9 @@ WORKLOAD_TEXT = {
           "+ U(0,0.02)), k=100, s=201, l=403, Rademacher Omega/Psi (exact in BF16)",
     "c5": "pure-quaternion flow snapshots A 2097152x256 FP32 (128^3 grid x 256 steps, 32 divergence-free "
           "Taylor-Green-type modes + 1e-4 noise), k=20, s=41, l=83, Gaussian Omega/Psi",
+    "lorenz": "4D Lorenz-type system snapshots A 20000x10000 FP32 (x + yi + zj + wk after each of 20000 "
+              "RK4 steps of 1e-3 from 10000 states on the radius-20 sphere, a=15, b=2, c=28), k=100, "
+              "s=201, l=403, Gaussian Omega/Psi",
 }
 
 
@@ -557,7 +619,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "bf16x3"])
     ap.add_argument("--workload", default="c2",
-                    help="c2 (default: the one-pass step) or c4 (the batched sketch, one GPU)")
+                    help="c2 (default: the one-pass step), c1, c3, c5, lorenz (the same step on those "
+                         "workloads), c4 (the batched sketch), rf_curve (rangefinder time vs m)")
     ap.add_argument("--rangefinder", default="pseudo_qr")
     ap.add_argument("--rf-prec", default="df64", choices=["df64", "fp64", "mixed"],
                     help="arithmetic of the rangefinder, core and truncation stages")
@@ -570,7 +633,7 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.cpu_rows is None:
-        args.cpu_rows = {"c3": 256}.get(args.workload, 4096)
+        args.cpu_rows = {"c3": 256, "lorenz": 1024}.get(args.workload, 4096)
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -578,6 +641,13 @@ def main():
     if args.workload == "c4":
         if rank == 0:      # the batch workload runs on one GPU / on the host cores
             run_batch(args) if args.impl == "ours" else batch_reference(args)
+        return
+    if args.workload == "rf_curve":
+        if rank == 0 and args.impl == "ours":
+            run_rf_curve(args)
+        elif rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the rangefinder timing curve "
+                              "has no oracle arm (the oracle's timing is in the c2 line)"}))
         return
     w = workload(args.workload)
     metric = "one-pass quaternion approx: A GB/s & TFLOPS, split-BF16 vs FP32 at equal error"

@@ -305,6 +305,20 @@ QS_API qs_status qs_reconstruct_error_static(int64_t m, int64_t n, int64_t s, in
                                              const void* const X_planes[4], int64_t ldx,
                                              double* rel_err_dev, void* stream);
 
+/* Input generator of the paper's hyperchaotic-system example (Sec. 5; the 4D Lorenz-type system
+ *   dx/dt = a (y - x), dy/dt = c x - y - x z + w, dz/dt = -b z + x y, dw/dt = (c - 1) y + w - x^3 / b,
+ * with a = 15, b = 2, c = 28 there).  Integrates `cols` trajectories from the initial states
+ * u0 (device, FP64, 4 x cols row-major: the x, y, z, w rows) by the classical fourth-order
+ * Runge-Kutta scheme with fixed step dt (the paper's step is not stated), one trajectory per
+ * GPU thread in FP64, and writes the state after step t + 1 of trajectory j as the
+ * quaternion entry (t, j) = x + y i + z j + w k of a steps x cols matrix: out[0..3] are its
+ * planes (device, row-major, leading dimension ldo >= cols), FP64 (QS_DT_F64) or FP32
+ * (QS_DT_F32, rounded from the FP64 state).  Enqueued on `stream`; QS_ERR_INVALID for bad
+ * arguments, QS_ERR_CUDA when the launch fails. */
+QS_API qs_status qs_lorenz4d(const double* u0, int64_t cols, int64_t steps, double dt, double a,
+                             double b, double c, void* const out[4], int32_t dtype, int64_t ldo,
+                             void* stream);
+
 /* Device pointer, leading dimension (elements), plane stride (elements) and element type
  * of an object in the workspace.  Views stay valid until qsketch_destroy. */
 QS_API qs_status qsketch_get(qs_handle_t h, int32_t which, void** dev_ptr, int64_t* ld,

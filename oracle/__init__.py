@@ -25,5 +25,6 @@ from .philox import (philox4x32_10, draw_embedding, draw_uniform_f, EMB_GAUSSIAN
 from .method import (sketch, thin_qr_complex, pseudo_qr, correction_step, epsilon_rule,
                      pseudo_svd, classify_pairs, qls_solve, qb_core, rel_error,
                      qmgs2, qsvd_dense, onepass, truncate, truncated_core)
+from .lorenz import lorenz4d_rhs, rk4_step, lorenz4d_snapshots
 
 __all__ = [n for n in dir() if not n.startswith("_")]

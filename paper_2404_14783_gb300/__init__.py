@@ -11,8 +11,9 @@ package is its thin Python binding.  See ``QSketch`` for the calls:
 """
 from .qsketch import (QSketch, QSError, QSConfig, load_library, ABI_SYMBOLS, LIB_PATH,
                       PRECISIONS, EMBEDDINGS, RANGEFINDERS, launch_count,
-                      reconstruct_error_static, update_batched, tune_batched, RF_PRECISIONS)
+                      reconstruct_error_static, update_batched, tune_batched, RF_PRECISIONS,
+                      lorenz4d)
 
 __all__ = ["QSketch", "QSError", "QSConfig", "load_library", "ABI_SYMBOLS", "LIB_PATH",
            "PRECISIONS", "EMBEDDINGS", "RANGEFINDERS", "launch_count", "reconstruct_error_static",
-           "update_batched", "tune_batched", "RF_PRECISIONS"]
+           "update_batched", "tune_batched", "RF_PRECISIONS", "lorenz4d"]

@@ -36,7 +36,7 @@ ABI_SYMBOLS = ("qsketch_workspace_bytes", "qsketch_create", "qsketch_update", "q
                "qonepass_core", "qreconstruct_error", "qsketch_get", "qs_last_device_error",
                "qsketch_destroy", "qs_status_string", "qs_launch_count", "qs_version",
                "qs_reconstruct_error_static", "qsketch_update_batched", "qtruncate",
-               "qsketch_update_host", "qsketch_tune_batched")
+               "qsketch_update_host", "qsketch_tune_batched", "qs_lorenz4d")
 
 
 class QSConfig(ctypes.Structure):
@@ -83,12 +83,13 @@ def load_library(path=LIB_PATH):
                                                 planes, I64, VP, VP]
     lib.qsketch_update_batched.argtypes = [I32, P(VP), P(VP), P(I64), VP]
     lib.qsketch_tune_batched.argtypes = [I32, P(VP), P(VP), P(I64), I32, VP]
+    lib.qs_lorenz4d.argtypes = [VP, I64, I64, D, D, D, D, planes, I32, I64, VP]
     lib.qtruncate.argtypes = [VP, I64, VP]
     lib.qsketch_update_host.argtypes = [VP, planes, I64, I64, VP, ctypes.c_size_t, VP, D, D, VP]
     for name in ("qsketch_create", "qsketch_update", "qrangefinder", "qonepass_core",
                  "qreconstruct_error", "qsketch_get", "qs_last_device_error", "qsketch_destroy",
                  "qs_reconstruct_error_static", "qsketch_update_batched", "qtruncate",
-                 "qsketch_update_host", "qsketch_tune_batched"):
+                 "qsketch_update_host", "qsketch_tune_batched", "qs_lorenz4d"):
         getattr(lib, name).restype = I32
     _lib = lib
     return lib
@@ -168,6 +169,25 @@ def tune_batched(sketches, matrices, reps=3, stream=None):
     count, hs, ptrs, lds = _batch_args(sketches, matrices)
     return _check(lib.qsketch_tune_batched(count, hs, ptrs, lds, int(reps), _stream_ptr(stream)),
                   "qsketch_tune_batched")
+
+
+def lorenz4d(u0, steps, dt, a=15.0, b=2.0, c=28.0, dtype=torch.float32, stream=None):
+    """qs_lorenz4d: RK4 trajectories of the 4D Lorenz-type system from the initial states u0
+    (a (4, cols) CUDA float64 tensor); returns the (4, steps, cols) quaternion matrix of the
+    states after each step (leading dimension padded to a multiple of 4), viewed as
+    (4, steps, cols)."""
+    lib = load_library()
+    if not (u0.is_cuda and u0.dtype == torch.float64 and u0.dim() == 2 and u0.shape[0] == 4):
+        raise ValueError("u0 must be a (4, cols) CUDA float64 tensor")
+    u0 = u0.contiguous()
+    cols = int(u0.shape[1])
+    ldo = (cols + 3) // 4 * 4
+    out = torch.empty((4, steps, ldo), dtype=dtype, device=u0.device)
+    ptrs = (ctypes.c_void_p * 4)(*[out[p].data_ptr() for p in range(4)])
+    _check(lib.qs_lorenz4d(ctypes.c_void_p(u0.data_ptr()), cols, int(steps), float(dt), float(a),
+                           float(b), float(c), ptrs, QS_DT_F64 if dtype == torch.float64 else QS_DT_F32,
+                           ldo, _stream_ptr(stream)), "qs_lorenz4d")
+    return out[:, :, :cols]
 
 
 def update_batched(sketches, matrices, stream=None):

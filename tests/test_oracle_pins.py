@@ -536,3 +536,25 @@ def test_philox_known_answers():
         w = [int(x, 16) for x in r]
         out = O.philox4x32_10(*(np.array([v], dtype=np.uint64) for v in w[:4]), w[4], w[5])
         assert [int(np.asarray(x).ravel()[0]) for x in out] == w[6:10]
+
+
+# ---------------------------------------------------------------- the Lorenz-type system
+def test_lorenz_rhs_at_a_hand_computed_point():
+    """The right-hand side of the paper's 4D system at (1, 2, 3, 4), a = 15, b = 2, c = 28:
+    (15 (2 - 1), 28 - 2 - 3 + 4, -6 + 2, 27 * 2 + 4 - 1/2) = (15, 27, -4, 57.5)."""
+    v = O.lorenz4d_rhs(np.array([1.0, 2.0, 3.0, 4.0]))
+    np.testing.assert_array_equal(v, [15.0, 27.0, -4.0, 57.5])
+
+
+def test_rk4_order_and_exact_linear_step():
+    """The RK4 step is exact to fifth order on u' = lam u (the truncated exponential series),
+    and on the Lorenz system halving the step divides the error at a fixed time by ~16."""
+    h, lam = 0.1, -1.3
+    z = lam * h
+    step = O.rk4_step(lambda u: lam * u, np.array([1.0]), h)[0]
+    assert abs(step - (1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24)) < 1e-15
+    u0 = WL.lorenz_initial_states(3, seed=1)
+    T = 0.05
+    ref = O.lorenz4d_snapshots(u0, 1600, T / 1600)[:, -1]
+    e = [np.abs(O.lorenz4d_snapshots(u0, n, T / n)[:, -1] - ref).max() for n in (50, 100)]
+    assert 12.0 < e[0] / e[1] < 20.0, e

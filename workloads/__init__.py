@@ -39,6 +39,11 @@ that are not available):
       keeps the field divergence free), times a time-periodic amplitude
       alpha_t sin(2 pi tau / T_t + phi_t), plus 1e-4 Gaussian noise; k=20, s=41, l=83;
       Gaussian embeddings (make_c5, built on the device).
+  lorenz  20000 x 10000 full quaternion, FP32: the states x + y i + z j + w k of the paper's
+      4D Lorenz-type system (Sec. 5; a = 15, b = 2, c = 28) along 10000 trajectories from
+      initial states on the sphere of radius 20, after each of 20000 fourth-order
+      Runge-Kutta steps of dt = 1e-3 (t in (0, 20]; the paper's solver steps are not stated),
+      integrated on the GPU (qs_lorenz4d) in FP64; k=100, s=201, l=403; Gaussian embeddings.
 Random quaternion-orthonormal factors are built as U = D Q W: Q real orthonormal (QR of a
 real Gaussian), W the unitary polar factor of an R x R quaternion Gaussian (from the
 eigendecomposition of its Hermitian complex form), D a diagonal of random unit
@@ -60,6 +65,9 @@ WORKLOADS = {
     # image-like pure quaternion (the colour-image experiment's shape), Rademacher embeddings
     "c3": dict(m=31365, n=27125, k=100, s=201, l=403, precision="bf16x3", emb="rademacher",
                seed=0, pure=True, modes=64),
+    # hyperchaotic-system snapshots: 20000 time instances x 10000 initial states (RK4, dt 1e-3)
+    "lorenz": dict(m=20000, n=10000, k=100, s=201, l=403, precision="bf16x3", emb="gaussian",
+                   seed=0, dt=1e-3, a=15.0, b=2.0, c=28.0, radius=20.0),
     # tall flow-snapshot pure quaternion (128^3 grid x 256 time steps), Gaussian embeddings
     "c5": dict(m=128 ** 3, n=256, k=20, s=41, l=83, precision="bf16x3", emb="gaussian", seed=0,
                pure=True, grid=128, modes=32),
@@ -339,3 +347,11 @@ def make_c5(device, grid=None, steps=None, seed=None, modes=None):
         torch.matmul(U[ch], ampf, out=A[ch])
         A[ch].add_(torch.randn((m, steps), generator=gen, device=device, dtype=torch.float32).mul_(1e-4))
     return A
+
+
+def lorenz_initial_states(cols, seed=0, radius=20.0):
+    """(4, cols) FP64 initial states (x, y, z, w) drawn uniformly on the sphere of the given
+    radius (normalised Gaussian vectors), as in the paper's hyperchaotic-system example."""
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal((4, cols))
+    return radius * u / np.linalg.norm(u, axis=0, keepdims=True)
