@@ -93,6 +93,7 @@ struct TcBatch {
   int tile_start[MAXB + 1];
   int count;
   static constexpr bool kTable = false;
+  using PT = const TcParams&;   // parameters used in place (constant bank)
   __device__ const TcParams& P(int i) const { return prm[i]; }
   __device__ const TcMaps& M(int i) const { return maps[i]; }
   __device__ int ts(int i) const { return tile_start[i]; }
@@ -121,6 +122,9 @@ struct TcTable {
   int tile_start[kMaxTable + 1];
   int count;
   static constexpr bool kTable = true;
+  // parameters copied once per tile (a reference into global memory would be re-read after
+  // every store the compiler cannot prove apart from it)
+  using PT = const TcParams;
   __device__ const TcParams& P(int i) const { return item[i]->prm; }
   __device__ const TcMaps& M(int i) const { return item[i]->maps; }
   __device__ int ts(int i) const { return tile_start[i]; }
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_sketch_kernel(const __grid_
       int last_item = -1;
       for (int t = blockIdx.x; t < ntiles && !stop && !sh->abort; t += gridDim.x, ++t_local) {
         const int it = item_of(t);
-        const TcParams& p = bt.P(it);
+        typename Src::PT p = bt.P(it);
         const TcMaps& mp = bt.M(it);
         cur_status = p.status;
         if constexpr (Src::kTable) {
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_sketch_kernel(const __grid_
       const uint64_t dA_y = sdesc(a_base, 16, 2048);      // A tile as the Y products' A operand
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok && !sh->abort; t += gridDim.x, ++t_local) {
-        const TcParams& p = bt.P(item_of(t));
+        typename Src::PT p = bt.P(item_of(t));
         cur_status = p.status;
         // products: hi*hi, then A_lo * (test hi) when nprod >= 2, (test lo) * A_hi when nprod == 3
         const bool alo = p.nprod >= 2, three = p.nprod == 3, pure = p.pure != 0;
@@ -384,7 +388,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_sketch_kernel(const __grid_
     int t_local = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok && !sh->abort; t += gridDim.x, ++t_local) {
-      const TcParams& p = bt.P(item_of(t));
+      typename Src::PT p = bt.P(item_of(t));
       if (!wait_bar(&sh->a_full, t_local & 1, sh, p.status)) { ok = false; break; }
       for (int gi = cw; gi < 64; gi += 4) {
         const int plane = gi >> 4, grp = gi & 15;
@@ -424,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_sketch_kernel(const __grid_
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok && !sh->abort; t += gridDim.x) {
       const int it = item_of(t);
-      const TcParams& p = bt.P(it);
+      typename Src::PT p = bt.P(it);
       const int lt = t - bt.ts(it), ti = lt / p.tiles_n, tj = lt % p.tiles_n;
       const int nwaves = nwaves_of(p);
       const bool wvec = ((p.col0 & 3) == 0) && ((p.ldw & 3) == 0);
