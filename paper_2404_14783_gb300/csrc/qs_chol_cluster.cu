@@ -38,6 +38,7 @@ namespace {
 namespace cg = cooperative_groups;
 
 constexpr int kCL = 8;     // CTAs per cluster (portable cluster size)
+constexpr int kMaxN = 128; // s at most
 constexpr int kNT = 512;   // threads per CTA
 
 struct CholClArgs {
@@ -129,7 +130,10 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kNT, 1)
   const QS<R, C> Lf = QS<R, C>::make(base, lf_cap);   // every CTA's copy of L, packed by columns
   const QS<R, C> Wp = QS<R, C>::make(base + NC * lf_cap, pool_cap);                 // own columns of G -> L
   const QS<R, C> Xp = QS<R, C>::make(base + NC * (lf_cap + pool_cap), pool_cap);    // own columns of L^{-1}
-  int* flag = reinterpret_cast<int*>(base + NC * (lf_cap + 2 * pool_cap));         // per column
+  // pivot-failure flag of each column, in static shared memory: kept apart from the dynamic
+  // region (a flag array placed after the working pools was found overwritten by stale data
+  // when the previous launch had used that memory differently)
+  __shared__ int flag[kMaxN];
   __shared__ double red[32];
 
   const bool stopped = (a.status[0] & kDevStopCorr) != 0;
@@ -390,7 +394,7 @@ size_t smem_cl(int n) {
   constexpr int NC = C ? 2 : 4;
   const int lf_cap = lf_capacity(n, NC);
   const int pool_cap = std::max(pool_off(n, 0, own_cols(n, 0)), 1);
-  return sizeof(R) * (size_t)NC * (lf_cap + 2 * pool_cap) + sizeof(int) * (size_t)n + 16;
+  return sizeof(R) * (size_t)NC * (lf_cap + 2 * pool_cap) + 16;
 }
 
 template <typename R, bool C>
@@ -410,7 +414,7 @@ constexpr size_t kMaxSmem = 225 * 1024;
 
 int qchol_cluster_max_n(int complex_only) {
   int n = 1;
-  while (n + 1 <= 128 && (complex_only ? smem_cl<double, true>(n + 1) : smem_cl<double, false>(n + 1)) <= kMaxSmem)
+  while (n + 1 <= kMaxN && (complex_only ? smem_cl<double, true>(n + 1) : smem_cl<double, false>(n + 1)) <= kMaxSmem)
     ++n;
   return n;
 }
