@@ -9,18 +9,19 @@
 //
 //   1. right-looking Cholesky, columns dealt round-robin to the 8 CTAs of a cluster (CTA c
 //      owns columns k = c (mod 8) in its working pool).  The owner of column j takes the
-//      pivot sqrt(d_j) (every thread forms it, so no CTA barrier is needed) and writes the
-//      scaled column into its own copy of L (packed by columns: one contiguous range); after
-//      one cluster barrier per column the other CTAs pull it into their copies through
-//      distributed shared memory, and every CTA applies L_ik -= L_ij conj(L_kj) to the
-//      columns it owns.  In the same sweep each CTA forms its own columns of L^{-1} by the
-//      forward substitution L X = I in right-looking form.  On breakdown: one retry with the
+//      pivot sqrt(d_j) (every thread forms it, so no CTA barrier is needed), scales the
+//      column and writes it, through distributed shared memory, into every CTA's copy of L
+//      (packed by columns, so a column is one contiguous range; the stores are spread over
+//      all threads of the CTA); one cluster barrier per column; every CTA then applies
+//      L_ik -= L_ij conj(L_kj) to the columns it owns.  On breakdown: one retry with the
 //      shifted Cholesky-QR shift 11 (rows s + s (s + 1)) u trace(G) (Fukaya et al. 2020);
-//   2. with a power slot: lambda_max(G) from three iterates z <- L L* z, and rho =
+//   2. L^{-1}: column k solves L x = e_k by forward substitution (one warp per column, the
+//      columns of every CTA's own set, from its full copy of L);
+//   3. with a power slot: lambda_max(G) from three iterates z <- L L* z, and rho =
 //      x* G^{-1} x = ||L^{-1} x||^2 on three iterates x <- G^{-1} x / |G^{-1} x| from
-//      (c, 0, -c, 0), run in lockstep; eps = 1 / sqrt(rho), kappa(H) = sqrt(lambda_max rho).
-//      The matrix-vector products run on the owned columns; partial vectors meet in every
-//      CTA's shared memory and are added in a fixed order, so every CTA holds the same bits.
+//      (c, 0, -c, 0); eps = 1 / sqrt(rho), kappa(H) = sqrt(lambda_max rho).  The matrix-vector
+//      products run on the owned columns; partial vectors meet in every CTA's shared memory
+//      and are added in a fixed order, so every CTA holds the same bits.
 //
 // Arithmetic R: df64 (double-float) or double.  The trip counts of all cluster barriers are
 // the same in every CTA (failure flags are published before the barrier that precedes their
@@ -67,13 +68,6 @@ __host__ __device__ __forceinline__ int pool_off(int n, int c, int q) {
 __host__ __device__ __forceinline__ int own_cols(int n, int c) {
   return c < n ? (n - c + kCL - 1) / kCL : 0;
 }
-// Per-component capacity of the L region: the packed lower triangle, or the exchange space
-// of the power iterates (2 kCL partial vectors and 6 vectors of n quaternions).
-__host__ __device__ __forceinline__ int lf_capacity(int n, int nc) {
-  const int tri = nc * (n * (n + 1) / 2), ex = (2 * kCL + 6) * 4 * n;
-  return (tri > ex ? tri : ex) / nc;
-}
-
 // Start of column j in a lower triangle packed by columns (column j holds rows j..n-1).
 __device__ __forceinline__ int cstart(int n, int j) { return j * n - j * (j - 1) / 2; }
 
@@ -124,16 +118,12 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kNT, 1)
   const int c = (int)cluster.block_rank();
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   const int nq = own_cols(n, c), npool = pool_off(n, c, nq);
-  const int lf_cap = lf_capacity(n, NC);
+  const int lf_cap = std::max(NC * ntri, (kCL + 3) * 4 * n) / NC;   // per component
   const int pool_cap = std::max(pool_off(n, 0, own_cols(n, 0)), 1);
   R* base = reinterpret_cast<R*>(smem_raw);
   const QS<R, C> Lf = QS<R, C>::make(base, lf_cap);   // every CTA's copy of L, packed by columns
-  const QS<R, C> Wp = QS<R, C>::make(base + NC * lf_cap, pool_cap);                 // own columns of G -> L
-  const QS<R, C> Xp = QS<R, C>::make(base + NC * (lf_cap + pool_cap), pool_cap);    // own columns of L^{-1}
-  // pivot-failure flag of each column, in static shared memory: kept apart from the dynamic
-  // region (a flag array placed after the working pools was found overwritten by stale data
-  // when the previous launch had used that memory differently)
-  __shared__ int flag[kMaxN];
+  const QS<R, C> Wp = QS<R, C>::make(base + NC * lf_cap, pool_cap);  // own columns (rows k..n-1)
+  __shared__ int flag[kMaxN];   // pivot-failure flag of each column (static shared memory)
   __shared__ double red[32];
 
   const bool stopped = (a.status[0] & kDevStopCorr) != 0;
@@ -146,7 +136,6 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kNT, 1)
     M[2 * a.psl + (int64_t)i * a.ldl + k] = to_d(v.y);
     M[3 * a.psl + (int64_t)i * a.ldl + k] = to_d(v.z);
   };
-  const QT<R> zero{R(0), R(0), R(0), R(0)};
   auto give_up = [&]() {   // L = L^{-1} = I on the own columns; the caller skips the result
     for (int e = tid; e < nq * n; e += nt) {
       const int q = e / n, i = e % n, k = c + kCL * q;
@@ -164,13 +153,7 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kNT, 1)
     return;
   }
 
-  // ------------------------------------------------------------------ 1. Cholesky and L^{-1}
-  // Column j: its owner takes the pivot, scales the column into its own copy of L; after the
-  // cluster barrier the other CTAs pull it into theirs (distributed shared memory loads).
-  // Every CTA then updates its own columns of G, and advances its own columns of X = L^{-1}
-  // by the forward substitution L X = I in right-looking form: X_jk = (delta_jk - X_jk) /
-  // L_jj, then X_ik += L_ij X_jk for i > j (X_ik holds sum_{m<j} L_im X_mk until row i is
-  // final).
+  // ------------------------------------------------------------------ 1. Cholesky
   double shift = 0.0;
   bool fail = false;
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -182,57 +165,39 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kNT, 1)
       if (!C) { y = gget(i, k, 2); z = gget(i, k, 3); }
       if (i == k) { x = y = z = 0.0; w += shift; }
       Wp.set(e, QT<R>{from_d<R>(w), from_d<R>(x), from_d<R>(y), from_d<R>(z)});
-      Xp.set(e, zero);
     }
     __syncthreads();
     fail = false;
     for (int j = 0; j < n; ++j) {
-      const int o = j % kCL, len = n - j, cs = cstart(n, j);
-      if (o == c) {   // owner: pivot (every thread forms it), scale, publish in the own copy
-        const int off = pool_off(n, c, j / kCL);
-        const R d = Wp[off].w;
+      if (j % kCL == c) {   // owner: pivot, scale, publish column j
+        const int off = pool_off(n, c, j / kCL), len = n - j, cs = cstart(n, j);
+        const R d = Wp[off].w;   // every thread forms the same pivot
         const double dd = to_d(d);
         const int f = (!(dd > 0.0) || !isfinite(dd)) ? 1 : 0;
         if (!f) {
           const R r = sqrt_(d), ir = rcp_(r);
-          for (int ii = tid; ii < len; ii += nt)
-            Lf.set(cs + ii, ii == 0 ? QT<R>{r, R(0), R(0), R(0)} : qscale<R, C>(Wp[off + ii], ir));
+          // (target CTA, row) pairs spread over the threads; consecutive threads write
+          // consecutive entries of one target
+          for (int p = tid; p < kCL * len; p += nt) {
+            const int tr = p / len, ii = p - tr * len;
+            const QT<R> v = ii == 0 ? QT<R>{r, R(0), R(0), R(0)} : qscale<R, C>(Wp[off + ii], ir);
+            remote<R, C>(cluster, Lf, tr).set(cs + ii, v);
+          }
         }
-        if (tid == 0) flag[j] = f;
+        if (tid < kCL) cluster.map_shared_rank(flag, tid)[j] = f;
       }
       cluster.sync();
-      const int f = *cluster.map_shared_rank(flag, o);
-      if (f) {
+      if (flag[j]) {
         fail = true;
         break;
       }
-      if (o != c) {   // pull column j from its owner
-        const QS<R, C> src = remote<R, C>(cluster, Lf, o);
-        for (int ii = tid; ii < len; ii += nt) Lf.set(cs + ii, src[cs + ii]);
-      }
-      __syncthreads();
-      // row j of the own columns of X: X_jk = (delta_jk - X_jk) / L_jj, own k <= j
-      const int qx = j < c ? 0 : (j - c) / kCL + 1;   // own columns k <= j: q < qx
-      if (tid < qx) {
-        const int k = c + kCL * tid, e = pool_off(n, c, tid) + j - k;
-        const R ir = rcp_(Lf[cs].w);
-        const QT<R> v = Xp[e];
-        Xp.set(e, qscale<R, C>(QT<R>{(j == k ? R(1) : R(0)) - v.w, -v.x, -v.y, -v.z}, ir));
-      }
-      __syncthreads();
-      // own columns k > j of G: L_ik -= L_ij conj(L_kj); own columns k <= j of X: rows i > j
-      const int e0 = pool_off(n, c, qx);
-      for (int e = e0 + tid; e < npool; e += nt) {
+      // trailing update of the own columns k > j with column j
+      const int q0 = j < c ? 0 : (j - c) / kCL + 1, cs = cstart(n, j);
+      for (int e = pool_off(n, c, q0) + tid; e < npool; e += nt) {
         int q, i;
         pool_rc(n, c, nq, e, q, i);
         const int k = c + kCL * q;
         Wp.set(e, qsub_mul_conj<R, C>(Wp[e], Lf[cs + i - j], Lf[cs + k - j]));
-      }
-      const int nx = qx * (len - 1);   // (row i > j, own column q < qx) pairs
-      for (int e = tid; e < nx; e += nt) {
-        const int q = e / (len - 1), i = j + 1 + e % (len - 1), k = c + kCL * q;
-        const int off = pool_off(n, c, q);
-        Xp.set(off + i - k, qmac<R, C>(Xp[off + i - k], Lf[cs + i - j], Xp[off + j - k]));
       }
       __syncthreads();
     }
@@ -257,112 +222,164 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kNT, 1)
     give_up();
     return;
   }
-  // L and L^{-1} to global memory (own columns, zero above the diagonal); the own columns of
-  // L also into the working pool (the power iterates use them once the copy of L becomes
-  // exchange space)
+  // L to global memory (own columns, zero above the diagonal), and into the working pool
+  // (the power iterates use the own columns after the copy of L becomes exchange space)
   for (int e = tid; e < nq * n; e += nt) {
     const int q = e / n, i = e % n, k = c + kCL * q;
-    const QT<R> v = i < k ? zero : Lf[cstart(n, k) + i - k];
+    const QT<R> v = i < k ? QT<R>{R(0), R(0), R(0), R(0)} : Lf[cstart(n, k) + i - k];
     put(a.Lg, i, k, v);
-    put(a.Li, i, k, i < k ? zero : Xp[pool_off(n, c, q) + i - k]);
     if (i >= k) Wp.set(pool_off(n, c, q) + i - k, v);
+  }
+
+  // ------------------------------------------------------------------ 2. L^{-1}, own columns
+  // Right-looking forward substitution: lane t owns rows k + t + 32 u and their running sums
+  // acc = sum_{m<i} L_rm x_m; at step i the owner of row i forms x_i = (delta_ik - acc_i) / L_ii
+  // and every lane adds L_ri x_i to its rows r > i.  n <= 128.
+  for (int q = warp; q < nq; q += nw) {
+    const int k = c + kCL * q;
+    QT<R> acc[4], xs[4];
+    R invd[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc[u] = QT<R>{R(0), R(0), R(0), R(0)};
+      xs[u] = acc[u];
+      const int r = k + lane + 32 * u;
+      invd[u] = r < n ? rcp_(Lf[cstart(n, r)].w) : R(0);
+    }
+    for (int i = k; i < n; ++i) {
+      const int li = i - k, owner = li & 31, uo = li >> 5;   // warp-uniform
+      QT<R> av = acc[0];
+      R id = invd[0];
+      if (uo == 1) { av = acc[1]; id = invd[1]; }
+      if (uo == 2) { av = acc[2]; id = invd[2]; }
+      if (uo == 3) { av = acc[3]; id = invd[3]; }
+      const R one = (i == k) ? R(1) : R(0);
+      QT<R> xi = qscale<R, C>(QT<R>{one - av.w, -av.x, -av.y, -av.z}, id);   // valid in the owner
+      xi.w = nrm_(shfl_r(xi.w, owner));
+      xi.x = nrm_(shfl_r(xi.x, owner));
+      if (!C) {
+        xi.y = nrm_(shfl_r(xi.y, owner));
+        xi.z = nrm_(shfl_r(xi.z, owner));
+      }
+      const int cs = cstart(n, i) - i, ulast = (n - 1 - k) >> 5;   // rows r: entry cs + r
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (u < uo || u > ulast) continue;   // warp-uniform: no live row in this slot
+        const int lr = lane + 32 * u, r = k + lr;
+        if (lr == li) xs[u] = xi;
+        if (lr > li && r < n) acc[u] = qmac<R, C>(acc[u], Lf[cs + r], xi);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = k + lane + 32 * u;
+      if (r < n) put(a.Li, r, k, xs[u]);
+    }
+    for (int r = lane; r < k; r += 32) put(a.Li, r, k, QT<R>{R(0), R(0), R(0), R(0)});
   }
   if (a.power_slot < 0 || C) {
     if (c == 0 && tid == 0) a.scalars[kScCholOk] = 1.0;
-    cluster.sync();   // the last column's owner stays until every CTA has pulled it
-    return;
+    return;   // no remote access follows the last cluster barrier
   }
-  __syncthreads();
+  __syncthreads();   // own columns of L^{-1} in global memory, visible to this CTA
   cluster.sync();    // no CTA still reads its copy of L: it becomes exchange space
 
-  // ------------------------------------------------------------------ 2. power iterates
-  // Both run in lockstep, two cluster barriers per iterate:
-  //   lambda_max(G): z <- L (L* z) / |.|, lambda = |L* z|^2 at the last iterate;
-  //   rho: x <- G^{-1} x / |.|, G^{-1} = L^{-*} L^{-1}, rho = |L^{-1} x|^2 at the last iterate.
-  // Exchange space: two sets of kCL partial vectors, then z, t, x, y, pz, px (n each).
-  auto vec = [&](int slot_) { return QS<R, false>::make(base + slot_ * 4 * n, n); };
-  const QS<R, false> z = vec(2 * kCL), t = vec(2 * kCL + 1), x = vec(2 * kCL + 2), y = vec(2 * kCL + 3);
-  const QS<R, false> pz = vec(2 * kCL + 4), px = vec(2 * kCL + 5);
-  const QS<R, false> Lw = QS<R, false>::make(base + NC * lf_cap, pool_cap);                // own L
-  const QS<R, false> Xw = QS<R, false>::make(base + NC * (lf_cap + pool_cap), pool_cap);   // own L^{-1}
+  // ------------------------------------------------------------------ 3. power iterates
+  // exchange space in the L region: kCL partial vectors, then vectors v, t, pv (n each)
+  const QS<R, false> v = QS<R, false>::make(base + kCL * 4 * n, n);
+  const QS<R, false> t = QS<R, false>::make(base + (kCL + 1) * 4 * n, n);
+  const QS<R, false> pv = QS<R, false>::make(base + (kCL + 2) * 4 * n, n);
+  auto slot = [&](int r) { return QS<R, false>::make(base + r * 4 * n, n); };
+  const QS<R, false> W4 = QS<R, false>::make(base + NC * lf_cap, pool_cap);   // own columns
   const double c0 = 1.0 / sqrt(2.0 * n);
   const QT<R> start{from_d<R>(c0), R(0), from_d<R>(-c0), R(0)};
-  // out_k = sum_{i >= k} conj(M_ik) in_i for the own columns k (one warp per column), into
-  // `dst` of every CTA
-  auto apply_conj = [&](const QS<R, false>& M, const QS<R, false>& in, const QS<R, false>& dst) {
+  // out_k = sum_{i >= k} conj(M_ik) in_i for the own columns k (one warp per column), written
+  // into `dst` of every CTA
+  auto apply_conj = [&](const QS<R, false>& in, const QS<R, false>& dst) {
     for (int q = warp; q < nq; q += nw) {
       const int k = c + kCL * q, off = pool_off(n, c, q);
-      QT<R> sacc = zero;
-      for (int i = k + lane; i < n; i += 32) sacc = qt_mac_conj_a(sacc, M[off + i - k], in[i]);
-      sacc = wsum4(sacc);
-      if (lane < kCL) remote<R, false>(cluster, dst, lane).set(k, sacc);
+      QT<R> s{R(0), R(0), R(0), R(0)};
+      for (int i = k + lane; i < n; i += 32) s = qt_mac_conj_a(s, W4[off + i - k], in[i]);
+      s = wsum4(s);
+      if (lane < kCL) remote<R, false>(cluster, dst, lane).set(k, s);
     }
   };
-  // partial out_i = sum_{own k <= i} M_ik in_k, computed into `part`
-  auto apply_part = [&](const QS<R, false>& M, const QS<R, false>& in, const QS<R, false>& part) {
+  // partial out_i = sum_{own k <= i} M_ik in_k into slot c of every CTA
+  auto apply_part = [&](const QS<R, false>& in) {
     for (int i = tid; i < n; i += nt) {
-      QT<R> sacc = zero;
+      QT<R> s{R(0), R(0), R(0), R(0)};
       for (int q = 0; q < nq; ++q) {
         const int k = c + kCL * q;
         if (k > i) break;
-        sacc = qt_mac(sacc, M[pool_off(n, c, q) + i - k], in[k]);
+        s = qt_mac(s, W4[pool_off(n, c, q) + i - k], in[k]);
       }
-      part.set(i, sacc);
+      pv.set(i, s);
     }
-  };
-  // the partial vector of this CTA into slot `set * kCL + c` of every CTA
-  auto push_part = [&](const QS<R, false>& part, int set) {
+    __syncthreads();
     for (int p = tid; p < kCL * n; p += nt) {
       const int tr = p / n, i = p - tr * n;
-      remote<R, false>(cluster, vec(set * kCL + c), tr).set(i, part[i]);
+      remote<R, false>(cluster, slot(c), tr).set(i, pv[i]);
     }
   };
-  // out = sum of the kCL partial vectors of `set` (fixed order); returns |out|^2
-  auto gather = [&](int set, const QS<R, false>& out) {
+  // out = sum of the kCL partial vectors (fixed order) scaled to unit length; returns |sum|^2
+  auto gather = [&](const QS<R, false>& out) {
     double nrm = 0.0;
     for (int i = tid; i < n; i += nt) {
-      QT<R> sacc = vec(set * kCL)[i];
+      QT<R> s = slot(0)[i];
       for (int r = 1; r < kCL; ++r) {
-        const QT<R> pp = vec(set * kCL + r)[i];
-        sacc = QT<R>{sacc.w + pp.w, sacc.x + pp.x, sacc.y + pp.y, sacc.z + pp.z};
+        const QT<R> p = slot(r)[i];
+        s = QT<R>{s.w + p.w, s.x + p.x, s.y + p.y, s.z + p.z};
       }
-      out.set(i, sacc);
-      nrm += qnorm2(sacc);
+      out.set(i, s);
+      nrm += qnorm2(s);
     }
     return cta_sum(nrm, red);
   };
-  auto norm_of = [&](const QS<R, false>& in) {
-    double sn = 0.0;
-    for (int i = tid; i < n; i += nt) sn += qnorm2(in[i]);
-    return cta_sum(sn, red);
-  };
-  auto normalise = [&](const QS<R, false>& v, double nrm2) {
+  auto normalise = [&](const QS<R, false>& in, const QS<R, false>& out, double nrm2) {
     const R inv = from_d<R>(nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0);
-    for (int i = tid; i < n; i += nt) v.set(i, qt_scale(v[i], inv));
+    for (int i = tid; i < n; i += nt) out.set(i, qt_scale(in[i], inv));
     __syncthreads();
+  };
+  auto norm_of = [&](const QS<R, false>& in) {
+    double s = 0.0;
+    for (int i = tid; i < n; i += nt) s += qnorm2(in[i]);
+    return cta_sum(s, red);
   };
 
-  for (int i = tid; i < n; i += nt) {
-    z.set(i, start);
-    x.set(i, start);
-  }
+  // lambda_max(G): z <- L (L* z) / |.|, lambda = |L* z|^2 at the last iterate
+  for (int i = tid; i < n; i += nt) v.set(i, start);
   __syncthreads();
-  double lam = 0.0, rho = 0.0;
+  double lam = 0.0;
   for (int it = 0; it < 3; ++it) {
-    apply_conj(Lw, z, t);            // t = L* z            (into every CTA)
-    apply_part(Xw, x, px);           // L^{-1} x, partial
-    __syncthreads();
-    push_part(px, 0);
+    apply_conj(v, t);                 // t = L* z
     cluster.sync();
     lam = norm_of(t);
-    rho = gather(0, y);              // y = L^{-1} x, rho = |y|^2
-    apply_part(Lw, t, pz);           // L t, partial
-    apply_conj(Xw, y, x);            // x' = L^{-*} y      (into every CTA)
-    __syncthreads();
-    push_part(pz, 1);
+    apply_part(t);                    // L t, partial sums
     cluster.sync();
-    normalise(z, gather(1, z));      // z = L t / |L t|
-    normalise(x, norm_of(x));        // x = x' / |x'|
+    const double nu = gather(v);      // v = L t
+    normalise(v, v, nu);
+  }
+  cluster.sync();   // every CTA has read its partial slots before they are rewritten
+
+  // rho: x <- G^{-1} x / |.| with G^{-1} = L^{-*} L^{-1}, rho = |L^{-1} x|^2 at the last iterate
+  for (int e = tid; e < nq * n; e += nt) {   // own columns of L^{-1} (rows >= k) from global
+    const int q = e / n, i = e % n, k = c + kCL * q;
+    if (i < k) continue;
+    const int64_t o = (int64_t)i * a.ldl + k;
+    W4.set(pool_off(n, c, q) + i - k,
+           QT<R>{from_d<R>(a.Li[o]), from_d<R>(a.Li[a.psl + o]), from_d<R>(a.Li[2 * a.psl + o]),
+                 from_d<R>(a.Li[3 * a.psl + o])});
+  }
+  for (int i = tid; i < n; i += nt) v.set(i, start);
+  __syncthreads();
+  double rho = 0.0;
+  for (int it = 0; it < 3; ++it) {
+    apply_part(v);                    // L^{-1} x, partial sums
+    cluster.sync();
+    rho = gather(t);                  // t = L^{-1} x, rho = |t|^2
+    apply_conj(t, v);                 // x' = L^{-*} t into v of every CTA
+    cluster.sync();
+    normalise(v, v, norm_of(v));
   }
   if (c == 0 && tid == 0) {
     a.scalars[kScCholOk] = 1.0;
@@ -386,15 +403,15 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kNT, 1)
       a.scalars[kScGate] = (u * kap * kap * kap < 0.04) ? 1.0 : 0.0;
     }
   }
-  cluster.sync();   // no CTA leaves while others may still read its shared memory
 }
 
 template <typename R, bool C>
 size_t smem_cl(int n) {
   constexpr int NC = C ? 2 : 4;
-  const int lf_cap = lf_capacity(n, NC);
+  const int ntri = n * (n + 1) / 2;
+  const int lf_cap = std::max(NC * ntri, (kCL + 3) * 4 * n) / NC;
   const int pool_cap = std::max(pool_off(n, 0, own_cols(n, 0)), 1);
-  return sizeof(R) * (size_t)NC * (lf_cap + 2 * pool_cap) + 16;
+  return sizeof(R) * (size_t)NC * (lf_cap + pool_cap) + 16;
 }
 
 template <typename R, bool C>
