@@ -207,12 +207,14 @@ QS_API qs_status qsketch_update_host(qs_handle_t h, const void* const A_host[4],
  * handles must be distinct.  All items are validated on the host before anything is
  * enqueued: QS_ERR_INVALID for a bad handle, plane, alignment or lda, QS_ERR_UNSUPPORTED
  * for a tensor-core handle with s > 256.  Items in the tensor-core modes (QS_PREC_BF16,
- * QS_PREC_BF16X3): each item's descriptor (tensor maps and parameters) is written into its
- * handle's workspace by one launch per 32 items, which also zeroes their sketches, and ONE
- * persistent fused-sketch launch then covers the tiles of all of them (up to 1024 items per
- * launch), in the order and on the number of CTAs that qsketch_tune_batched chose for a batch
- * of this signature (default: as given, one CTA per SM).  The other items run one update
- * each.  Everything is enqueued on `stream` with no host synchronisation and no allocation,
+ * QS_PREC_BF16X3) run in the plan that qsketch_tune_batched chose for a batch of this
+ * signature, by default: 32 items at a time, one launch that zeroes their sketches and one
+ * persistent fused-sketch launch over all their tiles (tensor maps and parameters in the
+ * kernel parameters).  The other plan form writes every item's descriptor into its handle's
+ * workspace (one launch per 32 items, which also zeroes their sketches) and covers the tiles of
+ * all items with ONE persistent launch (up to 1024 items per launch).  Plans also set the item
+ * order (as given, or largest m n first) and the number of persistent CTAs.  The other items
+ * run one update each.  Everything is enqueued on `stream` with no host synchronisation and no allocation,
  * so the call can be captured in a CUDA graph (the handles' workspaces and the A planes
  * must then stay in place for every replay). */
 QS_API qs_status qsketch_update_batched(int32_t count, const qs_handle_t* handles,
@@ -223,7 +225,9 @@ QS_API qs_status qsketch_update_batched(int32_t count, const qs_handle_t* handle
  * each matrix, Sec. 4.1).  Runs the batched update of exactly this batch (same conventions)
  * under each candidate plan -- the order of the items in the persistent launch (as given, or
  * largest m n first) and the number of persistent CTAs -- `reps` times each, after one
- * warm-up, timed with CUDA events on `stream`, and keeps the fastest plan for every later
+ * warm-up, timed with CUDA events on `stream` -- the plans: 32 items per launch or one launch
+ * for all items, as given or largest first, one CTA per SM or fewer -- and keeps the fastest
+ * plan for every later
  * qsketch_update_batched call whose batch has the same signature (per item m, n, s, l,
  * precision, embedding, pureness, in order; process-wide, thread-safe).  The sketches of the
  * handles are overwritten (as by the update itself).  This call synchronises `stream`, so it is

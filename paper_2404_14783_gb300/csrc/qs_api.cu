@@ -632,7 +632,8 @@ qs_status qsketch_tune_batched(int32_t count, const qs_handle_t* handles, const 
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return QS_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return QS_ERR_CUDA; }
-  static const TcBatchPlan cands[] = {{0, kNumSMs}, {1, kNumSMs}, {0, 144}, {1, 144}, {1, 128}};
+  static const TcBatchPlan cands[] = {{0, kNumSMs, 0}, {1, kNumSMs, 0}, {1, 144, 0}, {0, kNumSMs, 1},
+                                      {1, kNumSMs, 1}};
   float best = -1.f;
   TcBatchPlan best_plan = cands[0];
   qs_status rc = QS_OK;

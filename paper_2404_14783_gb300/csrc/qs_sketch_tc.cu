@@ -685,7 +685,7 @@ static_assert(sizeof(TcPrepare) <= 32764, "kernel parameters above the 32764-byt
 // descriptor to its place in global memory and releases the tensor maps to the copy engine.
 __global__ void batch_prepare_kernel(const __grid_constant__ TcPrepare pr) {
   const TcBatch<kMaxBatch>& bt = pr.bt;
-  if (blockIdx.x == 0) {
+  if (blockIdx.x == 0 && pr.dst[0]) {
     for (int i = 0; i < bt.count; ++i) {
       const uint32_t* src_m = reinterpret_cast<const uint32_t*>(&bt.maps[i]);
       uint32_t* dm = reinterpret_cast<uint32_t*>(&pr.dst[i]->maps);
@@ -738,6 +738,29 @@ qs_status tc_sketch_replace_batched(int count, const qs_handle_s* const* hs, con
     const qs_status r = tc_prepare(h, A + 4 * (int64_t)i, lda[i], 0, 0, h.cfg.m, h.cfg.n, 1.0,
                                    items[j].prm, items[j].maps);
     if (r != QS_OK) return r;
+  }
+  if (!plan || !plan->table) {
+    // chunks of kMaxBatch items, their descriptors in the kernel parameters: one launch
+    // zeroes the chunk's sketches, one persistent launch covers the chunk's tiles
+    for (int b0 = 0; b0 < count; b0 += kMaxBatch) {
+      TcPrepare pr;
+      pr.bt.count = std::min(kMaxBatch, count - b0);
+      pr.bt.tile_start[0] = 0;
+      for (int j = 0; j < pr.bt.count; ++j) {
+        pr.bt.maps[j] = items[b0 + j].maps;
+        pr.bt.prm[j] = items[b0 + j].prm;
+        pr.dst[j] = nullptr;
+        const int64_t tiles = (int64_t)items[b0 + j].prm.tiles_m * items[b0 + j].prm.tiles_n;
+        if (pr.bt.tile_start[j] + tiles > INT32_MAX) return QS_ERR_UNSUPPORTED;
+        pr.bt.tile_start[j + 1] = pr.bt.tile_start[j] + (int)tiles;
+      }
+      batch_prepare_kernel<<<2 * kNumSMs, 256, 0, st>>>(pr);
+      count_launch();
+      if (cudaGetLastError() != cudaSuccess) return QS_ERR_CUDA;
+      const qs_status r = launch_fused(pr.bt, st, plan ? plan->grid : kNumSMs);
+      if (r != QS_OK) return r;
+    }
+    return QS_OK;
   }
   for (int c0 = 0; c0 < count; c0 += kMaxTable) {
     const int cnt = std::min(kMaxTable, count - c0);

@@ -12,15 +12,17 @@ cudaError_t tc_pack_embeddings(const qs_handle_s& h, cudaStream_t st);
 qs_status tc_sketch_update(const qs_handle_s& h, const void* const A[4], int64_t lda, int64_t row0,
                            int64_t col0, int64_t mb, int64_t nb, double eta, cudaStream_t st);
 // Y_i = A_i Omega_i, W_i = Psi_i A_i (the sketches replaced) for count handles in the
-// tensor-core modes, whole matrices: one launch per 32 matrices writes their descriptors and
-// zeroes their Y and W, then one persistent launch covers all their tiles.  Arguments are
-// checked by the caller except the tensor-core rules, which fail the call before any launch.
+// tensor-core modes, whole matrices, in the plan's form (default: chunks of 32 items with
+// their descriptors in the kernel parameters).  Arguments are checked by the caller except the
+// tensor-core rules, which fail the call before any launch.
 // The items' descriptors go to their handles' workspaces (tc_item_bytes() at off_desc), so
 // one persistent launch covers up to 1024 items; a plan (from the autotuner) sets the item
 // order and the number of persistent CTAs.
 struct TcBatchPlan {
   int largest_first;   // 1: items by decreasing m n (the largest ones start first)
   int grid;            // persistent CTAs (<= the SM count)
+  int table;           // 1: one launch over all items, descriptors in global memory;
+                       // 0: one launch per 32 items, descriptors in the kernel parameters
 };
 size_t tc_item_bytes();
 qs_status tc_sketch_replace_batched(int count, const qs_handle_s* const* hs, const void* const* A,
