@@ -7,25 +7,31 @@
 // on G^{-1} (Sec. 3.1), the quaternion Cholesky-QR of pseudo-SVD (Alg. 2) and of the QB stage
 // (Alg. QLEQ on chi_{Psi H}).  One launch does all of it:
 //
-//   1. right-looking Cholesky, columns dealt round-robin to the 8 CTAs of a cluster (CTA c
-//      owns columns k = c (mod 8) in its working pool).  The owner of column j takes the
-//      pivot sqrt(d_j) (every thread forms it, so no CTA barrier is needed), scales the
-//      column and writes it, through distributed shared memory, into every CTA's copy of L
-//      (packed by columns, so a column is one contiguous range; the stores are spread over
-//      all threads of the CTA); one cluster barrier per column; every CTA then applies
-//      L_ik -= L_ij conj(L_kj) to the columns it owns.  On breakdown: one retry with the
+//   1. blocked right-looking Cholesky.  Columns form panels of kPB; panel p belongs to CTA
+//      p mod 8, which keeps the panel's columns (rows k..n-1) in its working pool.  The owner
+//      of a panel factors it alone (pivot sqrt(d_j), scaled column, update of the panel's
+//      later columns; CTA barriers only), writes the finished columns into its copy of L and
+//      into a packed copy in global memory (the L^{-1} output, unused until the end), and
+//      releases them with a state word in every CTA.  Each CTA takes the panels in order: it
+//      waits for panel p's state, copies the panel from global memory (L2), and if it owns
+//      panel p + 1 it first applies panel p to that panel alone and factors and publishes it
+//      (look-ahead); then it applies the rank-kPB update L_ik -= sum_t L_it conj(L_kt) to its
+//      other own columns.  One publication and one wait per panel, not per column.  Every
+//      wait is bounded (2 s from the start); the CTAs then exchange their outcomes (done,
+//      failed pivot, timeout) and take the same decision.  On breakdown: one retry with the
 //      shifted Cholesky-QR shift 11 (rows s + s (s + 1)) u trace(G) (Fukaya et al. 2020);
-//   2. L^{-1}: column k solves L x = e_k by forward substitution (one warp per column, the
-//      columns of every CTA's own set, from its full copy of L);
+//   2. L^{-1} in the same sweep: once a column m of L is final, the pool slot of column m
+//      holds column m of L^{-1} as a forward substitution L x = e_m taken panel by panel
+//      (the panel's rows by a triangular solve in one warp, the rows below by the same
+//      rank-kPB update as the factorisation), so the inverse needs no pass of its own;
 //   3. with a power slot: lambda_max(G) from three iterates z <- L L* z, and rho =
 //      x* G^{-1} x = ||L^{-1} x||^2 on three iterates x <- G^{-1} x / |G^{-1} x| from
-//      (c, 0, -c, 0); eps = 1 / sqrt(rho), kappa(H) = sqrt(lambda_max rho).  The matrix-vector
-//      products run on the owned columns; partial vectors meet in every CTA's shared memory
-//      and are added in a fixed order, so every CTA holds the same bits.
+//      (c, 0, -c, 0); eps = 1 / sqrt(rho), kappa(H) = sqrt(lambda_max rho).  One CTA, with
+//      both triangles in its shared memory; sums are taken in a fixed order.
 //
 // Arithmetic R: df64 (double-float) or double.  The trip counts of all cluster barriers are
-// the same in every CTA (failure flags are published before the barrier that precedes their
-// test), so the barriers always complete.
+// the same in every CTA (the outcome of an attempt is exchanged before the barrier that
+// precedes its test), so the barriers always complete.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -38,9 +44,13 @@ namespace {
 
 namespace cg = cooperative_groups;
 
-constexpr int kCL = 8;     // CTAs per cluster (portable cluster size)
-constexpr int kMaxN = 128; // s at most
-constexpr int kNT = 512;   // threads per CTA
+constexpr int kCL = 8;                       // CTAs per cluster (portable cluster size)
+constexpr int kMaxN = 128;                   // s at most
+constexpr int kNT = 512;                     // threads per CTA
+constexpr int kPB = 4;                       // columns per panel
+constexpr int kMaxPanels = kMaxN / kPB;      // 32
+constexpr int kMaxOwn = kMaxPanels / kCL * kPB;   // own columns of a CTA at most (16)
+constexpr int kGroups = 8;                   // partial sums per output in the matrix-vector products
 
 struct CholClArgs {
   const double* G;
@@ -61,32 +71,20 @@ struct CholClArgs {
   int gate_mode;
 };
 
-// Offset in the working pool of CTA c of its q-th own column k = c + 8 q (rows k..n-1).
-__host__ __device__ __forceinline__ int pool_off(int n, int c, int q) {
-  return q * (n - c) - kCL * q * (q - 1) / 2;
-}
-__host__ __device__ __forceinline__ int own_cols(int n, int c) {
-  return c < n ? (n - c + kCL - 1) / kCL : 0;
+// Own columns of CTA c: the columns of panels c, c + 8, ...; own index q <-> global column.
+__host__ __device__ __forceinline__ int own_col(int c, int q) { return (c + kCL * (q / kPB)) * kPB + q % kPB; }
+__host__ __device__ __forceinline__ int own_index(int k) { return (k / kPB / kCL) * kPB + k % kPB; }
+// Entries of CTA c's pool (own column k holds rows k..n-1).
+__host__ __device__ __forceinline__ int pool_entries(int n, int c) {
+  int e = 0;
+  for (int q = 0; own_col(c, q) < n; ++q) e += n - own_col(c, q);
+  return e;
 }
 // Start of column j in a lower triangle packed by columns (column j holds rows j..n-1).
-__device__ __forceinline__ int cstart(int n, int j) { return j * n - j * (j - 1) / 2; }
-
-// Own column q and row i of pool entry e.
-__device__ __forceinline__ void pool_rc(int n, int c, int nq, int e, int& q, int& i) {
-  int qq = 0;
-  while (qq + 1 < nq && pool_off(n, c, qq + 1) <= e) ++qq;
-  q = qq;
-  i = c + kCL * qq + (e - pool_off(n, c, qq));
-}
-
-template <typename R, bool C>
-__device__ __forceinline__ QS<R, C> remote(cg::cluster_group& cl, const QS<R, C>& v, unsigned r) {
-  QS<R, C> o;
-  o.c0 = cl.map_shared_rank(v.c0, r);
-  o.c1 = cl.map_shared_rank(v.c1, r);
-  o.c2 = C ? nullptr : cl.map_shared_rank(v.c2, r);
-  o.c3 = C ? nullptr : cl.map_shared_rank(v.c3, r);
-  return o;
+__host__ __device__ __forceinline__ int cstart(int n, int j) { return j * n - j * (j - 1) / 2; }
+__host__ __device__ __forceinline__ int groups_of(int n) {
+  const int g = kNT / n;
+  return g < 1 ? 1 : (g > kGroups ? kGroups : g);
 }
 
 template <typename R>
@@ -94,8 +92,8 @@ __device__ __forceinline__ double qnorm2(const QT<R>& v) {
   return to_d(v.w) * to_d(v.w) + to_d(v.x) * to_d(v.x) + to_d(v.y) * to_d(v.y) + to_d(v.z) * to_d(v.z);
 }
 
-// Sum over the CTA of one double per thread, in a fixed order (same bits in every CTA for
-// the same inputs); red has 32 slots.  Ends with a CTA barrier.
+// Sum over the CTA of one double per thread, in a fixed order (same bits for the same
+// inputs); red has 32 slots.  Ends with a CTA barrier.
 __device__ __forceinline__ double cta_sum(double v, double* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -107,6 +105,48 @@ __device__ __forceinline__ double cta_sum(double v, double* red) {
   return t;
 }
 
+// Panel states between the CTAs of the cluster: the owner releases its stores at cluster
+// scope and writes the state; a reader polls its own copy and acquires.
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void fence_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+__device__ __forceinline__ void st_relaxed_cluster(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.cluster.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_relaxed_cluster(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.cluster.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s from the kernel's start
+// The state at p once it reaches `want` (acquired), or 0 if the deadline passes first.
+__device__ __forceinline__ unsigned wait_state(const unsigned* p, unsigned want, unsigned long long deadline) {
+  for (unsigned it = 0;; ++it) {
+    const unsigned v = ld_relaxed_cluster(p);
+    if (v >= want) {
+      fence_cluster();
+      return v;
+    }
+    if ((it & 63u) == 63u && globaltimer() > deadline) return 0u;
+  }
+}
+
+// d > 0 and finite, without FP64 arithmetic (every thread of the CTA asks): a stored
+// double-float is normalised (|lo| <= ulp(hi) / 2), so its sign is the sign of hi.
+__device__ __forceinline__ bool positive(double d) { return d > 0.0 && isfinite(d); }
+__device__ __forceinline__ bool positive(df64 d) { return d.hi > 0.f && isfinite(d.hi); }
+
+// Global-memory values of the packed copy of L, read past L1 (the copy is rewritten by a
+// retry, and other CTAs write it).
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ df64 ld_cg(const df64* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return df64(v.x, v.y);
+}
+
 template <typename R, bool C>
 __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kNT, 1)
     qchol_cl_kernel(const CholClArgs a) {
@@ -114,20 +154,45 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kNT, 1)
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) uint8_t smem_raw[];
   constexpr int NC = C ? 2 : 4;
-  const int n = a.n, ntri = n * (n + 1) / 2;
+  const int n = a.n, ntri = n * (n + 1) / 2, P = (n + kPB - 1) / kPB;
   const int c = (int)cluster.block_rank();
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-  const int nq = own_cols(n, c), npool = pool_off(n, c, nq);
-  const int lf_cap = std::max(NC * ntri, (kCL + 3) * 4 * n) / NC;   // per component
-  const int pool_cap = std::max(pool_off(n, 0, own_cols(n, 0)), 1);
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   R* base = reinterpret_cast<R*>(smem_raw);
-  const QS<R, C> Lf = QS<R, C>::make(base, lf_cap);   // every CTA's copy of L, packed by columns
-  const QS<R, C> Wp = QS<R, C>::make(base + NC * lf_cap, pool_cap);  // own columns (rows k..n-1)
-  __shared__ int flag[kMaxN];   // pivot-failure flag of each column (static shared memory)
+  const QS<R, C> Lf = QS<R, C>::make(base, ntri);   // copy of L, packed by columns
+  int pool_cap = 1;
+  for (int r = 0; r < kCL; ++r) pool_cap = max(pool_cap, pool_entries(n, r));
+  const QS<R, C> Wp = QS<R, C>::make(base + NC * ntri, pool_cap);   // own columns (rows k..n-1)
+  // packed copy of L in global memory through which panels travel (component planes of Li)
+  const QS<R, C> Lb = QS<R, C>::make(reinterpret_cast<R*>(a.Li), (int)a.psl);
+
+  // state of panel p, pushed by its owner: 2 attempt + 1 published, 2 attempt + 2 failed pivot
+  __shared__ unsigned flag[kMaxPanels];
+  __shared__ int vote[2][kCL];        // each CTA's outcome of each attempt
   __shared__ double red[32];
+  __shared__ int own_k[kMaxOwn], own_off[kMaxOwn + 1], nq_s;
+  __shared__ int tab[kMaxOwn + 1], tab_start[kMaxOwn];   // entries of the current update
+  __shared__ double invd_raw[kPB];    // reciprocals of the current panel's diagonal (R values)
+  __shared__ double rho_raw;          // rho, handed from CTA 1 to CTA 0 (an R value)
+  __shared__ unsigned rho_flag;
+  R* invd = reinterpret_cast<R*>(invd_raw);
+  if (tid == 0) rho_flag = 0u;
+  for (int j = tid; j < kMaxPanels; j += nt) flag[j] = 0u;
+  if (tid < 2 * kCL) vote[tid / kCL][tid % kCL] = 0;
+  if (tid == 0) {
+    int q = 0, off = 0;
+    for (; own_col(c, q) < n; ++q) {
+      own_k[q] = own_col(c, q);
+      own_off[q] = off;
+      off += n - own_k[q];
+    }
+    own_off[q] = off;
+    nq_s = q;
+  }
+  const unsigned long long deadline = globaltimer() + kWaitNs;
 
   const bool stopped = (a.status[0] & kDevStopCorr) != 0;
-  cluster.sync();   // every CTA runs (and has read the status) before any remote access
+  cluster.sync();   // every CTA runs (and has cleared its states) before any remote access
+  const int nq = nq_s, npool = own_off[nq];
 
   auto gget = [&](int i, int k, int p) { return a.G[p * a.psg + (int64_t)i * a.ldg + k]; };
   auto put = [&](double* M, int i, int k, const QT<R>& v) {
@@ -138,7 +203,7 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kNT, 1)
   };
   auto give_up = [&]() {   // L = L^{-1} = I on the own columns; the caller skips the result
     for (int e = tid; e < nq * n; e += nt) {
-      const int q = e / n, i = e % n, k = c + kCL * q;
+      const int q = e / n, i = e % n, k = own_k[q];
       const QT<R> v{(i == k) ? R(1) : R(0), R(0), R(0), R(0)};
       put(a.Li, i, k, v);
       put(a.Lg, i, k, v);
@@ -153,235 +218,339 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kNT, 1)
     return;
   }
 
-  // ------------------------------------------------------------------ 1. Cholesky
+  // ---------------------------------------------------------------- panel routines
+  // Owner of panel pp: factor its columns (each updated by every earlier panel), write them
+  // into the local and the global copy of L, then publish the panel's state (okv, or
+  // okv + 1 after a failed pivot).
+  auto factor_publish = [&](int pp, unsigned okv) {
+    const int k0 = pp * kPB, k1 = min(k0 + kPB, n);
+    bool f = false;
+    for (int j = k0; j < k1; ++j) {
+      const int off = own_off[own_index(j)], len = n - j, cs = cstart(n, j);
+      const R d = Wp[off].w;   // every thread forms the same pivot
+      if (!positive(d)) {
+        f = true;
+        break;
+      }
+      const R r = sqrt_(d), ir = rcp_(r);
+      for (int ii = tid; ii < len; ii += nt) {
+        const QT<R> v = ii == 0 ? QT<R>{r, R(0), R(0), R(0)} : qscale<R, C>(Wp[off + ii], ir);
+        Lf.set(cs + ii, v);
+        Lb.set(cs + ii, v);
+      }
+      __syncthreads();
+      // the panel's later columns k: W_ik -= L_ij conj(L_kj), rows i >= k (sum_k n - k entries)
+      const int nk = k1 - 1 - j, tot = nk * (n - j - 1) - nk * (nk - 1) / 2;
+      for (int e = tid; e < tot; e += nt) {
+        int k = j + 1, ee = e;
+        while (ee >= n - k) { ee -= n - k; ++k; }
+        const int i = k + ee, ok = own_off[own_index(k)] + ee;
+        Wp.set(ok, qsub_mul_conj<R, C>(Wp[ok], Lf[cs + i - j], Lf[cs + k - j]));
+      }
+      __syncthreads();
+    }
+    if (tid < kCL) {   // release (cumulative over the CTA's stores, behind the barrier above)
+      fence_cluster();
+      st_relaxed_cluster(cluster.map_shared_rank(flag, tid) + pp, f ? okv + 1u : okv);
+    }
+  };
+  // Rows t in [max(m, k0), k1) of column m of L^{-1} for own column q (one warp, all lanes):
+  // the residuals r_t that the earlier panels left in the pool (e_m for a column created by
+  // this panel) become x_t = (r_t - sum_{t' < t} L_tt' x_t') / L_tt, stored in their place.
+  auto xsolve = [&](int q, int k0, int k1) {
+    const int m = own_k[q], off = own_off[q], t0 = max(m, k0), j = t0 + lane;
+    const bool act = j < k1;
+    QT<R> r{R(0), R(0), R(0), R(0)};
+    if (act) r = (m >= k0) ? QT<R>{(j == m) ? R(1) : R(0), R(0), R(0), R(0)} : Wp[off + j - m];
+    for (int t = t0; t < k1; ++t) {
+      const int src = t - t0;
+      QT<R> x = qscale<R, C>(r, invd[t - k0]);   // x_t, valid in lane src
+      x.w = shfl_r(x.w, src);
+      x.x = shfl_r(x.x, src);
+      if (!C) {
+        x.y = shfl_r(x.y, src);
+        x.z = shfl_r(x.z, src);
+      }
+      if (lane == src) {
+        r = x;
+      } else if (act && j > t) {   // r_j -= L_jt x_t
+        const QT<R> nx{-x.w, -x.x, -x.y, -x.z};
+        r = qmac<R, C>(r, Lf[cstart(n, t) + j - t], nx);
+      }
+    }
+    if (act) Wp.set(off + j - m, r);
+  };
+  // Rank-kPB update by panel p = columns k0..k1-1 of own pool entry (q, i):
+  //   Schur-complement column k >= k1:  W_ik -= sum_t L_it conj(L_kt);
+  //   L^{-1} column m < k1 (rows i >= k1): r_i -= sum_t L_it x_t, t >= max(m, k0); a column
+  //   created by this panel (m >= k0) starts from r_i = 0.
+  auto update_entry = [&](int q, int i, int k0, int k1) {
+    const int k = own_k[q], e = own_off[q] + (i - k);
+    const QT<R> zero{R(0), R(0), R(0), R(0)};
+    if (k >= k1) {
+      QT<R> w = Wp[e];
+      for (int t = k0; t < k1; ++t) {
+        const int cs = cstart(n, t) - t;
+        w = qsub_mul_conj<R, C>(w, Lf[cs + i], Lf[cs + k]);
+      }
+      Wp.set(e, w);
+    } else {
+      QT<R> w = (k >= k0) ? zero : Wp[e];
+      for (int t = max(k, k0); t < k1; ++t) {
+        const QT<R> x = Wp[own_off[q] + (t - k)];
+        const QT<R> nx{-x.w, -x.x, -x.y, -x.z};
+        w = qmac<R, C>(w, Lf[cstart(n, t) + i - t], nx);
+      }
+      Wp.set(e, w);
+    }
+  };
+
+  // ------------------------------------------------------------------ 1-2. L and L^{-1}
   double shift = 0.0;
-  bool fail = false;
+  int outcome = 0;   // of the last attempt, the same in every CTA: 0 done, 1 pivot failure, 2 timeout
   for (int attempt = 0; attempt < 2; ++attempt) {
+    const unsigned okv = 2u * (unsigned)attempt + 1u;
     for (int e = tid; e < npool; e += nt) {
-      int q, i;
-      pool_rc(n, c, nq, e, q, i);
-      const int k = c + kCL * q;
+      int q = 0;
+      while (q + 1 < nq && own_off[q + 1] <= e) ++q;
+      const int k = own_k[q], i = k + (e - own_off[q]);
       double w = gget(i, k, 0), x = gget(i, k, 1), y = 0.0, z = 0.0;
       if (!C) { y = gget(i, k, 2); z = gget(i, k, 3); }
       if (i == k) { x = y = z = 0.0; w += shift; }
       Wp.set(e, QT<R>{from_d<R>(w), from_d<R>(x), from_d<R>(y), from_d<R>(z)});
     }
     __syncthreads();
-    fail = false;
-    for (int j = 0; j < n; ++j) {
-      if (j % kCL == c) {   // owner: pivot, scale, publish column j
-        const int off = pool_off(n, c, j / kCL), len = n - j, cs = cstart(n, j);
-        const R d = Wp[off].w;   // every thread forms the same pivot
-        const double dd = to_d(d);
-        const int f = (!(dd > 0.0) || !isfinite(dd)) ? 1 : 0;
-        if (!f) {
-          const R r = sqrt_(d), ir = rcp_(r);
-          // (target CTA, row) pairs spread over the threads; consecutive threads write
-          // consecutive entries of one target
-          for (int p = tid; p < kCL * len; p += nt) {
-            const int tr = p / len, ii = p - tr * len;
-            const QT<R> v = ii == 0 ? QT<R>{r, R(0), R(0), R(0)} : qscale<R, C>(Wp[off + ii], ir);
-            remote<R, C>(cluster, Lf, tr).set(cs + ii, v);
-          }
-        }
-        if (tid < kCL) cluster.map_shared_rank(flag, tid)[j] = f;
-      }
-      cluster.sync();
-      if (flag[j]) {
-        fail = true;
+    if (c == 0) factor_publish(0, okv);
+    int mine = 0;
+    for (int p = 0; p < P; ++p) {
+      // thread 0 waits for panel p's state, the CTA barrier hands it (and the panel) on
+      unsigned v = okv;
+      if (tid == 0) v = wait_state(flag + p, okv, deadline);
+      if (__syncthreads_or(tid == 0 && v != okv)) {
+        mine = __syncthreads_or(tid == 0 && v == 0u) ? 2 : 1;
         break;
       }
-      // trailing update of the own columns k > j with column j
-      const int q0 = j < c ? 0 : (j - c) / kCL + 1, cs = cstart(n, j);
-      for (int e = pool_off(n, c, q0) + tid; e < npool; e += nt) {
-        int q, i;
-        pool_rc(n, c, nq, e, q, i);
-        const int k = c + kCL * q;
-        Wp.set(e, qsub_mul_conj<R, C>(Wp[e], Lf[cs + i - j], Lf[cs + k - j]));
+      const int k0 = p * kPB, k1 = min(k0 + kPB, n);
+      const bool mine_p = p % kCL == c;
+      if (!mine_p) {   // the panel's columns from the packed copy in global memory
+        const int b = cstart(n, k0), cnt = cstart(n, k1) - b;
+        for (int e = tid; e < NC * cnt; e += nt) {
+          const int comp = e / cnt, idx = b + (e - comp * cnt);
+          R* dst = comp == 0 ? Lf.c0 : comp == 1 ? Lf.c1 : comp == 2 ? Lf.c2 : Lf.c3;
+          const R* src = comp == 0 ? Lb.c0 : comp == 1 ? Lb.c1 : comp == 2 ? Lb.c2 : Lb.c3;
+          dst[idx] = ld_cg(src + idx);
+        }
+      }
+      if (tid < k1 - k0) {
+        const int cs = cstart(n, k0 + tid);
+        invd[tid] = rcp_(mine_p ? Lf.c0[cs] : ld_cg(Lb.c0 + cs));
       }
       __syncthreads();
-    }
-    if (!fail) break;
-    cluster.sync();   // every CTA has read the failure flag before any is rewritten
-    if (attempt == 0 && a.allow_shift) {
-      // shifted Cholesky-QR: shift = 11 (rows s + s (s + 1)) u trace(G), same bits in every CTA
-      double tr = 0.0;
-      for (int i = tid; i < n; i += nt) tr += gget(i, i, 0);
-      tr = cta_sum(tr, red);
-      shift = 11.0 * (a.shift_rows * n + (double)n * (n + 1)) * 1.1102230246251565e-16 * tr;
-      if (c == 0 && tid == 0) {
-        a.scalars[kScShift] = shift;
-        atomicOr(a.status, kDevRank);
+      const bool look = p + 1 < P && (p + 1) % kCL == c;
+      if (look) {   // panel p + 1 first, so that it is published as early as possible
+        const int n0 = k1, nk = min(n0 + kPB, n) - n0, tot = nk * (n - n0) - nk * (nk - 1) / 2;
+        for (int e = tid; e < tot; e += nt) {
+          int k = n0, ee = e;
+          while (ee >= n - k) { ee -= n - k; ++k; }
+          update_entry(own_index(k), k + ee, k0, k1);
+        }
+        __syncthreads();
+        factor_publish(p + 1, okv);
       }
-      continue;
+      // L^{-1}: the panel's rows of every own column m < k1 (one warp per column)
+      for (int q = warp; q < nq; q += kNT / 32)
+        if (own_k[q] < k1) xsolve(q, k0, k1);
+      if (tid == 0) {   // entries of the rank-kPB update (the look-ahead panel is done)
+        int acc = 0;
+        for (int q = 0; q < nq; ++q) {
+          const int k = own_k[q];
+          int start = k1, cnt = n - k1;
+          if (k >= k1) {
+            start = k;
+            cnt = (look && k / kPB == p + 1) ? 0 : n - k;
+          }
+          tab_start[q] = start;
+          tab[q] = acc;
+          acc += cnt;
+        }
+        tab[nq] = acc;
+      }
+      __syncthreads();
+      const int tot = tab[nq];
+      for (int e = tid; e < tot; e += nt) {
+        int q = 0;
+        while (tab[q + 1] <= e) ++q;
+        update_entry(q, tab_start[q] + (e - tab[q]), k0, k1);
+      }
+      // no barrier: the next panel's wait ends with one
     }
-    break;
+    // every CTA learns every CTA's outcome; after this barrier no CTA reads the packed copy
+    if (tid < kCL) cluster.map_shared_rank(&vote[attempt][0], tid)[c] = mine;
+    cluster.sync();
+    outcome = 0;
+    for (int r = 0; r < kCL; ++r) outcome = max(outcome, vote[attempt][r]);
+    if (outcome != 1 || attempt == 1 || !a.allow_shift) break;
+    // shifted Cholesky-QR: shift = 11 (rows s + s (s + 1)) u trace(G), same bits in every CTA
+    double tr = 0.0;
+    for (int i = tid; i < n; i += nt) tr += gget(i, i, 0);
+    tr = cta_sum(tr, red);
+    shift = 11.0 * (a.shift_rows * n + (double)n * (n + 1)) * 1.1102230246251565e-16 * tr;
+    if (c == 0 && tid == 0) {
+      a.scalars[kScShift] = shift;
+      atomicOr(a.status, kDevRank);
+    }
   }
-  if (fail) {
-    if (c == 0 && tid == 0) atomicOr(a.status, a.fail_bits);
+  if (outcome != 0) {
+    if (c == 0 && tid == 0) atomicOr(a.status, outcome == 2 ? kDevTimeout : a.fail_bits);
     give_up();
     return;
   }
-  // L to global memory (own columns, zero above the diagonal), and into the working pool
-  // (the power iterates use the own columns after the copy of L becomes exchange space)
+  // L and L^{-1} (own columns, zero above the diagonal) to global memory
   for (int e = tid; e < nq * n; e += nt) {
-    const int q = e / n, i = e % n, k = c + kCL * q;
-    const QT<R> v = i < k ? QT<R>{R(0), R(0), R(0), R(0)} : Lf[cstart(n, k) + i - k];
-    put(a.Lg, i, k, v);
-    if (i >= k) Wp.set(pool_off(n, c, q) + i - k, v);
-  }
-
-  // ------------------------------------------------------------------ 2. L^{-1}, own columns
-  // Right-looking forward substitution: lane t owns rows k + t + 32 u and their running sums
-  // acc = sum_{m<i} L_rm x_m; at step i the owner of row i forms x_i = (delta_ik - acc_i) / L_ii
-  // and every lane adds L_ri x_i to its rows r > i.  n <= 128.
-  for (int q = warp; q < nq; q += nw) {
-    const int k = c + kCL * q;
-    QT<R> acc[4], xs[4];
-    R invd[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      acc[u] = QT<R>{R(0), R(0), R(0), R(0)};
-      xs[u] = acc[u];
-      const int r = k + lane + 32 * u;
-      invd[u] = r < n ? rcp_(Lf[cstart(n, r)].w) : R(0);
-    }
-    for (int i = k; i < n; ++i) {
-      const int li = i - k, owner = li & 31, uo = li >> 5;   // warp-uniform
-      QT<R> av = acc[0];
-      R id = invd[0];
-      if (uo == 1) { av = acc[1]; id = invd[1]; }
-      if (uo == 2) { av = acc[2]; id = invd[2]; }
-      if (uo == 3) { av = acc[3]; id = invd[3]; }
-      const R one = (i == k) ? R(1) : R(0);
-      QT<R> xi = qscale<R, C>(QT<R>{one - av.w, -av.x, -av.y, -av.z}, id);   // valid in the owner
-      xi.w = nrm_(shfl_r(xi.w, owner));
-      xi.x = nrm_(shfl_r(xi.x, owner));
-      if (!C) {
-        xi.y = nrm_(shfl_r(xi.y, owner));
-        xi.z = nrm_(shfl_r(xi.z, owner));
+    const int q = e / n, i = e % n, k = own_k[q];
+    if (i < k) {   // plain zeros (a conversion to FP64 costs the FP64 pipe)
+      for (int pl = 0; pl < 4; ++pl) {
+        a.Lg[pl * a.psl + (int64_t)i * a.ldl + k] = 0.0;
+        a.Li[pl * a.psl + (int64_t)i * a.ldl + k] = 0.0;
       }
-      const int cs = cstart(n, i) - i, ulast = (n - 1 - k) >> 5;   // rows r: entry cs + r
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (u < uo || u > ulast) continue;   // warp-uniform: no live row in this slot
-        const int lr = lane + 32 * u, r = k + lr;
-        if (lr == li) xs[u] = xi;
-        if (lr > li && r < n) acc[u] = qmac<R, C>(acc[u], Lf[cs + r], xi);
-      }
+      continue;
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = k + lane + 32 * u;
-      if (r < n) put(a.Li, r, k, xs[u]);
-    }
-    for (int r = lane; r < k; r += 32) put(a.Li, r, k, QT<R>{R(0), R(0), R(0), R(0)});
+    put(a.Lg, i, k, Lf[cstart(n, k) + i - k]);
+    put(a.Li, i, k, Wp[own_off[q] + i - k]);
   }
   if (a.power_slot < 0 || C) {
     if (c == 0 && tid == 0) a.scalars[kScCholOk] = 1.0;
     return;   // no remote access follows the last cluster barrier
   }
-  __syncthreads();   // own columns of L^{-1} in global memory, visible to this CTA
-  cluster.sync();    // no CTA still reads its copy of L: it becomes exchange space
-
   // ------------------------------------------------------------------ 3. power iterates
-  // exchange space in the L region: kCL partial vectors, then vectors v, t, pv (n each)
-  const QS<R, false> v = QS<R, false>::make(base + kCL * 4 * n, n);
-  const QS<R, false> t = QS<R, false>::make(base + (kCL + 1) * 4 * n, n);
-  const QS<R, false> pv = QS<R, false>::make(base + (kCL + 2) * 4 * n, n);
-  auto slot = [&](int r) { return QS<R, false>::make(base + r * 4 * n, n); };
-  const QS<R, false> W4 = QS<R, false>::make(base + NC * lf_cap, pool_cap);   // own columns
-  const double c0 = 1.0 / sqrt(2.0 * n);
-  const QT<R> start{from_d<R>(c0), R(0), from_d<R>(-c0), R(0)};
-  // out_k = sum_{i >= k} conj(M_ik) in_i for the own columns k (one warp per column), written
-  // into `dst` of every CTA
-  auto apply_conj = [&](const QS<R, false>& in, const QS<R, false>& dst) {
-    for (int q = warp; q < nq; q += nw) {
-      const int k = c + kCL * q, off = pool_off(n, c, q);
-      QT<R> s{R(0), R(0), R(0), R(0)};
-      for (int i = k + lane; i < n; i += 32) s = qt_mac_conj_a(s, W4[off + i - k], in[i]);
-      s = wsum4(s);
-      if (lane < kCL) remote<R, false>(cluster, dst, lane).set(k, s);
+  // lambda on CTA 0 (its copy of L) while CTA 1 takes rho: it first gathers L^{-1}, packed by
+  // columns, from the working pools of all CTAs (distributed shared memory) into its copy of L
+  if (c == 1) {
+    const float b2 = (float)(2 * n + 1);
+    for (int f = tid; f < ntri; f += nt) {
+      // column k of packed entry f: the root of k^2 - (2n + 1) k + 2 f = 0, corrected
+      int k = (int)((b2 - sqrtf(fmaxf(b2 * b2 - 8.0f * (float)f, 0.0f))) * 0.5f);
+      k = min(max(k, 0), n - 1);
+      if (k + 1 < n && cstart(n, k + 1) <= f) ++k;
+      if (k > 0 && cstart(n, k) > f) --k;
+      const int i = k + (f - cstart(n, k)), r = (k / kPB) % kCL, qk = own_index(k);
+      int off = 0;
+      for (int q = 0; q < qk; ++q) off += n - own_col(r, q);
+      const QS<R, false> src{cluster.map_shared_rank(Wp.c0, r), cluster.map_shared_rank(Wp.c1, r),
+                             cluster.map_shared_rank(Wp.c2, r), cluster.map_shared_rank(Wp.c3, r)};
+      Lf.set(f, src[off + (i - k)]);
     }
-  };
-  // partial out_i = sum_{own k <= i} M_ik in_k into slot c of every CTA
-  auto apply_part = [&](const QS<R, false>& in) {
-    for (int i = tid; i < n; i += nt) {
+  }
+  __syncthreads();
+  cluster.sync();   // the pools are no longer read remotely
+  if (c >= 2) return;
+
+  // vectors and partial sums in the pool region (free now); kG partial sums per output
+  const int kG = groups_of(n), ch = (n + kG - 1) / kG;
+  R* vb = base + NC * ntri;
+  auto vec = [&](int slot) { return QS<R, false>::make(vb + slot * 4 * n, n); };
+  const QS<R, false> v = vec(0), t = vec(1);
+  const QS<R, false> M = QS<R, false>::make(base, ntri);   // the triangle in use, packed by columns
+  // out_k = sum_{i >= k} conj(M_ik) in_i
+  auto upper_conj = [&](const QS<R, false>& in, const QS<R, false>& out) {
+    for (int w = tid; w < n * kG; w += nt) {
+      const int k = w % n, g = w / n, cs = cstart(n, k) - k;
       QT<R> s{R(0), R(0), R(0), R(0)};
-      for (int q = 0; q < nq; ++q) {
-        const int k = c + kCL * q;
-        if (k > i) break;
-        s = qt_mac(s, W4[pool_off(n, c, q) + i - k], in[k]);
-      }
-      pv.set(i, s);
+      for (int i = max(k, g * ch); i < min(n, (g + 1) * ch); ++i) s = qt_mac_conj_a(s, M[cs + i], in[i]);
+      vec(2 + g).set(k, s);
     }
     __syncthreads();
-    for (int p = tid; p < kCL * n; p += nt) {
-      const int tr = p / n, i = p - tr * n;
-      remote<R, false>(cluster, slot(c), tr).set(i, pv[i]);
+    for (int k = tid; k < n; k += nt) {
+      QT<R> s = vec(2)[k];
+      for (int g = 1; g < kG; ++g) {
+        const QT<R> p = vec(2 + g)[k];
+        s = QT<R>{s.w + p.w, s.x + p.x, s.y + p.y, s.z + p.z};
+      }
+      out.set(k, s);
     }
+    __syncthreads();
   };
-  // out = sum of the kCL partial vectors (fixed order) scaled to unit length; returns |sum|^2
-  auto gather = [&](const QS<R, false>& out) {
-    double nrm = 0.0;
+  // out_i = sum_{k <= i} M_ik in_k
+  auto lower = [&](const QS<R, false>& in, const QS<R, false>& out) {
+    for (int w = tid; w < n * kG; w += nt) {
+      const int i = w % n, g = w / n;
+      QT<R> s{R(0), R(0), R(0), R(0)};
+      for (int k = g * ch; k < min((g + 1) * ch, i + 1); ++k) s = qt_mac(s, M[cstart(n, k) + i - k], in[k]);
+      vec(2 + g).set(i, s);
+    }
+    __syncthreads();
     for (int i = tid; i < n; i += nt) {
-      QT<R> s = slot(0)[i];
-      for (int r = 1; r < kCL; ++r) {
-        const QT<R> p = slot(r)[i];
+      QT<R> s = vec(2)[i];
+      for (int g = 1; g < kG; ++g) {
+        const QT<R> p = vec(2 + g)[i];
         s = QT<R>{s.w + p.w, s.x + p.x, s.y + p.y, s.z + p.z};
       }
       out.set(i, s);
-      nrm += qnorm2(s);
     }
-    return cta_sum(nrm, red);
-  };
-  auto normalise = [&](const QS<R, false>& in, const QS<R, false>& out, double nrm2) {
-    const R inv = from_d<R>(nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0);
-    for (int i = tid; i < n; i += nt) out.set(i, qt_scale(in[i], inv));
     __syncthreads();
   };
+  // |in|^2 in the working type (sums over the CTA in a fixed order; no FP64 arithmetic in
+  // every thread: the FP64 pipe is a small fraction of the FP32 one)
+  R* redr = reinterpret_cast<R*>(red);
   auto norm_of = [&](const QS<R, false>& in) {
-    double s = 0.0;
-    for (int i = tid; i < n; i += nt) s += qnorm2(in[i]);
-    return cta_sum(s, red);
+    R s(0);
+    for (int i = tid; i < n; i += nt) {
+      const QT<R> q = in[i];
+      s = fma(q.w, q.w, fma(q.x, q.x, fma(q.y, q.y, fma(q.z, q.z, s))));
+    }
+    s = wsum(s);
+    if (lane == 0) redr[warp] = nrm_(s);
+    __syncthreads();
+    R t = redr[0];
+    for (int w = 1; w < kNT / 32; ++w) t = t + redr[w];
+    __syncthreads();
+    return nrm_(t);
   };
+  auto normalise = [&](const QS<R, false>& in) {
+    const R nrm2 = norm_of(in);
+    const R inv = positive(nrm2) ? rcp_(sqrt_(nrm2)) : R(0);
+    for (int i = tid; i < n; i += nt) in.set(i, qt_scale(in[i], inv));
+    __syncthreads();
+  };
+  const R c0 = rcp_(sqrt_(R(2 * n)));   // 1 / sqrt(2 s)
+  const QT<R> start{c0, R(0), -c0, R(0)};
 
-  // lambda_max(G): z <- L (L* z) / |.|, lambda = |L* z|^2 at the last iterate
+  // CTA 0: lambda_max(G): z <- L (L* z) / |.|, lambda = |L* z|^2 at the last iterate.
+  // CTA 1: rho: x <- G^{-1} x / |.| with G^{-1} = L^{-*} L^{-1}, rho = |L^{-1} x|^2 at the last
+  // iterate.
   for (int i = tid; i < n; i += nt) v.set(i, start);
   __syncthreads();
-  double lam = 0.0;
+  R val(0);
   for (int it = 0; it < 3; ++it) {
-    apply_conj(v, t);                 // t = L* z
-    cluster.sync();
-    lam = norm_of(t);
-    apply_part(t);                    // L t, partial sums
-    cluster.sync();
-    const double nu = gather(v);      // v = L t
-    normalise(v, v, nu);
+    if (c == 0) {
+      upper_conj(v, t);   // t = L* z
+      val = norm_of(t);
+      lower(t, v);        // v = L t
+    } else {
+      lower(v, t);        // t = L^{-1} x
+      val = norm_of(t);
+      upper_conj(t, v);   // x' = L^{-*} t
+    }
+    normalise(v);
   }
-  cluster.sync();   // every CTA has read its partial slots before they are rewritten
-
-  // rho: x <- G^{-1} x / |.| with G^{-1} = L^{-*} L^{-1}, rho = |L^{-1} x|^2 at the last iterate
-  for (int e = tid; e < nq * n; e += nt) {   // own columns of L^{-1} (rows >= k) from global
-    const int q = e / n, i = e % n, k = c + kCL * q;
-    if (i < k) continue;
-    const int64_t o = (int64_t)i * a.ldl + k;
-    W4.set(pool_off(n, c, q) + i - k,
-           QT<R>{from_d<R>(a.Li[o]), from_d<R>(a.Li[a.psl + o]), from_d<R>(a.Li[2 * a.psl + o]),
-                 from_d<R>(a.Li[3 * a.psl + o])});
+  if (c == 1) {   // hand rho to CTA 0 (release, then its state)
+    if (tid == 0) {
+      *cluster.map_shared_rank(reinterpret_cast<R*>(&rho_raw), 0) = val;
+      fence_cluster();
+      st_relaxed_cluster(cluster.map_shared_rank(&rho_flag, 0), 1u);
+    }
+    return;
   }
-  for (int i = tid; i < n; i += nt) v.set(i, start);
-  __syncthreads();
-  double rho = 0.0;
-  for (int it = 0; it < 3; ++it) {
-    apply_part(v);                    // L^{-1} x, partial sums
-    cluster.sync();
-    rho = gather(t);                  // t = L^{-1} x, rho = |t|^2
-    apply_conj(t, v);                 // x' = L^{-*} t into v of every CTA
-    cluster.sync();
-    normalise(v, v, norm_of(v));
+  const R lam_r = val;
+  R rho_r(0);
+  bool rho_ok = true;
+  if (tid == 0) {
+    rho_ok = wait_state(&rho_flag, 1u, deadline) != 0u;
+    if (rho_ok) rho_r = *reinterpret_cast<R*>(&rho_raw);
+    else atomicOr(a.status, kDevTimeout);
   }
-  if (c == 0 && tid == 0) {
+  if (tid == 0) {
+    const double lam = to_d(lam_r), rho = rho_ok ? to_d(rho_r) : 0.0;
     a.scalars[kScCholOk] = 1.0;
     a.scalars[kScLamMax] = lam;
     const int slot_ = a.power_slot;
@@ -405,13 +574,18 @@ __global__ void __cluster_dims__(kCL, 1, 1) __launch_bounds__(kNT, 1)
   }
 }
 
+// Second shared-memory region (R values): the pool, or the power iterates' vectors if larger.
+template <bool C>
+int region2(int n) {
+  int pool = 1;
+  for (int r = 0; r < kCL; ++r) pool = std::max(pool, pool_entries(n, r));
+  return C ? 2 * pool : 4 * std::max(pool, (2 + groups_of(n)) * n);
+}
+
 template <typename R, bool C>
 size_t smem_cl(int n) {
   constexpr int NC = C ? 2 : 4;
-  const int ntri = n * (n + 1) / 2;
-  const int lf_cap = std::max(NC * ntri, (kCL + 3) * 4 * n) / NC;
-  const int pool_cap = std::max(pool_off(n, 0, own_cols(n, 0)), 1);
-  return sizeof(R) * (size_t)NC * (lf_cap + pool_cap) + 16;
+  return sizeof(R) * ((size_t)NC * (n * (n + 1) / 2) + (size_t)region2<C>(n)) + 16;
 }
 
 template <typename R, bool C>
@@ -443,6 +617,8 @@ cudaError_t launch_qchol_cluster(const double* G, int64_t ldg, int64_t psg, doub
                                  cudaStream_t st, const double* gate, double thr, int gate_mode) {
   if (n < 1 || n > qchol_cluster_max_n(complex_only) || !Lg || !Li) return cudaErrorInvalidValue;
   if (complex_only && power_slot >= 0) return cudaErrorInvalidValue;
+  // the packed copy of L travels through the planes of Li: each must hold n (n + 1) / 2 values
+  if (ldl < n || psl < (int64_t)n * ldl) return cudaErrorInvalidValue;
   const CholClArgs a{G, ldg, psg, Lg, Li, ldl, psl, n, allow_shift, shift_rows, power_slot, kappa_stop,
                      status, scalars, fail_bits, gate, thr, gate_mode};
   if (use_df64) return complex_only ? launch_cl<df64, true>(a, st) : launch_cl<df64, false>(a, st);
