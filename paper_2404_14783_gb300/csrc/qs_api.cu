@@ -382,6 +382,18 @@ qs_status core_solve(const Ctx& x) {
   // P^dagger (s x l), in the working precision of W; with an uncorrected H the norm of
   // P^dagger is kappa(H) times that of P, so it stays FP64 and X accumulates in double-float
   const bool wide = !x.mixed() || !x.h->h_well_conditioned;
+  if (wide && x.acc_hi() == 2) {
+    // double-float: X* = W* (P^dagger)* as a tall product (n rows, s columns: 64 x 16 tiles,
+    // no padding of s to 64 and about two full waves), stored conjugate-transposed into X
+    GemmDesc d{};
+    d.M = x.n; d.N = s; d.K = l;
+    x.W().cplanes(d.a); d.lda = x.W().ld; d.a_f64 = x.W().f64; d.conj_a = 1;
+    ZT.cplanes(d.b); d.ldb = ZT.ld; d.b_f64 = 1;
+    x.X().planes(d.c); d.ldc = x.X().ld; d.c_f64 = x.X().f64;
+    d.alpha = 1.0; d.beta = 0.0; d.acc_f64 = 2; d.splits = 1; d.ct_out = 1;
+    QS_CU(launch_qgemm(d, x.st));
+    return QS_OK;
+  }
   const Mat Zw{Z.p, Z.ld, Z.ps, wide ? 1 : 0};
   QS_CU(launch_qconjT(ZT.p, 1, ZT.ld, ZT.ps, Zw.p, Zw.f64, Zw.ld, Zw.ps, (int)l, s, x.st));
   // X = P^dagger W (s x n).  Split-K partial sums are added with atomics into X; an FP32 X

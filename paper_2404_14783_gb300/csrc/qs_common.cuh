@@ -124,6 +124,8 @@ struct GemmDesc {
   int herm;      // C = A* A is Hermitian: the small kernel computes only tiles on/above the
                  // diagonal (the caller mirrors the rest)
   int cplx_out;  // small kernel with conj_a: form only the complex part (planes w, x) of C
+  int ct_out;    // tall kernel: store the conjugate transpose of the product (C holds
+                 // (op(A) B)*, an N x M matrix with leading dimension ldc); splits == 1
 };
 // Plane pointers of a matrix with uniform plane stride.
 inline void planes_of(const void* base, int64_t ps, int esize, int64_t offset_elems,

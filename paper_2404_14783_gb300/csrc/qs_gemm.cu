@@ -118,6 +118,7 @@ __global__ void draw_kernel(T* out, int64_t rows, int64_t cols, int kind, uint32
 cudaError_t launch_qgemm(const GemmDesc& d, cudaStream_t st) {
   if (d.M <= 0 || d.N <= 0) return cudaSuccess;
   if (d.K <= 0 || d.splits < 1) return cudaErrorInvalidValue;
+  if (d.ct_out && (d.splits != 1 || d.small || d.epi)) return cudaErrorInvalidValue;
   if (d.acc_f64 == 0) {
     if (d.a_f64 || d.b_f64 || d.c_f64) return cudaErrorInvalidValue;
     return launch_qgemm_f32(d, st);

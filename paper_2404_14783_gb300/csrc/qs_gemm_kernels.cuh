@@ -224,8 +224,9 @@ __global__ void __launch_bounds__(256, TN == 1 ? 3 : ((sizeof(ACC) == 4 || TN ==
       if (n >= g.N) continue;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        TC* dst = static_cast<TC*>(g.c[q]) + m * g.ldc + n;
-        const ACC v = alpha * acc[q][i][j];
+        // element (m, n) of the product, or of its conjugate transpose at (n, m)
+        TC* dst = static_cast<TC*>(g.c[q]) + (g.ct_out ? n * g.ldc + m : m * g.ldc + n);
+        const ACC v = (g.ct_out && q) ? -(alpha * acc[q][i][j]) : alpha * acc[q][i][j];
         if (g.splits > 1) {
           atomicAdd(dst, static_cast<TC>(v));
         } else if (g.beta == 0.0) {
@@ -336,11 +337,15 @@ cudaError_t launch_t(const GemmDesc& d, cudaStream_t st) {
   const bool bcplx = !d.b[2] && !d.b[3] && d.b[0] && d.b[1];
   // double-float tall products with a narrow N: 64 x 32 tiles (4 x 2 outputs per thread), or
   // 64 x 16 (4 x 1) when that pads N by at least N/8 less (s = 101: 112 columns, not 128)
-  const bool narrow = std::is_same<ACC, df64>::value && !d.conj_a && d.epi == 0;
+  const bool narrow = std::is_same<ACC, df64>::value && d.epi == 0 && (!d.conj_a || !bcplx);
   const bool tn1 = narrow && ((d.N + 31) / 32 * 32 - (d.N + 15) / 16 * 16) * 8 >= d.N;
   dim3 grid2((unsigned)((d.M + 63) / 64), (unsigned)((d.N + 31) / 32), (unsigned)d.splits);
   dim3 grid1((unsigned)((d.M + 63) / 64), (unsigned)((d.N + 15) / 16), (unsigned)d.splits);
-  if (d.conj_a)
+  if (d.conj_a && tn1)
+    qgemm_kernel<ACC, TA, TB, TC, true, false, false, 1><<<grid1, 256, 0, st>>>(d);
+  else if (d.conj_a && narrow)
+    qgemm_kernel<ACC, TA, TB, TC, true, false, false, 2><<<grid2, 256, 0, st>>>(d);
+  else if (d.conj_a)
     qgemm_kernel<ACC, TA, TB, TC, true><<<grid, 256, 0, st>>>(d);
   else if (tn1 && bcplx)
     qgemm_kernel<ACC, TA, TB, TC, false, true, false, 1><<<grid1, 256, 0, st>>>(d);
