@@ -16,6 +16,7 @@
 #include "qs_small.cuh"
 #include "qs_err_tc.cuh"
 #include "qs_householder.cuh"
+#include "qs_oz.cuh"
 #include "qs_sketch_tc.cuh"
 
 using namespace qs;
@@ -61,6 +62,8 @@ inline bool hx_f64(const qs_config& c) {
 }
 
 // Workspace layout; fills offsets of h (if non-null) and returns total bytes.
+constexpr size_t kOzBudget = (size_t)256 << 20;   // scratch cap of the sliced products
+
 size_t plan(const qs_config& c, qs_handle_s* h) {
   const size_t es = c.prec == QS_PREC_FP64 ? 8 : 4;
   const size_t ehx = hx_f64(c) ? 8 : 4;   // H, X, H_r, X_r
@@ -95,6 +98,16 @@ size_t plan(const qs_config& c, qs_handle_s* h) {
   // truncation stage: X* (n x s, FP64), H_r (m x s), X_r (s x n), sigma (s)
   size_t o_trunc = take(align_up(4 * n * s * 8) + align_up(4 * m * s * ehx) + align_up(4 * s * n * ehx) +
                         s * 8);
+  // sliced tensor-core products of the double-float stages with an FP32 tall operand
+  // (Y D, Y R^{-1}, W* Z*): slices of a row chunk of the tall operand and of the small one
+  int64_t oz_chunk = 0;
+  size_t oz_bytes = 0;
+  const int64_t kq_max = (int64_t)std::max(s, l);
+  if (c.prec != QS_PREC_FP64 && c.rf_prec != QS_RF_PREC_FP64 && oz_supported(kq_max, (int64_t)s)) {
+    oz_chunk = oz_chunk_rows((int64_t)std::max(m, n), kq_max, (int64_t)s, kOzBudget);
+    oz_bytes = oz_scratch_bytes(oz_chunk, kq_max, (int64_t)s);
+  }
+  size_t o_oz = take(oz_bytes);
   if (h) {
     h->esize = (int)es;
     h->hx_esize = (int)ehx;
@@ -103,6 +116,7 @@ size_t plan(const qs_config& c, qs_handle_s* h) {
     h->off_small = o_small; h->off_p = o_p; h->off_core = o_core; h->off_pack = o_pack;
     h->off_psvd = o_psvd; h->off_epack = o_epack; h->off_trunc = o_trunc; h->off_hh = o_hh;
     h->off_desc = o_desc;
+    h->off_oz = o_oz; h->oz_chunk = oz_chunk;
     h->off_tail = off; h->small_bytes = small_bytes; h->core_bytes = core_bytes;
     h->pack_bytes = pack_bytes;
   }
@@ -224,6 +238,31 @@ cudaError_t gemm_bcplx(const Ctx& x, const Mat& A, const Mat& B, const Mat& C, i
   return launch_qgemm(d, x.st);
 }
 
+// Sliced tensor-core product C = op(A) B (qs_oz.cu) for an FP32 tall operand under the
+// double-float stages: the workspace holds its scratch and the operands fit its sizes.
+bool oz_ok(const Ctx& x, const Mat& A, const Mat& B, const Mat& C, int64_t kq, int64_t nq) {
+  return x.h->oz_chunk > 0 && x.acc_hi() == 2 && !A.f64 && B.f64 && C.f64 && oz_supported(kq, nq);
+}
+cudaError_t oz_gemm(const Ctx& x, const Mat& A, bool conj_a, int64_t rows, int64_t kq, const Mat& B,
+                    int64_t nq, const Mat& C, bool ct) {
+  const void* ap[4];
+  const void* bp[4];
+  void* cp[4];
+  A.cplanes(ap);
+  B.cplanes(bp);
+  C.planes(cp);
+  const float* af[4];
+  const double* bd[4];
+  double* cd[4];
+  for (int p = 0; p < 4; ++p) {
+    af[p] = static_cast<const float*>(ap[p]);
+    bd[p] = static_cast<const double*>(bp[p]);
+    cd[p] = static_cast<double*>(cp[p]);
+  }
+  return launch_oz_gemm(af, A.ld, conj_a ? 1 : 0, rows, kq, bd, B.ld, nq, cd, C.ld, ct ? 1 : 0,
+                        x.h->ws + x.h->off_oz, x.h->oz_chunk, x.status(), x.st);
+}
+
 // Gram G = A* A of a tall m x s matrix (FP64 result).  complex_part: only the complex part
 // (planes w, x) is formed, the y, z planes are zero -- what a Cholesky-QR of the compact
 // complex form A_c needs (A_c* A_c is the complex part of A* A).
@@ -277,7 +316,10 @@ qs_status pseudo_qr(const Ctx& x, int ncorr) {
   QS_CU(launch_qconjT(Li.p, 1, Li.ld, Li.ps, D.p, 1, D.ld, D.ps, s, s, x.st));   // D = R^{-1}
   // second Cholesky-QR pass on T = Y R^{-1} restores orthogonality of the Q factor; R^{-1}
   // is complex (the y, z planes of D are zero), which the product exploits
-  QS_CU(gemm_bcplx(x, Y, D, T, x.m, s, s, x.acc_hi()));
+  if (oz_ok(x, Y, D, T, s, s))
+    QS_CU(oz_gemm(x, Y, false, x.m, s, D, s, T, false));
+  else
+    QS_CU(gemm_bcplx(x, Y, D, T, x.m, s, s, x.acc_hi()));
   QS_CU(gram(x, T, x.m, s, G));
   QS_CU(chol_inv(x, G, L, Li, 1, 0, 2.0 * x.m, -1, kDevRank | kDevStopCorr));
   QS_CU(launch_qconjT(Li.p, 1, Li.ld, Li.ps, R2.p, 1, R2.ld, R2.ps, s, s, x.st));
@@ -344,7 +386,10 @@ qs_status corrections(const Ctx& x, int ncorr, const Mat& B, Mat Dcur, Mat Dnext
   }
   // H = B D in the FP64 class: D carries the correction factors, whose norm times ||Y||
   // is far above 1/u32, so an FP32 product would tilt the range of H away from that of Y
-  QS_CU(gemm(x, B, false, Dcur, x.H(), x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
+  if (oz_ok(x, B, Dcur, x.H(), s, s))
+    QS_CU(oz_gemm(x, B, false, x.m, s, Dcur, s, x.H(), false));
+  else
+    QS_CU(gemm(x, B, false, Dcur, x.H(), x.m, s, s, 1.0, 0.0, x.acc_hi(), false));
   return QS_OK;
 }
 
@@ -382,6 +427,10 @@ qs_status core_solve(const Ctx& x) {
   // P^dagger (s x l), in the working precision of W; with an uncorrected H the norm of
   // P^dagger is kappa(H) times that of P, so it stays FP64 and X accumulates in double-float
   const bool wide = !x.mixed() || !x.h->h_well_conditioned;
+  if (wide && oz_ok(x, x.W(), ZT, x.X(), l, s)) {   // the same on the tensor cores
+    QS_CU(oz_gemm(x, x.W(), true, x.n, l, ZT, s, x.X(), true));
+    return QS_OK;
+  }
   if (wide && x.acc_hi() == 2) {
     // double-float: X* = W* (P^dagger)* as a tall product (n rows, s columns: 64 x 16 tiles,
     // no padding of s to 64 and about two full waves), stored conjugate-transposed into X

@@ -53,8 +53,11 @@ def _cfg(**kw):
 def test_workspace_bytes_and_validation(lib):
     good = lib.qsketch_workspace_bytes(ctypes.byref(_cfg()))
     assert good > 0 and good % 256 == 0
-    # FP32 modes store half-size objects
-    assert lib.qsketch_workspace_bytes(ctypes.byref(_cfg(prec=1))) < good
+    # FP32 storage with native-FP64 stages stores half-size objects; with the default
+    # double-float stages the workspace adds the scratch of the sliced tensor-core products
+    f32_fp64 = lib.qsketch_workspace_bytes(ctypes.byref(_cfg(prec=1, rf_prec=1)))
+    assert f32_fp64 < good
+    assert lib.qsketch_workspace_bytes(ctypes.byref(_cfg(prec=1))) > f32_fp64
     for bad in (dict(s=0), dict(l=4), dict(l=81), dict(m=0), dict(emb=2), dict(prec=9),
                 dict(flags=1), dict(pure=3), dict(s=2000, l=2000, m=5000, n=5000),
                 dict(rf_prec=3), dict(rf_prec=-1), dict(reserved=1)):
@@ -105,11 +108,15 @@ def test_test_flag_only_in_tensor_core_modes(lib):
 
 
 def test_rf_precision_sets_the_storage_of_h_and_x(lib):
-    """FP32-storage modes keep H and X in FP64 unless the stages after the sketch run mixed."""
+    """FP32-storage modes keep H and X in FP64 unless the stages after the sketch run mixed;
+    the double-float and mixed stages add the scratch of the sliced tensor-core products."""
     fp32_df = lib.qsketch_workspace_bytes(ctypes.byref(_cfg(prec=1, rf_prec=0)))
     fp32_64 = lib.qsketch_workspace_bytes(ctypes.byref(_cfg(prec=1, rf_prec=1)))
     fp32_mx = lib.qsketch_workspace_bytes(ctypes.byref(_cfg(prec=1, rf_prec=2)))
-    assert fp32_df == fp32_64 > fp32_mx > 0
+    m, n, s = 100, 80, 5
+    hx_fp32_saving = 4 * (m * s + s * n) * 4      # H and X in FP32 instead of FP64
+    assert fp32_df > fp32_64 > 0 and fp32_df > fp32_mx > 0
+    assert fp32_df - fp32_mx >= hx_fp32_saving - 2 * 256
 
 
 def test_static_error_binding_checks_shapes_before_any_launch(lib):
