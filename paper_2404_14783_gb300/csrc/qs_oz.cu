@@ -13,28 +13,39 @@
 // product (Sec. 2).
 // Slicing.  Row i of the real A is scaled by 2^-e_i (2^e_i > max |a_ik|) and cut into S = 8
 // slices of integers t_a in [-64, 64]: x = 2^e_i sum_a t_a 2^-6a (round to nearest at each
-// step, so |t_a| <= 32 for a > 1); column j of R(B) likewise with 2^f_j and u_b.  A slice
-// is exact in BF16.
+// step, so |t_a| <= 32 for a > 1); column j of R(B) likewise with 2^f_j and u_b.  Slice a is
+// stored as t_a 2^-6(a-1), exact in BF16, so that the product of slices a and b carries its
+// weight 2^-6(a+b-2) relative to the leading level.
 // Products.  For each level l = a + b = 2..9 the tensor cores accumulate
-//   sum_{a+b=l} T_a U_b   (FP32 in TMEM, one accumulator of 64 columns per level).
-// Its terms are integers; for l <= 5 the sum stays below 2^24 in magnitude for K <= 2048
-// (|t_1|, |u_1| <= 64, the other slices <= 32: at most 6144 K), so it is exact in FP32 in any
-// order; the levels
-// l >= 6 weigh 2^-24 of the leading one and more, so their FP32 rounding is far below the
-// double-float level.  Levels l > 9 (2^-42 and below, with the slicing remainder of 2^-48)
-// are dropped.  The epilogue forms C_ij = sum_l 2^(e_i + f_j - 6 l) level_l in double-float,
-// smallest level first.
+//   sum_{a+b=l} T_a U_b   (FP32 in TMEM, one accumulator of 64 columns per level, level l
+//   at column 64 (l - 2)).
+// The terms of a level are integers times one power of two; their sum stays below 2^24 in
+// magnitude for K <= 1536 (|t_1|, |u_1| <= 64, the other slices <= 32: at most 10240 K for
+// l = 9), so every level is exact in FP32 whatever the order and the rounding of the
+// accumulation (the tensor cores' FP32 accumulation is not rounded to nearest: one shared
+// accumulator for the levels 6..9 measured errors of 2e-12 that grew with K).  Levels l > 9
+// (2^-42 and below, with the slicing remainder of 2^-48) are dropped.  The epilogue forms
+// C_ij = 2^(e_i + f_j - 12) times the sum of the eight accumulators in double-float, smallest
+// first.
+// Stacked products.  The B slices of a stage lie one after another in shared memory and the
+// level accumulators one after another in TMEM, so for slice a of A one MMA with N = 64 n
+// computes T_a [U_1 .. U_n] into the accumulators of the levels a + 1 .. a + n: 12 MMAs
+// (N = 256, 192, 128 or 64) per K step of 16 instead of 36 with N = 64, the A operand read
+// once per stack.
 //
 // Kernels: oz_slice_b (R(B), K-major slices, column exponents), oz_rowexp and oz_slice_a
 // (row exponents, slices of A through a shared-memory transpose so that both the reads of A
 // or A* and the writes of the slices are coalesced), and oz_gemm_kernel:
-//   one CTA per 128 x 64 tile of the real C; 192 threads;
-//   warp 0   TMA producer: per K step of 16, the 8 slices of the A tile (128 x 16) and of
-//            the B tile (64 x 16), 32-byte swizzle, 48 KB per stage, 4 stages;
-//   warp 1   TMEM owner (512 columns: 8 levels x 64) and MMA issuer: 36 BF16 MMAs
-//            (M = 128, N = 64, K = 16) per stage, one per slice pair;
-//   warps 2-5 epilogue: TMEM -> registers, scaled double-float sums, FP64 store of the tile
-//            (through shared memory for row-major C; directly for the conjugate transpose).
+//   one CTA per 128 x 64 tile of the real C; 320 threads;
+//   warp 0   TMA producer: per K step of 32, the 8 slices of the A tile (128 x 32) and of
+//            the B tile (64 x 32), 64-byte rows and swizzle, 96 KB per stage, 2 stages;
+//   warp 1   TMEM owner (512 columns: 8 levels x 64) and MMA issuer: 2 x 12 stacked BF16
+//            MMAs (M = 128, K = 16) per stage;
+//   warps 2-9 epilogue (two per TMEM lane quarter, 32 columns each): TMEM -> registers, the
+//            accumulators summed in double-float, one exact power-of-two scale, FP64 by
+//            integer operations (a conversion on the FP64 pipe, 1/64 of the FP32 rate, cost
+//            more than the sums), store of the tile (through shared memory for row-major C;
+//            directly, coalesced, for the conjugate transpose).
 // Every wait is bounded (2 s of %globaltimer); on expiry the CTA records the timeout in the
 // status word, stops issuing work, waits (bounded) for its own copies and MMAs, frees TMEM
 // and returns.
@@ -58,13 +69,14 @@ using namespace tc;
 constexpr int kS = 8;                 // slices per operand
 constexpr int kBeta = 6;              // bits per slice
 constexpr int kLevMin = 2, kLevMax = 9;
-constexpr int kBM = 128, kBN = 64, kBK = 16;
-constexpr int kStages = 4;
-constexpr int kABox = kBM * kBK * 2;  // 4 KB
-constexpr int kBBox = kBN * kBK * 2;  // 2 KB
-constexpr int kStageBytes = kS * kABox + kS * kBBox;   // 48 KB
-constexpr int kThreads = 192;
-constexpr int kMaxK = 2048;           // real K (4 kq) with exact leading levels
+constexpr int kAcc = kLevMax - kLevMin + 1;   // one accumulator per level
+constexpr int kBM = 128, kBN = 64, kBK = 32;
+constexpr int kStages = 2;
+constexpr int kABox = kBM * kBK * 2;  // 8 KB (64-byte rows)
+constexpr int kBBox = kBN * kBK * 2;  // 4 KB
+constexpr int kStageBytes = kS * kABox + kS * kBBox;   // 96 KB
+constexpr int kThreads = 320;
+constexpr int kMaxK = 1536;           // real K (4 kq) with every level exact
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 // R(B): block (row plane pa, column plane q) = sign * B_plane   (Hamilton product, Sec. 2)
@@ -124,7 +136,8 @@ __global__ void __launch_bounds__(256) oz_slice_b_kernel(const double* b0, const
       y *= 64.0;
       const double t = rint(y);
       y -= t;
-      slices[((int64_t)b * np + j) * kp + c] = __float2bfloat16_rn((float)t);
+      // u_b 2^-6(b-1): exact in BF16 (an integer of at most 7 bits times a power of two)
+      slices[((int64_t)b * np + j) * kp + c] = __float2bfloat16_rn(ldexpf((float)t, -kBeta * b));
     }
   }
 }
@@ -135,14 +148,21 @@ __global__ void __launch_bounds__(256) oz_rowexp_kernel(const float* a0, const f
                                                         const float* a3, int64_t lda, int conj_a,
                                                         int64_t rows, int kq, int* __restrict__ eexp) {
   const float* A[4] = {a0, a1, a2, a3};
-  if (conj_a) {   // row i = column i of A: one thread per row (consecutive threads, consecutive i)
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= rows) return;
+  if (conj_a) {   // row i = column i of A: 32 consecutive i per warp (coalesced), 8 warps along k
+    __shared__ float red[8][32];
+    const int64_t i = blockIdx.x * (int64_t)32 + (threadIdx.x & 31);
+    const int kw = threadIdx.x >> 5;
     float mx = 0.f;
-    for (int p = 0; p < 4; ++p)
-      if (A[p])
-        for (int k = 0; k < kq; ++k) mx = fmaxf(mx, fabsf(A[p][(int64_t)k * lda + i]));
-    eexp[i] = exp_above_f(mx);
+    if (i < rows)
+      for (int p = 0; p < 4; ++p)
+        if (A[p])
+          for (int k = kw; k < kq; k += 8) mx = fmaxf(mx, fabsf(A[p][(int64_t)k * lda + i]));
+    red[kw][threadIdx.x & 31] = mx;
+    __syncthreads();
+    if (kw == 0 && i < rows) {
+      for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w][threadIdx.x & 31]);
+      eexp[i] = exp_above_f(mx);
+    }
   } else {        // one warp per row
     const int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -201,7 +221,7 @@ __global__ void __launch_bounds__(256) oz_slice_a_kernel(const float* a0, const 
       y *= 64.f;
       const float t = rintf(y);
       y -= t;
-      slices[((int64_t)a * mc + i) * kp + c] = __float2bfloat16_rn(t);
+      slices[((int64_t)a * mc + i) * kp + c] = __float2bfloat16_rn(ldexpf(t, -kBeta * a));   // t_a 2^-6(a-1)
     }
   }
 }
@@ -257,6 +277,42 @@ __device__ __forceinline__ df64 add_f(df64 acc, float v) {
   return df_fast_two_sum(s, __fadd_rn(acc.lo, err));
 }
 
+// hi + lo (a normalised double-float) as a double, rounded to nearest even, with integer
+// operations only.  The exponent of lo is at least 24 below that of hi, so lo's bits either
+// lie on the double's grid at hi's exponent or are rounded into it; a borrow (hi a power of
+// two, lo of the other sign) renormalises by a shift.
+__device__ __forceinline__ double df_to_double(float hi, float lo) {
+  const uint32_t hb = __float_as_uint(hi), lb = __float_as_uint(lo);
+  const int eh = (int)((hb >> 23) & 0xffu), el = (int)((lb >> 23) & 0xffu);
+  if (eh == 0 || eh == 255 || el == 255) return (double)hi + (double)lo;   // zero, subnormal, special
+  unsigned long long M = (unsigned long long)((hb & 0x7fffffu) | 0x800000u) << 29;
+  const unsigned long long ml = el ? (unsigned long long)((lb & 0x7fffffu) | 0x800000u)
+                                   : (unsigned long long)(lb & 0x7fffffu);
+  const int sh = (el ? el : 1) - eh + 29;   // lo's units relative to the double's at hi
+  unsigned long long L;
+  if (sh >= 0) {
+    L = ml << sh;
+  } else if (-sh >= 25) {
+    L = 0;   // below half a unit, never a tie (ml < 2^24)
+  } else {
+    const int d = -sh;
+    L = ml >> d;
+    const unsigned long long rem = ml & ((1ull << d) - 1ull), half = 1ull << (d - 1);
+    if (rem > half || (rem == half && (L & 1ull))) ++L;
+  }
+  M = ((lb ^ hb) >> 31) ? M - L : M + L;
+  int e = eh - 127 + 1023;
+  if (M >> 53) {   // carry (only if lo were not normalised)
+    M >>= 1;
+    ++e;
+  }
+  const int lz = __clzll((long long)M) - 11;   // borrow: renormalise
+  M <<= lz;
+  e -= lz;
+  return __longlong_as_double((long long)(((unsigned long long)(hb >> 31) << 63) |
+                                          ((unsigned long long)e << 52) | (M & 0xfffffffffffffull)));
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
                    const OzParams p) {
@@ -289,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      uint32_t uses[kStages] = {0, 0, 0, 0};
+      uint32_t uses[kStages] = {0, 0};
       int slot = 0;
       for (int ks = 0; ks < p.ksteps && !sh->abort; ++ks) {
         if (uses[slot] > 0 && !oz_wait(&sh->empty[slot], (uses[slot] - 1) & 1, sh, p.status)) break;
@@ -308,22 +364,27 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      uint32_t uses[kStages] = {0, 0, 0, 0};
+      uint32_t uses[kStages] = {0, 0};
       int slot = 0;
       const uint32_t r_base = smem_u32(sRing);
-      const uint32_t idesc = idesc_bf16(kBM, kBN, 0, 0);
       for (int ks = 0; ks < p.ksteps && !sh->abort; ++ks) {
         if (!oz_wait(&sh->full[slot], uses[slot] & 1, sh, p.status)) break;
         tc_fence_after();
         const uint32_t stage = r_base + slot * kStageBytes;
-        for (int lev = kLevMin; lev <= kLevMax; ++lev) {
-          const uint32_t d = tmem + (uint32_t)((lev - kLevMin) * kBN);
-          const int a_lo = max(1, lev - kS), a_hi = min(kS, lev - 1);
-          for (int a = a_lo; a <= a_hi; ++a) {
-            const int b = lev - a;
-            const uint64_t ad = sdesc(stage + (a - 1) * kABox, 16, 256, kSw32);
-            const uint64_t bd = sdesc(stage + kS * kABox + (b - 1) * kBBox, 16, 256, kSw32);
-            umma(d, ad, bd, idesc, (ks > 0 || a > a_lo) ? 1u : 0u);
+        // slice a of A times the stacked slices b = b0 .. b0 + n - 1 of B (n <= 4: N <= 256)
+        // into the accumulators of the levels a + b0 .. a + b0 + n - 1; every level's first
+        // MMA comes from a = 1
+        for (int a = 1; a <= kS; ++a) {
+          const int nb = kLevMax - a;   // b = 1 .. nb
+          const uint64_t ad = sdesc(stage + (a - 1) * kABox, 16, 512, kSw64);
+          for (int b0 = 1; b0 <= nb; b0 += 4) {
+            const int n = min(4, nb - b0 + 1);
+            const uint32_t d = tmem + (uint32_t)((a + b0 - kLevMin) * kBN);
+            const uint64_t bd = sdesc(stage + kS * kABox + (b0 - 1) * kBBox, 16, 512, kSw64);
+            const uint32_t idesc = idesc_bf16(kBM, kBN * n, 0, 0);
+            const uint32_t acc = (ks > 0 || a > 1) ? 1u : 0u;
+            umma(d, ad, bd, idesc, acc);
+            umma(d, ad + 2, bd + 2, idesc, 1u);   // second K half: 32 B further along K
           }
         }
         umma_commit(&sh->empty[slot]);
@@ -334,52 +395,62 @@ __global__ void __launch_bounds__(kThreads, 1)
       oz_wait(&sh->done, 0, sh, p.status, true);
     }
   } else {
-    // ------------------------------------------------------------ epilogue (warps 2-5)
-    const int lq = warp & 3;          // TMEM lane quarter of this warp
+    // ------------------------------------------------------------ epilogue (warps 2-9)
+    // two warps per TMEM lane quarter (TMEM lanes 32 (warp mod 4) ..), one column half each
+    const int lq = warp & 3, ch = (warp - 2) >> 2;
     const int r = lq * 32 + lane;     // row within the tile
     const int64_t i = (int64_t)ti * kBM + r;
     const bool row_ok = i < p.rows;
     const int er = row_ok ? p.eexp[i] : 0;
+    constexpr int kC = kBN / 2;       // columns of this thread
+    const uint32_t trow = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(ch * kC);
     if (oz_wait(&sh->done, 0, sh, p.status)) {
       tc_fence_after();
-      df64 acc[kBN];
+      // the level accumulators, smallest first, in double-float; each holds its weight
+      // relative to the leading level (pre-scaled slices)
+      df64 acc[kC];
 #pragma unroll
-      for (int cc = 0; cc < kBN; ++cc) acc[cc] = df64(0.f, 0.f);
-      for (int lev = kLevMax; lev >= kLevMin; --lev) {   // smallest weights first
+      for (int c = 0; c < kC; ++c) acc[c] = df64(0.f, 0.f);
+      for (int ai = kAcc - 1; ai >= 0; --ai) {
 #pragma unroll
-        for (int c16 = 0; c16 < kBN; c16 += 16) {
+        for (int c16 = 0; c16 < kC; c16 += 16) {
           float v[16];
-          tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)((lev - kLevMin) * kBN + c16), v);
+          tmem_ld16(trow + (uint32_t)(ai * kBN + c16), v);
 #pragma unroll
-          for (int u = 0; u < 16; ++u)
-            acc[c16 + u] = add_f(acc[c16 + u], scale2(v[u], er + sh->fcol[c16 + u] - kBeta * lev));
+          for (int u = 0; u < 16; ++u) acc[c16 + u] = add_f(acc[c16 + u], v[u]);
         }
+      }
+      // C_ij = acc 2^(e_i + f_j - 6 kLevMin), exact scaling, then FP64 without the FP64 pipe
+      double val[kC];
+#pragma unroll
+      for (int c = 0; c < kC; ++c) {
+        const int k = er + sh->fcol[ch * kC + c] - kBeta * kLevMin;
+        val[c] = df_to_double(scale2(acc[c].hi, k), scale2(acc[c].lo, k));
       }
       if (p.ct) {
         // conjugate transpose: C_q[jj][i], lanes along i (coalesced)
 #pragma unroll
-        for (int cc = 0; cc < kBN; ++cc) {
-          const int jg = tj * kBN + cc;
+        for (int c = 0; c < kC; ++c) {
+          const int jg = tj * kBN + ch * kC + c;
           if (!row_ok || jg >= p.nv) continue;
           const int q = jg / p.nq, jj = jg % p.nq;
-          const double v = (double)acc[cc].hi + (double)acc[cc].lo;
-          p.c[q][(int64_t)jj * p.ldc + i] = q ? -v : v;
+          p.c[q][(int64_t)jj * p.ldc + i] = q ? -val[c] : val[c];
         }
       } else {
-        // row-major: stage the warp's 32 rows in shared memory (the operand ring is free once
-        // the last MMA completed), then write each row along its columns
-        double* stg = reinterpret_cast<double*>(sRing) + lq * 32 * (kBN + 1);
+        // row-major: stage the warp's 32 rows x 32 columns in shared memory (the operand
+        // ring is free once the last MMA completed), then write each row along its columns
+        double* stg = reinterpret_cast<double*>(sRing) + (warp - 2) * 32 * (kC + 1);
 #pragma unroll
-        for (int cc = 0; cc < kBN; ++cc) stg[lane * (kBN + 1) + cc] = (double)acc[cc].hi + (double)acc[cc].lo;
+        for (int c = 0; c < kC; ++c) stg[lane * (kC + 1) + c] = val[c];
         __syncwarp();
-        for (int rr = 0; rr < 32; ++rr) {
-          const int64_t ir = (int64_t)ti * kBM + lq * 32 + rr;
-          if (ir >= p.rows) break;
-          for (int cc = lane; cc < kBN; cc += 32) {
-            const int jg = tj * kBN + cc;
-            if (jg >= p.nv) continue;
-            const int q = jg / p.nq, jj = jg % p.nq;
-            p.c[q][ir * p.ldc + jj] = stg[rr * (kBN + 1) + cc];
+        for (int c = lane; c < kC; c += 32) {
+          const int jg = tj * kBN + ch * kC + c;
+          if (jg >= p.nv) continue;
+          const int q = jg / p.nq, jj = jg % p.nq;
+          for (int rr = 0; rr < 32; ++rr) {
+            const int64_t ir = (int64_t)ti * kBM + lq * 32 + rr;
+            if (ir >= p.rows) break;
+            p.c[q][ir * p.ldc + jj] = stg[rr * (kC + 1) + c];
           }
         }
       }
@@ -401,7 +472,7 @@ struct OzGeom {
 };
 OzGeom oz_geom(int64_t chunk_rows, int64_t kq, int64_t nq) {
   OzGeom g;
-  g.kp = rup(4 * kq, kBK);
+  g.kp = rup(4 * kq, kBK);   // K steps of 32 (64-byte box rows)
   g.np = rup(4 * nq, kBN);
   g.mc = rup(std::max<int64_t>(chunk_rows, 1), kBM);
   g.a_bytes = (size_t)rup((int64_t)kS * g.mc * g.kp * 2, 256);
@@ -452,10 +523,10 @@ cudaError_t launch_oz_gemm(const float* const A[4], int64_t lda, int conj_a, int
   }
   CUtensorMap tA, tB;
   if (!make_map(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, sa, (uint64_t)g.kp, (uint64_t)(kS * g.mc),
-                (uint64_t)g.kp, kBK, kBM, CU_TENSOR_MAP_SWIZZLE_32B))
+                (uint64_t)g.kp, kBK, kBM, CU_TENSOR_MAP_SWIZZLE_64B))
     return cudaErrorInvalidValue;
   if (!make_map(&tB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, sb, (uint64_t)g.kp, (uint64_t)(kS * g.np),
-                (uint64_t)g.kp, kBK, kBN, CU_TENSOR_MAP_SWIZZLE_32B))
+                (uint64_t)g.kp, kBK, kBN, CU_TENSOR_MAP_SWIZZLE_64B))
     return cudaErrorInvalidValue;
 
   oz_slice_b_kernel<<<(unsigned)g.np, 256, 0, st>>>(B[0], B[1], B[2], B[3], ldb, (int)kq, (int)nq, (int)g.kp,
@@ -468,14 +539,14 @@ cudaError_t launch_oz_gemm(const float* const A[4], int64_t lda, int conj_a, int
     const float* Ac[4];
     for (int p = 0; p < 4; ++p) Ac[p] = A[p] ? A[p] + (conj_a ? r0 : r0 * lda) : nullptr;
     if (conj_a)
-      oz_rowexp_kernel<<<(unsigned)((rc + 255) / 256), 256, 0, st>>>(Ac[0], Ac[1], Ac[2], Ac[3], lda, 1, rc,
+      oz_rowexp_kernel<<<(unsigned)((rc + 31) / 32), 256, 0, st>>>(Ac[0], Ac[1], Ac[2], Ac[3], lda, 1, rc,
                                                                        (int)kq, ea);
     else
       oz_rowexp_kernel<<<(unsigned)((rc + 7) / 8), 256, 0, st>>>(Ac[0], Ac[1], Ac[2], Ac[3], lda, 0, rc,
                                                                   (int)kq, ea);
     count_launch();
     const int64_t mt = rup(rc, kBM);
-    oz_slice_a_kernel<<<dim3((unsigned)(g.kp / 32 + (g.kp % 32 ? 1 : 0)), (unsigned)(mt / 32)), dim3(32, 8), 0,
+    oz_slice_a_kernel<<<dim3((unsigned)(g.kp / 32), (unsigned)(mt / 32)), dim3(32, 8), 0,
                         st>>>(Ac[0], Ac[1], Ac[2], Ac[3], lda, conj_a, rc, (int)kq, (int)g.kp, g.mc, ea, sa);
     count_launch();
     OzParams prm{};
