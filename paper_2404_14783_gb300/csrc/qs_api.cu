@@ -62,7 +62,7 @@ inline bool hx_f64(const qs_config& c) {
 }
 
 // Workspace layout; fills offsets of h (if non-null) and returns total bytes.
-constexpr size_t kOzBudget = (size_t)256 << 20;   // scratch cap of the sliced products
+constexpr size_t kOzBudget = (size_t)512 << 20;   // scratch cap of the sliced products
 
 size_t plan(const qs_config& c, qs_handle_s* h) {
   const size_t es = c.prec == QS_PREC_FP64 ? 8 : 4;
@@ -106,6 +106,11 @@ size_t plan(const qs_config& c, qs_handle_s* h) {
   if (c.prec != QS_PREC_FP64 && c.rf_prec != QS_RF_PREC_FP64 && oz_supported(kq_max, (int64_t)s)) {
     oz_chunk = oz_chunk_rows((int64_t)std::max(m, n), kq_max, (int64_t)s, kOzBudget);
     oz_bytes = oz_scratch_bytes(oz_chunk, kq_max, (int64_t)s);
+    // the long-K products (Psi H, the Gram of an FP64 tall matrix), the whole K at once
+    // when it fits the cap
+    const size_t split = std::max(oz_splitk_bytes((int64_t)l, (int64_t)m, (int64_t)s),
+                                  oz_splitk_bytes((int64_t)s, (int64_t)m, (int64_t)s));
+    oz_bytes = std::max(oz_bytes, std::min(split, kOzBudget));
   }
   size_t o_oz = take(oz_bytes);
   if (h) {
@@ -116,7 +121,7 @@ size_t plan(const qs_config& c, qs_handle_s* h) {
     h->off_small = o_small; h->off_p = o_p; h->off_core = o_core; h->off_pack = o_pack;
     h->off_psvd = o_psvd; h->off_epack = o_epack; h->off_trunc = o_trunc; h->off_hh = o_hh;
     h->off_desc = o_desc;
-    h->off_oz = o_oz; h->oz_chunk = oz_chunk;
+    h->off_oz = o_oz; h->oz_chunk = oz_chunk; h->oz_bytes = oz_bytes;
     h->off_tail = off; h->small_bytes = small_bytes; h->core_bytes = core_bytes;
     h->pack_bytes = pack_bytes;
   }
@@ -263,11 +268,39 @@ cudaError_t oz_gemm(const Ctx& x, const Mat& A, bool conj_a, int64_t rows, int64
                         x.h->ws + x.h->off_oz, x.h->oz_chunk, x.status(), x.st);
 }
 
+// Split-K form of the sliced product for a long K (Psi H, the Gram T* T): the double-float
+// stages, FP64 B and C, op(A) short enough for one row chunk.
+constexpr int64_t kOzMinK = 1024;   // below this K the SIMT products are as fast
+bool oz_split_ok(const Ctx& x, int64_t rows, int64_t kq, int64_t nq, const Mat& B, const Mat& C) {
+  return x.h->oz_chunk > 0 && x.acc_hi() == 2 && kq >= kOzMinK && B.f64 && C.f64 &&
+         oz_splitk_supported(rows, nq, x.h->oz_bytes);
+}
+cudaError_t oz_gemm_splitk(const Ctx& x, const Mat& A, bool conj_a, int64_t rows, int64_t kq, const Mat& B,
+                           int64_t nq, const Mat& C) {
+  const void* ap[4];
+  const void* bp[4];
+  void* cp[4];
+  A.cplanes(ap);
+  B.cplanes(bp);
+  C.planes(cp);
+  const double* bd[4];
+  double* cd[4];
+  for (int p = 0; p < 4; ++p) {
+    bd[p] = static_cast<const double*>(bp[p]);
+    cd[p] = static_cast<double*>(cp[p]);
+  }
+  return launch_oz_gemm_splitk(ap, A.f64, A.ld, conj_a ? 1 : 0, rows, kq, bd, B.ld, nq, cd, C.ld,
+                               x.h->ws + x.h->off_oz, x.h->oz_bytes, x.status(), x.st);
+}
+
 // Gram G = A* A of a tall m x s matrix (FP64 result).  complex_part: only the complex part
 // (planes w, x) is formed, the y, z planes are zero -- what a Cholesky-QR of the compact
 // complex form A_c needs (A_c* A_c is the complex part of A* A).
 cudaError_t gram(const Ctx& x, const Mat& A, int64_t rows, int64_t cols, const Mat& G,
                  const double* gate = nullptr, double gate_skip = 0.0, bool complex_part = false) {
+  // an FP64 tall matrix under the double-float stages: the whole Gram on the tensor cores
+  if (!gate && !complex_part && A.f64 && oz_split_ok(x, cols, rows, cols, A, G))
+    return oz_gemm_splitk(x, A, true, cols, rows, A, cols, G);
   if (!is_small(cols, cols))
     return gemm(x, A, true, A, G, cols, cols, rows, 1.0, 0.0, x.acc_hi(), true, gate, gate_skip);
   // Hermitian: tiles on and above the diagonal, then the mirror
@@ -405,7 +438,10 @@ qs_status core_solve(const Ctx& x) {
   // pseudo-SVD) kappa(P) is small and an FP32 product, widened for the small solve, keeps
   // the FP32 level of the sketch; an uncorrected pseudo-QR H has kappa(Y), which would
   // amplify the FP32 rounding of P into X, so that product accumulates in double-float.
-  if (!x.mixed() || !x.h->h_well_conditioned) {
+  if (!x.psi().f64 && oz_split_ok(x, l, x.m, s, x.H(), P) &&
+      (!x.mixed() || !x.h->h_well_conditioned)) {
+    QS_CU(oz_gemm_splitk(x, x.psi(), false, l, x.m, x.H(), s, P));   // on the tensor cores
+  } else if (!x.mixed() || !x.h->h_well_conditioned) {
     QS_CU(gemm(x, x.psi(), false, x.H(), P, l, s, x.m, 1.0, 0.0, x.acc_hi(), true));
   } else {
     const Mat P32{x.core(0).p, s, l * s, 0};

@@ -90,6 +90,7 @@ struct qs_handle_s {
   size_t off_gram, off_small, off_p, off_core, off_pack, off_psvd, off_epack, off_trunc, off_hh, off_desc, off_tail;
   size_t off_oz;       // scratch of the sliced tensor-core products (qs_oz.cu)
   int64_t oz_chunk;    // their row chunk (0: not planned, the SIMT products run)
+  size_t oz_bytes;     // their scratch bytes
   size_t small_bytes, core_bytes, pack_bytes;
   // 0 after a pseudo-QR without corrections (H inherits kappa(Y)); the core solve then
   // forms Psi H in the FP64 class in the FP32 modes

@@ -77,6 +77,7 @@ constexpr int kBBox = kBN * kBK * 2;  // 4 KB
 constexpr int kStageBytes = kS * kABox + kS * kBBox;   // 96 KB
 constexpr int kThreads = 320;
 constexpr int kMaxK = 1536;           // real K (4 kq) with every level exact
+constexpr int64_t kMaxSplitRows = 4096;   // rows of op(A) in the split-K form (one row chunk)
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 // R(B): block (row plane pa, column plane q) = sign * B_plane   (Hamilton product, Sec. 2)
@@ -85,125 +86,173 @@ __constant__ int8_t kRSign[4][4] = {{1, 1, 1, 1}, {-1, 1, -1, 1}, {-1, 1, 1, -1}
 
 __host__ __device__ inline int64_t rup(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
-// Exponent e with 2^(e-1) <= |x| < 2^e (0 for x = 0).
-__device__ __forceinline__ int exp_above(double x) {
-  int e;
-  frexp(x, &e);
-  return x == 0.0 ? 0 : e;
+
+// FP64 values are sliced with integer operations on their bit patterns (the FP64 pipe runs
+// at 1/64 of the FP32 rate, which made the slicing of a tall FP64 operand cost more than its
+// product).
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
 }
-__device__ __forceinline__ int exp_above_f(float x) {
-  int e;
-  frexpf(x, &e);
-  return x == 0.f ? 0 : e;
+// frexp exponent of the value with these absolute bits (0 for zero and subnormals)
+__device__ __forceinline__ int exp_of_bits(unsigned long long ab) {
+  const int E = (int)(ab >> 52);
+  return E == 0 ? 0 : E - 1022;
+}
+// Digits t_1..t_S of y = v 2^-e (|y| < 1): Y = y 2^48 rounded to an integer, then
+// t_a = Y / 2^(48 - 6a) rounded (half up) with the remainder carried on, so |t_1| <= 64 and
+// |t_a| <= 32 after; the part of y below 2^-48 is dropped (the slicing remainder).
+__device__ __forceinline__ void digits_d(double v, int e, int* t) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7ff);
+  long long Y = 0;
+  if (E != 0) {   // zero and subnormals give 0
+    const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = 1027 + e - E;   // Y = M 2^-sh, sh > 4 because |y| < 1
+    if (sh < 63) Y = (long long)((M + (1ull << (sh - 1))) >> sh);
+    if (b >> 63) Y = -Y;
+  }
+#pragma unroll
+  for (int a = 1; a <= kS; ++a) {
+    const int shift = 48 - kBeta * a;
+    const long long ta = shift > 0 ? (Y + (1ll << (shift - 1))) >> shift : Y;
+    Y -= ta << shift;
+    t[a - 1] = (int)ta;
+  }
+}
+__device__ __forceinline__ void digits(double v, int e, int* t) { digits_d(v, e, t); }
+// FP32 values: the same digits in FP32 arithmetic (exact: y has 24 significant bits)
+__device__ __forceinline__ void digits(float v, int e, int* t) {
+  float y = ldexpf(v, -e);
+#pragma unroll
+  for (int a = 0; a < kS; ++a) {
+    y *= 64.f;
+    const float r = rintf(y);
+    y -= r;
+    t[a] = (int)r;
+  }
+}
+__device__ __forceinline__ __nv_bfloat16 slice_bf16(int t, int a0) {   // t 2^-6 a0, exact
+  return __float2bfloat16_rn(ldexpf((float)t, -kBeta * a0));
 }
 
 // ------------------------------------------------------------------------ slicing of R(B)
-// One CTA per column j of R(B) (np rows of the K-major slices; j >= 4 nq are zero).
-__global__ void __launch_bounds__(256) oz_slice_b_kernel(const double* b0, const double* b1, const double* b2,
-                                                         const double* b3, int64_t ldb, int kq, int nq, int kp,
-                                                         __nv_bfloat16* __restrict__ slices, int np,
-                                                         int* __restrict__ fexp) {
+// Column exponents of R(B): one CTA per column j (np of them; j >= 4 nq get 0), the maximum
+// over all 4 kq rows.
+__device__ __forceinline__ double rb_val(const double* const* B, int64_t ldb, int kq, int nq, int j, int c) {
+  if (j >= 4 * nq || c >= 4 * kq) return 0.0;
+  const int q = j / nq, jj = j % nq, pa = c / kq, k = c % kq;
+  const double* src = B[kRPlane[pa][q]];
+  return src ? kRSign[pa][q] * src[(int64_t)k * ldb + jj] : 0.0;
+}
+__global__ void __launch_bounds__(256) oz_colexp_kernel(const double* b0, const double* b1, const double* b2,
+                                                        const double* b3, int64_t ldb, int kq, int nq,
+                                                        int* __restrict__ fexp) {
   const double* B[4] = {b0, b1, b2, b3};
-  const int j = blockIdx.x, kr = 4 * kq;
-  const bool live = j < 4 * nq;
-  const int q = live ? j / nq : 0, jj = live ? j % nq : 0;
-  __shared__ double red[8];
-  __shared__ int f_s;
-  auto val = [&](int c) -> double {
-    if (!live || c >= kr) return 0.0;
-    const int pa = c / kq, k = c % kq;
-    const double* src = B[kRPlane[pa][q]];
-    return src ? kRSign[pa][q] * src[(int64_t)k * ldb + jj] : 0.0;
-  };
-  double mx = 0.0;
-  for (int c = threadIdx.x; c < kr; c += blockDim.x) mx = fmax(mx, fabs(val(c)));
+  const int j = blockIdx.x;
+  __shared__ unsigned long long red[8];
+  unsigned long long mx = 0;
+  for (int c = threadIdx.x; c < 4 * kq; c += blockDim.x) mx = max(mx, abs_bits(rb_val(B, ldb, kq, nq, j, c)));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-    f_s = exp_above(m);
-    fexp[j] = f_s;
+    unsigned long long m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[w]);
+    fexp[j] = exp_of_bits(m);
   }
-  __syncthreads();
-  const int f = f_s;
-  for (int c = threadIdx.x; c < kp; c += blockDim.x) {
-    double y = ldexp(val(c), -f);
+}
+// Slices of the columns c0 .. c0 + kw - 1 of R(B) (K-major: row j of slice b holds column j;
+// zero past 4 kq).  One CTA per column j.
+__global__ void __launch_bounds__(256) oz_slice_b_kernel(const double* b0, const double* b1, const double* b2,
+                                                         const double* b3, int64_t ldb, int kq, int nq, int c0,
+                                                         int kw, const int* __restrict__ fexp,
+                                                         __nv_bfloat16* __restrict__ slices, int np) {
+  const double* B[4] = {b0, b1, b2, b3};
+  const int j = blockIdx.x, f = fexp[j];
+  for (int c = threadIdx.x; c < kw; c += blockDim.x) {
+    int t[kS];
+    digits_d(rb_val(B, ldb, kq, nq, j, c0 + c), f, t);
 #pragma unroll
-    for (int b = 0; b < kS; ++b) {
-      y *= 64.0;
-      const double t = rint(y);
-      y -= t;
-      // u_b 2^-6(b-1): exact in BF16 (an integer of at most 7 bits times a power of two)
-      slices[((int64_t)b * np + j) * kp + c] = __float2bfloat16_rn(ldexpf((float)t, -kBeta * b));
-    }
+    for (int b = 0; b < kS; ++b)   // u_b 2^-6(b-1): exact in BF16
+      slices[((int64_t)b * np + j) * kw + c] = slice_bf16(t[b], b);
   }
 }
 
 // ------------------------------------------------------------------------ slicing of A
-// Row exponents of the real op(A) for rows r0 .. r0 + rows - 1 (chunk-local index).
-__global__ void __launch_bounds__(256) oz_rowexp_kernel(const float* a0, const float* a1, const float* a2,
-                                                        const float* a3, int64_t lda, int conj_a,
-                                                        int64_t rows, int kq, int* __restrict__ eexp) {
-  const float* A[4] = {a0, a1, a2, a3};
+
+// Row exponents of the real op(A) (A in FP32 or FP64) over all 4 kq columns.
+__device__ __forceinline__ unsigned long long mag(double v) { return abs_bits(v); }
+__device__ __forceinline__ unsigned long long mag(float v) {   // as the bits of the same double
+  const unsigned fb = __float_as_uint(v) & 0x7fffffffu, ef = fb >> 23;
+  return ef == 0u ? 0ull
+                  : ((unsigned long long)(ef - 127u + 1023u) << 52) | ((unsigned long long)(fb & 0x7fffffu) << 29);
+}
+template <typename TA>
+__global__ void __launch_bounds__(256) oz_rowexp_kernel(const TA* a0, const TA* a1, const TA* a2, const TA* a3,
+                                                        int64_t lda, int conj_a, int64_t rows, int kq,
+                                                        int* __restrict__ eexp) {
+  const TA* A[4] = {a0, a1, a2, a3};
   if (conj_a) {   // row i = column i of A: 32 consecutive i per warp (coalesced), 8 warps along k
-    __shared__ float red[8][32];
+    __shared__ TA red[8][32];
     const int64_t i = blockIdx.x * (int64_t)32 + (threadIdx.x & 31);
     const int kw = threadIdx.x >> 5;
-    float mx = 0.f;
+    TA mx = TA(0);
     if (i < rows)
       for (int p = 0; p < 4; ++p)
         if (A[p])
-          for (int k = kw; k < kq; k += 8) mx = fmaxf(mx, fabsf(A[p][(int64_t)k * lda + i]));
+          for (int k = kw; k < kq; k += 8) {
+            const TA v = fabs(A[p][(int64_t)k * lda + i]);
+            mx = v > mx ? v : mx;   // compare, not the FP64 fmax
+          }
     red[kw][threadIdx.x & 31] = mx;
     __syncthreads();
     if (kw == 0 && i < rows) {
-      for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w][threadIdx.x & 31]);
-      eexp[i] = exp_above_f(mx);
+      for (int w = 1; w < 8; ++w) mx = red[w][threadIdx.x & 31] > mx ? red[w][threadIdx.x & 31] : mx;
+      eexp[i] = exp_of_bits(mag(mx));
     }
   } else {        // one warp per row
     const int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= rows) return;
-    float mx = 0.f;
+    unsigned long long mx = 0;
     for (int p = 0; p < 4; ++p)
       if (A[p])
-        for (int k = lane; k < kq; k += 32) mx = fmaxf(mx, fabsf(A[p][i * lda + k]));
+        for (int k = lane; k < kq; k += 32) mx = max(mx, mag(A[p][i * lda + k]));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) eexp[i] = exp_above_f(mx);
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) eexp[i] = exp_of_bits(mx);
   }
 }
 
-// Slices of the real op(A) (chunk rows x kp columns, K-major, zero padded to mc rows), one
-// 32 x 32 tile per CTA of 32 x 8 threads: the tile is read in the layout of A (row-major A:
-// along k; A*: along i), transposed in shared memory, and written along the columns.
-__global__ void __launch_bounds__(256) oz_slice_a_kernel(const float* a0, const float* a1, const float* a2,
-                                                         const float* a3, int64_t lda, int conj_a,
-                                                         int64_t rows, int kq, int kp, int64_t mc,
-                                                         const int* __restrict__ eexp,
+// Slices of the columns c0 .. c0 + kw - 1 of the real op(A) (rows x kw, K-major, zero padded
+// to mc rows and past 4 kq), one 32 x 32 tile per CTA of 32 x 8 threads: the tile is read in
+// the layout of A (row-major A: along k; A*: along i), transposed in shared memory, and
+// written along the columns.  The slicing steps are exact in the type of A.
+template <typename TA>
+__global__ void __launch_bounds__(256) oz_slice_a_kernel(const TA* a0, const TA* a1, const TA* a2, const TA* a3,
+                                                         int64_t lda, int conj_a, int64_t rows, int kq, int c0,
+                                                         int kw, int64_t mc, const int* __restrict__ eexp,
                                                          __nv_bfloat16* __restrict__ slices) {
-  const float* A[4] = {a0, a1, a2, a3};
-  __shared__ float tile[32][33];
+  const TA* A[4] = {a0, a1, a2, a3};
+  __shared__ TA tile[32][33];
   const int64_t i0 = (int64_t)blockIdx.y * 32;
-  const int c0 = blockIdx.x * 32, tx = threadIdx.x, ty = threadIdx.y, kr = 4 * kq;
+  const int cb = blockIdx.x * 32, tx = threadIdx.x, ty = threadIdx.y, kr = 4 * kq;
   // column c of the real A: plane c / kq, index c % kq; A* negates the planes x, y, z
   for (int u = ty; u < 32; u += 8) {
-    float v = 0.f;
+    TA v = TA(0);
     if (conj_a) {   // lanes along i
       const int64_t i = i0 + tx;
-      const int c = c0 + u;
-      if (i < rows && c < kr) {
+      const int c = c0 + cb + u;
+      if (i < rows && c < kr && cb + u < kw) {
         const int p = c / kq, k = c % kq;
-        if (A[p]) v = (p ? -1.f : 1.f) * A[p][(int64_t)k * lda + i];
+        if (A[p]) v = (p ? TA(-1) : TA(1)) * A[p][(int64_t)k * lda + i];
       }
       tile[tx][u] = v;
     } else {        // lanes along k
       const int64_t i = i0 + u;
-      const int c = c0 + tx;
-      if (i < rows && c < kr) {
+      const int c = c0 + cb + tx;
+      if (i < rows && c < kr && cb + tx < kw) {
         const int p = c / kq, k = c % kq;
         if (A[p]) v = A[p][i * lda + k];
       }
@@ -213,23 +262,135 @@ __global__ void __launch_bounds__(256) oz_slice_a_kernel(const float* a0, const 
   __syncthreads();
   for (int u = ty; u < 32; u += 8) {
     const int64_t i = i0 + u;
-    const int c = c0 + tx;
-    if (i >= mc || c >= kp) continue;
-    float y = (i < rows) ? ldexpf(tile[u][tx], -eexp[i]) : 0.f;
+    const int c = cb + tx;
+    if (i >= mc || c >= kw) continue;
+    int t[kS];
+    if (i < rows) {
+      digits(tile[u][tx], eexp[i], t);
+    } else {
 #pragma unroll
-    for (int a = 0; a < kS; ++a) {
-      y *= 64.f;
-      const float t = rintf(y);
-      y -= t;
-      slices[((int64_t)a * mc + i) * kp + c] = __float2bfloat16_rn(ldexpf(t, -kBeta * a));   // t_a 2^-6(a-1)
+      for (int a = 0; a < kS; ++a) t[a] = 0;
     }
+#pragma unroll
+    for (int a = 0; a < kS; ++a)   // t_a 2^-6(a-1)
+      slices[((int64_t)a * mc + i) * kw + c] = slice_bf16(t[a], a);
+  }
+}
+
+// ------------------------------------------------------------------------ long-K forms
+// Row exponents of op(A) for a long K: each CTA takes the maxima of a K range and raises
+// eexp[i] (cleared to a large negative value first) by atomicMax.
+template <typename TA>
+__global__ void __launch_bounds__(256) oz_rowexp_long_kernel(const TA* a0, const TA* a1, const TA* a2, const TA* a3,
+                                                             int64_t lda, int conj_a, int64_t rows, int kq, int kchunk,
+                                                             int* __restrict__ eexp) {
+  const TA* A[4] = {a0, a1, a2, a3};
+  __shared__ unsigned long long red[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int k0 = blockIdx.y * kchunk, k1 = min(kq, k0 + kchunk);
+  if (conj_a) {   // 32 consecutive rows i (columns of A, coalesced) x 8 lanes along k
+    const int64_t i = blockIdx.x * (int64_t)32 + tx;
+    unsigned long long mx = 0;
+    if (i < rows)
+      for (int p = 0; p < 4; ++p)
+        if (A[p])
+          for (int k = k0 + ty; k < k1; k += 8) mx = max(mx, mag(A[p][(int64_t)k * lda + i]));
+    red[ty][tx] = mx;
+    __syncthreads();
+    if (ty == 0 && i < rows) {
+      for (int w = 1; w < 8; ++w) mx = max(mx, red[w][tx]);
+      if (mx) atomicMax(eexp + i, exp_of_bits(mx));
+    }
+  } else {        // 8 rows, one warp each, lanes along k (coalesced)
+    const int64_t i = blockIdx.x * (int64_t)8 + ty;
+    if (i >= rows) return;
+    unsigned long long mx = 0;
+    for (int p = 0; p < 4; ++p)
+      if (A[p])
+        for (int k = k0 + tx; k < k1; k += 32) mx = max(mx, mag(A[p][i * lda + k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (tx == 0 && mx) atomicMax(eexp + i, exp_of_bits(mx));
+  }
+}
+
+// Column exponents of R(B) for a tall B (kq rows): column (q, jj) of R(B) holds column jj of
+// every plane of B, so its maximum is that of column jj over the four planes.  CTAs of 32
+// columns (lanes along jj, coalesced) x a K range, atomicMax into cexp[jj].
+__global__ void __launch_bounds__(256) oz_colexp_long_kernel(const double* b0, const double* b1, const double* b2,
+                                                             const double* b3, int64_t ldb, int kq, int nq, int kchunk,
+                                                             int* __restrict__ cexp) {
+  const double* B[4] = {b0, b1, b2, b3};
+  __shared__ unsigned long long red[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int jj = blockIdx.x * 32 + tx;
+  const int k0 = blockIdx.y * kchunk, k1 = min(kq, k0 + kchunk);
+  unsigned long long mx = 0;
+  if (jj < nq)
+    for (int p = 0; p < 4; ++p)
+      if (B[p])
+        for (int k = k0 + ty; k < k1; k += 8) mx = max(mx, abs_bits(B[p][(int64_t)k * ldb + jj]));
+  red[ty][tx] = mx;
+  __syncthreads();
+  if (ty == 0 && jj < nq) {
+    for (int w = 1; w < 8; ++w) mx = max(mx, red[w][tx]);
+    if (mx) atomicMax(cexp + jj, exp_of_bits(mx));
+  }
+}
+// fexp[j] of column j of R(B) from the column exponents of B (0 past 4 nq and for a zero column)
+__global__ void oz_colexp_expand_kernel(const int* __restrict__ cexp, int nq, int np, int* __restrict__ fexp) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= np) return;
+  const int e = j < 4 * nq ? cexp[j % nq] : 0;
+  fexp[j] = e < -4000 ? 0 : e;
+}
+__global__ void oz_clamp_exp_kernel(int* __restrict__ e, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n && e[i] < -4000) e[i] = 0;   // a zero row
+}
+
+// Slices of the columns c0 .. c0 + kw - 1 of R(B) for a tall B, 32 (c) x 32 (j) tiles through
+// shared memory: read along the columns jj of B (coalesced), written along c (K-major).
+__global__ void __launch_bounds__(256) oz_slice_b_long_kernel(const double* b0, const double* b1, const double* b2,
+                                                              const double* b3, int64_t ldb, int kq, int nq, int c0,
+                                                              int kw, const int* __restrict__ fexp,
+                                                              __nv_bfloat16* __restrict__ slices, int np) {
+  const double* B[4] = {b0, b1, b2, b3};
+  __shared__ double tile[32][33];
+  const int cb = blockIdx.x * 32, jb = blockIdx.y * 32, tx = threadIdx.x, ty = threadIdx.y;
+  for (int u = ty; u < 32; u += 8) tile[u][tx] = rb_val(B, ldb, kq, nq, jb + tx, c0 + cb + u);   // [c][j]
+  __syncthreads();
+  for (int u = ty; u < 32; u += 8) {
+    const int j = jb + u, c = cb + tx;
+    if (j >= np || c >= kw) continue;
+    int t[kS];
+    digits_d(tile[tx][u], fexp[j], t);
+#pragma unroll
+    for (int b = 0; b < kS; ++b) slices[((int64_t)b * np + j) * kw + c] = slice_bf16(t[b], b);
+  }
+}
+
+// C_q[i][jj] (+)= sum over z (in order) of the partial tiles part[z][i][q nq + jj]; the first
+// K chunk stores, the later ones add, so the result does not depend on the schedule.
+__global__ void oz_reduce_kernel(const double* __restrict__ part, int nz, int64_t zstride, int np, int64_t rows,
+                                 int nq, double* c0, double* c1, double* c2, double* c3, int64_t ldc, int first) {
+  double* C[4] = {c0, c1, c2, c3};
+  const int64_t tot = rows * 4 * nq;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / (4 * nq);
+    const int jg = (int)(e % (4 * nq)), q = jg / nq, jj = jg % nq;
+    double acc = 0.0;
+    for (int z = 0; z < nz; ++z) acc += part[z * zstride + i * np + jg];
+    C[q][i * ldc + jj] = first ? acc : C[q][i * ldc + jj] + acc;
   }
 }
 
 // ------------------------------------------------------------------------ the product
 struct OzParams {
   int64_t rows;        // valid rows of this chunk
-  int ksteps;          // kp / 16
+  int ksteps;          // K steps of 32 per CTA
+  int ksteps_total;    // K steps of the slices (CTA z takes steps z ksteps ..)
+  int64_t zstride;     // split K: CTA z stores its tile at c[0] + z zstride (a partial sum)
   int mc, np;          // slice row pitches of A (rows) and B (columns)
   int nv, nq;          // valid real columns (4 nq), quaternion columns
   int ct;
@@ -347,14 +508,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       uint32_t uses[kStages] = {0, 0};
       int slot = 0;
-      for (int ks = 0; ks < p.ksteps && !sh->abort; ++ks) {
+      const int k0 = blockIdx.z * p.ksteps, nks = min(p.ksteps, p.ksteps_total - k0);
+      for (int ks = 0; ks < nks && !sh->abort; ++ks) {
         if (uses[slot] > 0 && !oz_wait(&sh->empty[slot], (uses[slot] - 1) & 1, sh, p.status)) break;
         uint8_t* dst = sRing + slot * kStageBytes;
         mbar_expect_tx(&sh->full[slot], (uint32_t)kStageBytes);
         for (int a = 0; a < kS; ++a)
-          tma_load_2d(dst + a * kABox, &tA, ks * kBK, a * p.mc + ti * kBM, &sh->full[slot]);
+          tma_load_2d(dst + a * kABox, &tA, (k0 + ks) * kBK, a * p.mc + ti * kBM, &sh->full[slot]);
         for (int b = 0; b < kS; ++b)
-          tma_load_2d(dst + kS * kABox + b * kBBox, &tB, ks * kBK, b * p.np + tj * kBN, &sh->full[slot]);
+          tma_load_2d(dst + kS * kABox + b * kBBox, &tB, (k0 + ks) * kBK, b * p.np + tj * kBN, &sh->full[slot]);
         ++uses[slot];
         slot = (slot + 1) % kStages;
       }
@@ -367,7 +529,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t uses[kStages] = {0, 0};
       int slot = 0;
       const uint32_t r_base = smem_u32(sRing);
-      for (int ks = 0; ks < p.ksteps && !sh->abort; ++ks) {
+      const int nks = min(p.ksteps, p.ksteps_total - (int)blockIdx.z * p.ksteps);
+      for (int ks = 0; ks < nks && !sh->abort; ++ks) {
         if (!oz_wait(&sh->full[slot], uses[slot] & 1, sh, p.status)) break;
         tc_fence_after();
         const uint32_t stage = r_base + slot * kStageBytes;
@@ -450,7 +613,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int rr = 0; rr < 32; ++rr) {
             const int64_t ir = (int64_t)ti * kBM + lq * 32 + rr;
             if (ir >= p.rows) break;
-            p.c[q][ir * p.ldc + jj] = stg[rr * (kC + 1) + c];
+            p.c[q][blockIdx.z * p.zstride + ir * p.ldc + jj] = stg[rr * (kC + 1) + c];
           }
         }
       }
@@ -500,6 +663,38 @@ int64_t oz_chunk_rows(int64_t rows, int64_t kq_max, int64_t nq_max, size_t budge
   return std::min<int64_t>(mc, rup(rows, kBM));
 }
 
+namespace {
+
+cudaError_t set_attr() {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)oz_smem_bytes());
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  return cudaSuccess;
+}
+
+template <typename TA>
+void rowexp(const TA* const A[4], int64_t lda, int conj_a, int64_t rows, int64_t kq, int* ea, cudaStream_t st) {
+  if (conj_a)
+    oz_rowexp_kernel<TA><<<(unsigned)((rows + 31) / 32), 256, 0, st>>>(A[0], A[1], A[2], A[3], lda, 1, rows, (int)kq, ea);
+  else
+    oz_rowexp_kernel<TA><<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(A[0], A[1], A[2], A[3], lda, 0, rows, (int)kq, ea);
+  count_launch();
+}
+
+template <typename TA>
+void slice_a(const TA* const A[4], int64_t lda, int conj_a, int64_t rows, int64_t kq, int c0, int kw, int64_t mc,
+             const int* ea, __nv_bfloat16* sa, cudaStream_t st) {
+  oz_slice_a_kernel<TA><<<dim3((unsigned)((kw + 31) / 32), (unsigned)(rup(rows, kBM) / 32)), dim3(32, 8), 0, st>>>(
+      A[0], A[1], A[2], A[3], lda, conj_a, rows, (int)kq, c0, kw, mc, ea, sa);
+  count_launch();
+}
+
+}  // namespace
+
 cudaError_t launch_oz_gemm(const float* const A[4], int64_t lda, int conj_a, int64_t rows, int64_t kq,
                            const double* const B[4], int64_t ldb, int64_t nq, double* const C[4],
                            int64_t ldc, int ct, void* scratch, int64_t chunk_rows, int32_t* status,
@@ -513,14 +708,8 @@ cudaError_t launch_oz_gemm(const float* const A[4], int64_t lda, int conj_a, int
   __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(base + g.a_bytes);
   int* ea = reinterpret_cast<int*>(base + g.a_bytes + g.b_bytes);
   int* fb = reinterpret_cast<int*>(base + g.a_bytes + g.b_bytes + g.e_bytes);
-
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)oz_smem_bytes());
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  cudaError_t e = set_attr();
+  if (e != cudaSuccess) return e;
   CUtensorMap tA, tB;
   if (!make_map(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, sa, (uint64_t)g.kp, (uint64_t)(kS * g.mc),
                 (uint64_t)g.kp, kBK, kBM, CU_TENSOR_MAP_SWIZZLE_64B))
@@ -529,29 +718,22 @@ cudaError_t launch_oz_gemm(const float* const A[4], int64_t lda, int conj_a, int
                 (uint64_t)g.kp, kBK, kBN, CU_TENSOR_MAP_SWIZZLE_64B))
     return cudaErrorInvalidValue;
 
-  oz_slice_b_kernel<<<(unsigned)g.np, 256, 0, st>>>(B[0], B[1], B[2], B[3], ldb, (int)kq, (int)nq, (int)g.kp,
-                                                   sb, (int)g.np, fb);
+  oz_colexp_kernel<<<(unsigned)g.np, 256, 0, st>>>(B[0], B[1], B[2], B[3], ldb, (int)kq, (int)nq, fb);
   count_launch();
-  cudaError_t e = cudaGetLastError();
+  oz_slice_b_kernel<<<(unsigned)g.np, 256, 0, st>>>(B[0], B[1], B[2], B[3], ldb, (int)kq, (int)nq, 0, (int)g.kp,
+                                                   fb, sb, (int)g.np);
+  count_launch();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int64_t r0 = 0; r0 < rows; r0 += g.mc) {
     const int64_t rc = std::min<int64_t>(g.mc, rows - r0);
     const float* Ac[4];
     for (int p = 0; p < 4; ++p) Ac[p] = A[p] ? A[p] + (conj_a ? r0 : r0 * lda) : nullptr;
-    if (conj_a)
-      oz_rowexp_kernel<<<(unsigned)((rc + 31) / 32), 256, 0, st>>>(Ac[0], Ac[1], Ac[2], Ac[3], lda, 1, rc,
-                                                                       (int)kq, ea);
-    else
-      oz_rowexp_kernel<<<(unsigned)((rc + 7) / 8), 256, 0, st>>>(Ac[0], Ac[1], Ac[2], Ac[3], lda, 0, rc,
-                                                                  (int)kq, ea);
-    count_launch();
-    const int64_t mt = rup(rc, kBM);
-    oz_slice_a_kernel<<<dim3((unsigned)(g.kp / 32), (unsigned)(mt / 32)), dim3(32, 8), 0,
-                        st>>>(Ac[0], Ac[1], Ac[2], Ac[3], lda, conj_a, rc, (int)kq, (int)g.kp, g.mc, ea, sa);
-    count_launch();
+    rowexp<float>(Ac, lda, conj_a, rc, kq, ea, st);
+    slice_a<float>(Ac, lda, conj_a, rc, kq, 0, (int)g.kp, g.mc, ea, sa, st);
     OzParams prm{};
     prm.rows = rc;
-    prm.ksteps = (int)(g.kp / kBK);
+    prm.ksteps = prm.ksteps_total = (int)(g.kp / kBK);
     prm.mc = (int)g.mc;
     prm.np = (int)g.np;
     prm.nv = (int)(4 * nq);
@@ -559,9 +741,11 @@ cudaError_t launch_oz_gemm(const float* const A[4], int64_t lda, int conj_a, int
     prm.ct = ct;
     prm.ldc = ldc;
     for (int p = 0; p < 4; ++p) prm.c[p] = C[p] + (ct ? r0 : r0 * ldc);
+    prm.zstride = 0;
     prm.eexp = ea;
     prm.fexp = fb;
     prm.status = status;
+    const int64_t mt = rup(rc, kBM);
     oz_gemm_kernel<<<dim3((unsigned)(mt / kBM), (unsigned)(g.np / kBN)), kThreads, oz_smem_bytes(), st>>>(tA, tB,
                                                                                                        prm);
     count_launch();
@@ -569,6 +753,149 @@ cudaError_t launch_oz_gemm(const float* const A[4], int64_t lda, int conj_a, int
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+namespace {
+constexpr int kSplitSteps = kMaxK / kBK;   // K steps of 32 per CTA in the split form (exact levels)
+
+struct SplitGeom {
+  int64_t mp, np, kc, nz;   // padded rows and real columns, K chunk, partial tiles per chunk
+  size_t off_e, off_f, off_ce, off_part, off_sa, off_sb, total;
+};
+SplitGeom split_geom(int64_t rows, int64_t kq, int64_t nq, int64_t kc) {
+  SplitGeom g;
+  g.mp = rup(rows, kBM);
+  g.np = rup(4 * nq, kBN);
+  g.kc = kc;
+  g.nz = (kc / kBK + kSplitSteps - 1) / kSplitSteps;
+  size_t o = 0;
+  auto take = [&](size_t b) { const size_t r = o; o += (size_t)rup((int64_t)b, 256); return r; };
+  g.off_e = take(g.mp * 4);
+  g.off_f = take(g.np * 4);
+  g.off_ce = take(nq * 4);
+  g.off_part = take((size_t)g.nz * g.mp * g.np * 8);
+  g.off_sa = take((size_t)kS * g.mp * kc * 2);
+  g.off_sb = take((size_t)kS * g.np * kc * 2);
+  g.total = o;
+  (void)kq;
+  return g;
+}
+// largest K chunk (a multiple of 256, at most the whole K) whose scratch fits
+int64_t split_kc(int64_t rows, int64_t kq, int64_t nq, size_t bytes) {
+  int64_t lo = 0, hi = rup(4 * kq, 256) / 256;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (split_geom(rows, kq, nq, mid * 256).total <= bytes) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo * 256;
+}
+}  // namespace
+
+bool oz_splitk_supported(int64_t rows, int64_t nq, size_t scratch_bytes) {
+  if (rows < 1 || nq < 1 || rows > kMaxSplitRows || 4 * nq > kMaxK) return false;
+  return split_geom(rows, 1, nq, 256).total <= scratch_bytes;
+}
+
+size_t oz_splitk_bytes(int64_t rows, int64_t kq, int64_t nq) {
+  return split_geom(rows, kq, nq, rup(4 * kq, 256)).total;
+}
+
+template <typename TA>
+static cudaError_t splitk(const TA* const A[4], int64_t lda, int conj_a, int64_t rows, int64_t kq,
+                          const double* const B[4], int64_t ldb, int64_t nq, double* const C[4], int64_t ldc,
+                          void* scratch, size_t scratch_bytes, int32_t* status, cudaStream_t st) {
+  const int64_t kr = 4 * kq;
+  const int64_t kc = split_kc(rows, kq, nq, scratch_bytes);
+  if (kc < 256) return cudaErrorInvalidValue;
+  const SplitGeom g = split_geom(rows, kq, nq, kc);
+  uint8_t* base = static_cast<uint8_t*>(scratch);
+  int* ea = reinterpret_cast<int*>(base + g.off_e);
+  int* fb = reinterpret_cast<int*>(base + g.off_f);
+  int* ce = reinterpret_cast<int*>(base + g.off_ce);
+  double* part = reinterpret_cast<double*>(base + g.off_part);
+  __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(base + g.off_sa);
+  __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(base + g.off_sb);
+  cudaError_t e = set_attr();
+  if (e != cudaSuccess) return e;
+  CUtensorMap tA, tB;
+  if (!make_map(&tA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, sa, (uint64_t)kc, (uint64_t)(kS * g.mp), (uint64_t)kc,
+                kBK, kBM, CU_TENSOR_MAP_SWIZZLE_64B))
+    return cudaErrorInvalidValue;
+  if (!make_map(&tB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, sb, (uint64_t)kc, (uint64_t)(kS * g.np), (uint64_t)kc,
+                kBK, kBN, CU_TENSOR_MAP_SWIZZLE_64B))
+    return cudaErrorInvalidValue;
+  // exponents over the whole K (cleared to a large negative value, then raised by atomicMax)
+  e = cudaMemsetAsync(ea, 0x80, (size_t)g.mp * 4, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ce, 0x80, (size_t)nq * 4, st);
+  if (e != cudaSuccess) return e;
+  const int kcr = 512;   // K range of one exponent CTA
+  if (conj_a)
+    oz_rowexp_long_kernel<TA><<<dim3((unsigned)((rows + 31) / 32), (unsigned)((kq + kcr - 1) / kcr)), 256, 0, st>>>(
+        A[0], A[1], A[2], A[3], lda, 1, rows, (int)kq, kcr, ea);
+  else
+    oz_rowexp_long_kernel<TA><<<dim3((unsigned)((rows + 7) / 8), (unsigned)((kq + kcr - 1) / kcr)), 256, 0, st>>>(
+        A[0], A[1], A[2], A[3], lda, 0, rows, (int)kq, kcr, ea);
+  count_launch();
+  oz_clamp_exp_kernel<<<(unsigned)((g.mp + 255) / 256), 256, 0, st>>>(ea, g.mp);
+  count_launch();
+  oz_colexp_long_kernel<<<dim3((unsigned)((nq + 31) / 32), (unsigned)((kq + kcr - 1) / kcr)), 256, 0, st>>>(
+      B[0], B[1], B[2], B[3], ldb, (int)kq, (int)nq, kcr, ce);
+  count_launch();
+  oz_colexp_expand_kernel<<<(unsigned)((g.np + 255) / 256), 256, 0, st>>>(ce, (int)nq, (int)g.np, fb);
+  count_launch();
+  const int tiles_m = (int)(g.mp / kBM), tiles_n = (int)(g.np / kBN);
+  for (int64_t c0 = 0; c0 < kr; c0 += kc) {
+    const int kw = (int)std::min<int64_t>(kc, rup(kr - c0, kBK));
+    slice_a<TA>(A, lda, conj_a, rows, kq, (int)c0, (int)kc, g.mp, ea, sa, st);
+    oz_slice_b_long_kernel<<<dim3((unsigned)(kc / 32), (unsigned)(g.np / 32)), dim3(32, 8), 0, st>>>(
+        B[0], B[1], B[2], B[3], ldb, (int)kq, (int)nq, (int)c0, (int)kc, fb, sb, (int)g.np);
+    count_launch();
+    const int ksteps_total = kw / kBK;
+    const int nz = (ksteps_total + kSplitSteps - 1) / kSplitSteps;
+    OzParams prm{};
+    prm.rows = rows;
+    prm.ksteps = kSplitSteps;
+    prm.ksteps_total = ksteps_total;
+    prm.zstride = g.mp * g.np;
+    prm.mc = (int)g.mp;
+    prm.np = (int)g.np;
+    prm.nv = (int)g.np;   // the partial tile keeps every real column, q = 0
+    prm.nq = (int)g.np;
+    prm.ct = 0;
+    prm.ldc = g.np;
+    for (int p = 0; p < 4; ++p) prm.c[p] = part;
+    prm.eexp = ea;
+    prm.fexp = fb;
+    prm.status = status;
+    // the tiles of one K range are launched together, so they share its slices in L2
+    oz_gemm_kernel<<<dim3((unsigned)tiles_m, (unsigned)tiles_n, (unsigned)nz), kThreads, oz_smem_bytes(), st>>>(
+        tA, tB, prm);
+    count_launch();
+    oz_reduce_kernel<<<(unsigned)std::min<int64_t>((rows * 4 * nq + 255) / 256, 8 * kNumSMs), 256, 0, st>>>(
+        part, nz, g.mp * g.np, (int)g.np, rows, (int)nq, C[0], C[1], C[2], C[3], ldc, c0 == 0 ? 1 : 0);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_oz_gemm_splitk(const void* const A[4], int a_f64, int64_t lda, int conj_a, int64_t rows,
+                                  int64_t kq, const double* const B[4], int64_t ldb, int64_t nq, double* const C[4],
+                                  int64_t ldc, void* scratch, size_t scratch_bytes, int32_t* status,
+                                  cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  if (kq < 1 || !oz_splitk_supported(rows, nq, scratch_bytes) || !scratch) return cudaErrorInvalidValue;
+  if (reinterpret_cast<uintptr_t>(scratch) & 255) return cudaErrorInvalidValue;
+  if (a_f64) {
+    const double* Ad[4];
+    for (int p = 0; p < 4; ++p) Ad[p] = static_cast<const double*>(A[p]);
+    return splitk<double>(Ad, lda, conj_a, rows, kq, B, ldb, nq, C, ldc, scratch, scratch_bytes, status, st);
+  }
+  const float* Af[4];
+  for (int p = 0; p < 4; ++p) Af[p] = static_cast<const float*>(A[p]);
+  return splitk<float>(Af, lda, conj_a, rows, kq, B, ldb, nq, C, ldc, scratch, scratch_bytes, status, st);
 }
 
 }  // namespace qs

@@ -31,4 +31,16 @@ cudaError_t launch_oz_gemm(const float* const A[4], int64_t lda, int conj_a, int
                            int64_t ldc, int ct, void* scratch, int64_t chunk_rows, int32_t* status,
                            cudaStream_t st);
 
+// The same product for a long K (e.g. Psi H or the Gram T* T): each CTA sums the exact slice
+// products of a K range of at most 1536 into a partial tile, and the partial tiles are added
+// into C in a fixed order (deterministic).  A: FP32 or FP64 planes (a_f64).  op(A) has at most
+// 4096 rows; the slices of the largest K chunk that fits scratch_bytes are formed at a time.
+bool oz_splitk_supported(int64_t rows, int64_t nq, size_t scratch_bytes);
+// Scratch for the whole K in one chunk (fewer, larger launches).
+size_t oz_splitk_bytes(int64_t rows, int64_t kq, int64_t nq);
+cudaError_t launch_oz_gemm_splitk(const void* const A[4], int a_f64, int64_t lda, int conj_a, int64_t rows,
+                                  int64_t kq, const double* const B[4], int64_t ldb, int64_t nq, double* const C[4],
+                                  int64_t ldc, void* scratch, size_t scratch_bytes, int32_t* status,
+                                  cudaStream_t st);
+
 }  // namespace qs
