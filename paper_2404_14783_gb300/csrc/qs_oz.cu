@@ -55,6 +55,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "qs_df64.cuh"
 #include "qs_oz.cuh"
@@ -98,10 +99,28 @@ __device__ __forceinline__ int exp_of_bits(unsigned long long ab) {
   const int E = (int)(ab >> 52);
   return E == 0 ? 0 : E - 1022;
 }
-// Digits t_1..t_S of y = v 2^-e (|y| < 1): Y = y 2^48 rounded to an integer, then
-// t_a = Y / 2^(48 - 6a) rounded (half up) with the remainder carried on, so |t_1| <= 64 and
-// |t_a| <= 32 after; the part of y below 2^-48 is dropped (the slicing remainder).
-__device__ __forceinline__ void digits_d(double v, int e, int* t) {
+// x * 2^k in FP32 (exact unless the result leaves the normal range)
+__device__ __forceinline__ float scale2(float x, int k) {
+  if (k >= -126 && k <= 127) return x * __int_as_float((k + 127) << 23);
+  return ldexpf(x, k);
+}
+// Four base-64 digits of y (|y| <= 1, a multiple of 2^-24): t_a = rint(64 y_(a-1)),
+// y_a = 64 y_(a-1) - t_a, all exact in FP32; |t_1| <= 64, |t_a| <= 32 after, and the fourth
+// remainder is zero.
+__device__ __forceinline__ void digits4(float y, float* t) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    y *= 64.f;
+    const float r = rintf(y);
+    y -= r;
+    t[a] = r;
+  }
+}
+// Digits t_1..t_S (as FP32 integers) of y = v 2^-e (|y| < 1).  FP64 v: Y = y 2^48 rounded to
+// an integer from the bit pattern, split as Y = H 2^24 + L with L in [-2^23, 2^23) (so
+// |H| <= 2^24), and the four digits of H 2^-24 and of L 2^-24 taken in FP32 -- no FP64
+// arithmetic; the part of y below 2^-48 is dropped (the slicing remainder).
+__device__ __forceinline__ void digits(double v, int e, float* t) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const int E = (int)((b >> 52) & 0x7ff);
   long long Y = 0;
@@ -111,37 +130,41 @@ __device__ __forceinline__ void digits_d(double v, int e, int* t) {
     if (sh < 63) Y = (long long)((M + (1ull << (sh - 1))) >> sh);
     if (b >> 63) Y = -Y;
   }
-#pragma unroll
-  for (int a = 1; a <= kS; ++a) {
-    const int shift = 48 - kBeta * a;
-    const long long ta = shift > 0 ? (Y + (1ll << (shift - 1))) >> shift : Y;
-    Y -= ta << shift;
-    t[a - 1] = (int)ta;
-  }
+  int L = (int)(Y & 0xffffff);
+  if (L >= 0x800000) L -= 0x1000000;
+  const int H = (int)((Y - L) >> 24);
+  digits4((float)H * 0x1p-24f, t);
+  digits4((float)L * 0x1p-24f, t + 4);
 }
-__device__ __forceinline__ void digits(double v, int e, int* t) { digits_d(v, e, t); }
-// FP32 values: the same digits in FP32 arithmetic (exact: y has 24 significant bits)
-__device__ __forceinline__ void digits(float v, int e, int* t) {
-  float y = ldexpf(v, -e);
+// FP32 values: y has at most 24 significant bits below its own exponent, so its digits are
+// taken in FP32 directly (exact).
+__device__ __forceinline__ void digits(float v, int e, float* t) {
+  float y = scale2(v, -e);
 #pragma unroll
   for (int a = 0; a < kS; ++a) {
     y *= 64.f;
     const float r = rintf(y);
     y -= r;
-    t[a] = (int)r;
+    t[a] = r;
   }
 }
-__device__ __forceinline__ __nv_bfloat16 slice_bf16(int t, int a0) {   // t 2^-6 a0, exact
-  return __float2bfloat16_rn(ldexpf((float)t, -kBeta * a0));
+// t 2^-6 a0 as BF16 bits (|t| <= 64: exact, the low half of the FP32 pattern is zero)
+__device__ __forceinline__ uint16_t slice_bits(float t, int a0) {
+  return (uint16_t)(__float_as_uint(t * __int_as_float((127 - kBeta * a0) << 23)) >> 16);
 }
 
 // ------------------------------------------------------------------------ slicing of R(B)
 // Column exponents of R(B): one CTA per column j (np of them; j >= 4 nq get 0), the maximum
 // over all 4 kq rows.
-__device__ __forceinline__ double rb_val(const double* const* B, int64_t ldb, int kq, int nq, int j, int c) {
+// plane p of four (selected without a dynamically indexed local array)
+template <typename T>
+__device__ __forceinline__ T* pick(T* const (&P)[4], int p) {
+  return p == 0 ? P[0] : p == 1 ? P[1] : p == 2 ? P[2] : P[3];
+}
+__device__ __forceinline__ double rb_val(const double* const (&B)[4], int64_t ldb, int kq, int nq, int j, int c) {
   if (j >= 4 * nq || c >= 4 * kq) return 0.0;
   const int q = j / nq, jj = j % nq, pa = c / kq, k = c % kq;
-  const double* src = B[kRPlane[pa][q]];
+  const double* src = pick(B, kRPlane[pa][q]);
   return src ? kRSign[pa][q] * src[(int64_t)k * ldb + jj] : 0.0;
 }
 __global__ void __launch_bounds__(256) oz_colexp_kernel(const double* b0, const double* b1, const double* b2,
@@ -170,12 +193,13 @@ __global__ void __launch_bounds__(256) oz_slice_b_kernel(const double* b0, const
                                                          __nv_bfloat16* __restrict__ slices, int np) {
   const double* B[4] = {b0, b1, b2, b3};
   const int j = blockIdx.x, f = fexp[j];
+  uint16_t* out = reinterpret_cast<uint16_t*>(slices);
   for (int c = threadIdx.x; c < kw; c += blockDim.x) {
-    int t[kS];
-    digits_d(rb_val(B, ldb, kq, nq, j, c0 + c), f, t);
+    float t[kS];
+    digits(rb_val(B, ldb, kq, nq, j, c0 + c), f, t);
 #pragma unroll
     for (int b = 0; b < kS; ++b)   // u_b 2^-6(b-1): exact in BF16
-      slices[((int64_t)b * np + j) * kw + c] = slice_bf16(t[b], b);
+      out[((int64_t)b * np + j) * kw + c] = slice_bits(t[b], b);
   }
 }
 
@@ -226,54 +250,64 @@ __global__ void __launch_bounds__(256) oz_rowexp_kernel(const TA* a0, const TA* 
 }
 
 // Slices of the columns c0 .. c0 + kw - 1 of the real op(A) (rows x kw, K-major, zero padded
-// to mc rows and past 4 kq), one 32 x 32 tile per CTA of 32 x 8 threads: the tile is read in
-// the layout of A (row-major A: along k; A*: along i), transposed in shared memory, and
-// written along the columns.  The slicing steps are exact in the type of A.
+// to mc rows and past 4 kq; kw even), one tile of 32 rows x 64 columns per CTA of 32 x 8
+// threads: the tile is read in the layout of A (row-major A: along k; A*: along i), transposed
+// in shared memory, and written along the columns, two columns per thread (128-byte rows per
+// warp).  The slicing steps are exact in the type of A.
 template <typename TA>
 __global__ void __launch_bounds__(256) oz_slice_a_kernel(const TA* a0, const TA* a1, const TA* a2, const TA* a3,
                                                          int64_t lda, int conj_a, int64_t rows, int kq, int c0,
                                                          int kw, int64_t mc, const int* __restrict__ eexp,
                                                          __nv_bfloat16* __restrict__ slices) {
   const TA* A[4] = {a0, a1, a2, a3};
-  __shared__ TA tile[32][33];
+  __shared__ TA tile[32][65];   // [row][column]
   const int64_t i0 = (int64_t)blockIdx.y * 32;
-  const int cb = blockIdx.x * 32, tx = threadIdx.x, ty = threadIdx.y, kr = 4 * kq;
+  const int cb = blockIdx.x * 64, tx = threadIdx.x, ty = threadIdx.y, kr = 4 * kq;
   // column c of the real A: plane c / kq, index c % kq; A* negates the planes x, y, z
-  for (int u = ty; u < 32; u += 8) {
-    TA v = TA(0);
-    if (conj_a) {   // lanes along i
+  if (conj_a) {   // lanes along i
+    for (int u = ty; u < 64; u += 8) {
+      TA v = TA(0);
       const int64_t i = i0 + tx;
       const int c = c0 + cb + u;
       if (i < rows && c < kr && cb + u < kw) {
         const int p = c / kq, k = c % kq;
-        if (A[p]) v = (p ? TA(-1) : TA(1)) * A[p][(int64_t)k * lda + i];
+        const TA* src = pick(A, p);
+        if (src) v = (p ? TA(-1) : TA(1)) * src[(int64_t)k * lda + i];
       }
       tile[tx][u] = v;
-    } else {        // lanes along k
-      const int64_t i = i0 + u;
-      const int c = c0 + cb + tx;
-      if (i < rows && c < kr && cb + tx < kw) {
-        const int p = c / kq, k = c % kq;
-        if (A[p]) v = A[p][i * lda + k];
-      }
-      tile[u][tx] = v;
     }
+  } else {        // lanes along k
+    for (int u = ty; u < 32; u += 8)
+#pragma unroll
+      for (int h = 0; h < 64; h += 32) {
+        TA v = TA(0);
+        const int64_t i = i0 + u;
+        const int c = c0 + cb + h + tx;
+        if (i < rows && c < kr && cb + h + tx < kw) {
+          const int p = c / kq, k = c % kq;
+          const TA* src = pick(A, p);
+          if (src) v = src[i * lda + k];
+        }
+        tile[u][h + tx] = v;
+      }
   }
   __syncthreads();
+  uint32_t* out = reinterpret_cast<uint32_t*>(slices);
   for (int u = ty; u < 32; u += 8) {
     const int64_t i = i0 + u;
-    const int c = cb + tx;
+    const int c = cb + 2 * tx;
     if (i >= mc || c >= kw) continue;
-    int t[kS];
+    float t0[kS], t1[kS];
     if (i < rows) {
-      digits(tile[u][tx], eexp[i], t);
+      digits(tile[u][2 * tx], eexp[i], t0);
+      digits(tile[u][2 * tx + 1], eexp[i], t1);
     } else {
 #pragma unroll
-      for (int a = 0; a < kS; ++a) t[a] = 0;
+      for (int a = 0; a < kS; ++a) t0[a] = t1[a] = 0.f;
     }
 #pragma unroll
     for (int a = 0; a < kS; ++a)   // t_a 2^-6(a-1)
-      slices[((int64_t)a * mc + i) * kw + c] = slice_bf16(t[a], a);
+      out[(((int64_t)a * mc + i) * kw + c) >> 1] = (uint32_t)slice_bits(t0[a], a) | ((uint32_t)slice_bits(t1[a], a) << 16);
   }
 }
 
@@ -337,11 +371,13 @@ __global__ void __launch_bounds__(256) oz_colexp_long_kernel(const double* b0, c
     if (mx) atomicMax(cexp + jj, exp_of_bits(mx));
   }
 }
-// fexp[j] of column j of R(B) from the column exponents of B (0 past 4 nq and for a zero column)
-__global__ void oz_colexp_expand_kernel(const int* __restrict__ cexp, int nq, int np, int* __restrict__ fexp) {
+// fexp[j] of column j of R(B) from the column exponents of B, repeated over the reps column
+// blocks (0 past reps nq and for a zero column)
+__global__ void oz_colexp_expand_kernel(const int* __restrict__ cexp, int nq, int reps, int np,
+                                        int* __restrict__ fexp) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= np) return;
-  const int e = j < 4 * nq ? cexp[j % nq] : 0;
+  const int e = j < reps * nq ? cexp[j % nq] : 0;
   fexp[j] = e < -4000 ? 0 : e;
 }
 __global__ void oz_clamp_exp_kernel(int* __restrict__ e, int64_t n) {
@@ -349,24 +385,28 @@ __global__ void oz_clamp_exp_kernel(int* __restrict__ e, int64_t n) {
   if (i < n && e[i] < -4000) e[i] = 0;   // a zero row
 }
 
-// Slices of the columns c0 .. c0 + kw - 1 of R(B) for a tall B, 32 (c) x 32 (j) tiles through
-// shared memory: read along the columns jj of B (coalesced), written along c (K-major).
+// Slices of the columns c0 .. c0 + kw - 1 of R(B) for a tall B (kw even), 64 (c) x 32 (j)
+// tiles through shared memory: read along the columns jj of B (coalesced), written along c
+// (K-major), two values of c per thread (128-byte rows per warp).
 __global__ void __launch_bounds__(256) oz_slice_b_long_kernel(const double* b0, const double* b1, const double* b2,
                                                               const double* b3, int64_t ldb, int kq, int nq, int c0,
                                                               int kw, const int* __restrict__ fexp,
                                                               __nv_bfloat16* __restrict__ slices, int np) {
   const double* B[4] = {b0, b1, b2, b3};
-  __shared__ double tile[32][33];
-  const int cb = blockIdx.x * 32, jb = blockIdx.y * 32, tx = threadIdx.x, ty = threadIdx.y;
-  for (int u = ty; u < 32; u += 8) tile[u][tx] = rb_val(B, ldb, kq, nq, jb + tx, c0 + cb + u);   // [c][j]
+  __shared__ double tile[32][65];   // [j][c]
+  const int cb = blockIdx.x * 64, jb = blockIdx.y * 32, tx = threadIdx.x, ty = threadIdx.y;
+  for (int u = ty; u < 64; u += 8) tile[tx][u] = rb_val(B, ldb, kq, nq, jb + tx, c0 + cb + u);
   __syncthreads();
+  uint32_t* out = reinterpret_cast<uint32_t*>(slices);
   for (int u = ty; u < 32; u += 8) {
-    const int j = jb + u, c = cb + tx;
+    const int j = jb + u, c = cb + 2 * tx;
     if (j >= np || c >= kw) continue;
-    int t[kS];
-    digits_d(tile[tx][u], fexp[j], t);
+    float t0[kS], t1[kS];
+    digits(tile[u][2 * tx], fexp[j], t0);
+    digits(tile[u][2 * tx + 1], fexp[j], t1);
 #pragma unroll
-    for (int b = 0; b < kS; ++b) slices[((int64_t)b * np + j) * kw + c] = slice_bf16(t[b], b);
+    for (int b = 0; b < kS; ++b)
+      out[(((int64_t)b * np + j) * kw + c) >> 1] = (uint32_t)slice_bits(t0[b], b) | ((uint32_t)slice_bits(t1[b], b) << 16);
   }
 }
 
@@ -381,7 +421,8 @@ __global__ void oz_reduce_kernel(const double* __restrict__ part, int nz, int64_
     const int jg = (int)(e % (4 * nq)), q = jg / nq, jj = jg % nq;
     double acc = 0.0;
     for (int z = 0; z < nz; ++z) acc += part[z * zstride + i * np + jg];
-    C[q][i * ldc + jj] = first ? acc : C[q][i * ldc + jj] + acc;
+    double* cq = pick(C, q);
+    cq[i * ldc + jj] = first ? acc : cq[i * ldc + jj] + acc;
   }
 }
 
@@ -425,11 +466,6 @@ __device__ bool oz_wait(uint64_t* bar, uint32_t parity, OzShared* sh, int32_t* s
   }
 }
 
-// x * 2^k in FP32 (exact unless the result leaves the normal range)
-__device__ __forceinline__ float scale2(float x, int k) {
-  if (k >= -126 && k <= 127) return x * __int_as_float((k + 127) << 23);
-  return ldexpf(x, k);
-}
 // acc + v (v an FP32 value), compensated
 __device__ __forceinline__ df64 add_f(df64 acc, float v) {
   const float s = __fadd_rn(acc.hi, v);
@@ -597,7 +633,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int jg = tj * kBN + ch * kC + c;
           if (!row_ok || jg >= p.nv) continue;
           const int q = jg / p.nq, jj = jg % p.nq;
-          p.c[q][(int64_t)jj * p.ldc + i] = q ? -val[c] : val[c];
+          pick(p.c, q)[(int64_t)jj * p.ldc + i] = q ? -val[c] : val[c];
         }
       } else {
         // row-major: stage the warp's 32 rows x 32 columns in shared memory (the operand
@@ -610,10 +646,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int jg = tj * kBN + ch * kC + c;
           if (jg >= p.nv) continue;
           const int q = jg / p.nq, jj = jg % p.nq;
+          double* cq = pick(p.c, q);
           for (int rr = 0; rr < 32; ++rr) {
             const int64_t ir = (int64_t)ti * kBM + lq * 32 + rr;
             if (ir >= p.rows) break;
-            p.c[q][blockIdx.z * p.zstride + ir * p.ldc + jj] = stg[rr * (kC + 1) + c];
+            cq[blockIdx.z * p.zstride + ir * p.ldc + jj] = stg[rr * (kC + 1) + c];
           }
         }
       }
@@ -688,7 +725,7 @@ void rowexp(const TA* const A[4], int64_t lda, int conj_a, int64_t rows, int64_t
 template <typename TA>
 void slice_a(const TA* const A[4], int64_t lda, int conj_a, int64_t rows, int64_t kq, int c0, int kw, int64_t mc,
              const int* ea, __nv_bfloat16* sa, cudaStream_t st) {
-  oz_slice_a_kernel<TA><<<dim3((unsigned)((kw + 31) / 32), (unsigned)(rup(rows, kBM) / 32)), dim3(32, 8), 0, st>>>(
+  oz_slice_a_kernel<TA><<<dim3((unsigned)((kw + 63) / 64), (unsigned)(rup(rows, kBM) / 32)), dim3(32, 8), 0, st>>>(
       A[0], A[1], A[2], A[3], lda, conj_a, rows, (int)kq, c0, kw, mc, ea, sa);
   count_launch();
 }
@@ -825,30 +862,41 @@ static cudaError_t splitk(const TA* const A[4], int64_t lda, int conj_a, int64_t
   if (!make_map(&tB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, sb, (uint64_t)kc, (uint64_t)(kS * g.np), (uint64_t)kc,
                 kBK, kBN, CU_TENSOR_MAP_SWIZZLE_64B))
     return cudaErrorInvalidValue;
-  // exponents over the whole K (cleared to a large negative value, then raised by atomicMax)
-  e = cudaMemsetAsync(ea, 0x80, (size_t)g.mp * 4, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ce, 0x80, (size_t)nq * 4, st);
+  // exponents over the whole K (cleared to a large negative value, then raised by atomicMax);
+  // the K range of one exponent CTA gives at least ~600 CTAs
+  bool gram = std::is_same<TA, double>::value && conj_a && rows == nq && lda == ldb;   // op(A) = B*
+  for (int p = 0; p < 4; ++p) gram = gram && static_cast<const void*>(A[p]) == static_cast<const void*>(B[p]);
+  e = cudaMemsetAsync(ce, 0x80, (size_t)nq * 4, st);
+  if (e == cudaSuccess && !gram) e = cudaMemsetAsync(ea, 0x80, (size_t)g.mp * 4, st);
   if (e != cudaSuccess) return e;
-  const int kcr = 512;   // K range of one exponent CTA
-  if (conj_a)
-    oz_rowexp_long_kernel<TA><<<dim3((unsigned)((rows + 31) / 32), (unsigned)((kq + kcr - 1) / kcr)), 256, 0, st>>>(
-        A[0], A[1], A[2], A[3], lda, 1, rows, (int)kq, kcr, ea);
-  else
-    oz_rowexp_long_kernel<TA><<<dim3((unsigned)((rows + 7) / 8), (unsigned)((kq + kcr - 1) / kcr)), 256, 0, st>>>(
-        A[0], A[1], A[2], A[3], lda, 0, rows, (int)kq, kcr, ea);
+  auto kcr_for = [&](int64_t gx) { return (int)std::max<int64_t>(64, rup((kq * gx + 607) / 608, 64)); };
+  if (!gram) {
+    const int64_t gx = conj_a ? (rows + 31) / 32 : (rows + 7) / 8;
+    const int kcr = kcr_for(gx);
+    oz_rowexp_long_kernel<TA><<<dim3((unsigned)gx, (unsigned)((kq + kcr - 1) / kcr)), 256, 0, st>>>(
+        A[0], A[1], A[2], A[3], lda, conj_a, rows, (int)kq, kcr, ea);
+    count_launch();
+    oz_clamp_exp_kernel<<<(unsigned)((g.mp + 255) / 256), 256, 0, st>>>(ea, g.mp);
+    count_launch();
+  }
+  {
+    const int64_t gx = (nq + 31) / 32;
+    const int kcr = kcr_for(gx);
+    oz_colexp_long_kernel<<<dim3((unsigned)gx, (unsigned)((kq + kcr - 1) / kcr)), 256, 0, st>>>(
+        B[0], B[1], B[2], B[3], ldb, (int)kq, (int)nq, kcr, ce);
+    count_launch();
+  }
+  oz_colexp_expand_kernel<<<(unsigned)((g.np + 255) / 256), 256, 0, st>>>(ce, (int)nq, 4, (int)g.np, fb);
   count_launch();
-  oz_clamp_exp_kernel<<<(unsigned)((g.mp + 255) / 256), 256, 0, st>>>(ea, g.mp);
-  count_launch();
-  oz_colexp_long_kernel<<<dim3((unsigned)((nq + 31) / 32), (unsigned)((kq + kcr - 1) / kcr)), 256, 0, st>>>(
-      B[0], B[1], B[2], B[3], ldb, (int)kq, (int)nq, kcr, ce);
-  count_launch();
-  oz_colexp_expand_kernel<<<(unsigned)((g.np + 255) / 256), 256, 0, st>>>(ce, (int)nq, (int)g.np, fb);
-  count_launch();
+  if (gram) {   // the row exponents of B* are the column exponents of B
+    oz_colexp_expand_kernel<<<(unsigned)((g.mp + 255) / 256), 256, 0, st>>>(ce, (int)nq, 1, (int)g.mp, ea);
+    count_launch();
+  }
   const int tiles_m = (int)(g.mp / kBM), tiles_n = (int)(g.np / kBN);
   for (int64_t c0 = 0; c0 < kr; c0 += kc) {
     const int kw = (int)std::min<int64_t>(kc, rup(kr - c0, kBK));
     slice_a<TA>(A, lda, conj_a, rows, kq, (int)c0, (int)kc, g.mp, ea, sa, st);
-    oz_slice_b_long_kernel<<<dim3((unsigned)(kc / 32), (unsigned)(g.np / 32)), dim3(32, 8), 0, st>>>(
+    oz_slice_b_long_kernel<<<dim3((unsigned)(kc / 64), (unsigned)(g.np / 32)), dim3(32, 8), 0, st>>>(
         B[0], B[1], B[2], B[3], ldb, (int)kq, (int)nq, (int)c0, (int)kc, fb, sb, (int)g.np);
     count_launch();
     const int ksteps_total = kw / kBK;

@@ -20,9 +20,9 @@
 //   warp 0      TMA producer: A tile (FP32, 4 x 32 KB) and a 3-stage ring of BF16 operand
 //               chunks of Psi (128 rows x 64) and Omega^T (NS rows x 64), SW128 layout.
 //   warp 1      TMEM owner and MMA issuer (one elected thread).
-//   warps 2-5   converters: FP32 -> BF16 hi/lo in place (an 8-row group of 2 KB becomes a
+//   warps 2-9   converters: FP32 -> BF16 hi/lo in place (an 8-row group of 2 KB becomes a
 //               1 KB hi atom and a 1 KB lo atom, so the operand's 8-row stride is 2048 B).
-//   warps 6-9   epilogue: TMEM -> registers -> red.global.add.v4.f32 into Y and W (L2).
+//   warps 10-13 epilogue: TMEM -> registers -> red.global.add.v4.f32 into Y and W (L2).
 // TMEM (512 columns) is split into two halves used by alternating "waves": one W wave per
 // 128-row slice of Psi (W_q for q = 0..3, N = 64 columns each) and two Y waves (a pair of
 // output planes each, N = NS columns) -- or, when NS > 128, four single-plane Y waves with
@@ -51,7 +51,8 @@ constexpr int kBM = 128, kBN = 64;
 constexpr int kStages = 3;
 constexpr int kStageBytes = 32768;
 constexpr int kABytes = 4 * 32768;
-constexpr int kThreads = 320;
+constexpr int kConvWarps = 8;   // the conversion sits between the tiles' MMAs: two warps per scheduler
+constexpr int kThreads = 32 * (2 + kConvWarps + 4);
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 // Hamilton-product tables (Sec. 2).  Y = A Omega: output plane q, Omega plane b -> A plane a.
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_sketch_kernel(const __grid_
 
   if (threadIdx.x == 0) {
     mbar_init(&sh->a_full, 1);
-    mbar_init(&sh->a_ready, 4);
+    mbar_init(&sh->a_ready, kConvWarps);
     mbar_init(&sh->a_free, 1);
     for (int h = 0; h < 2; ++h) {
       mbar_init(&sh->h_full[h], 1);
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_sketch_kernel(const __grid_
       umma_commit(&sh->done);
       wait_bar(&sh->done, 0, sh, cur_status, true);
     }
-  } else if (warp >= 2 && warp <= 5) {
+  } else if (warp >= 2 && warp < 2 + kConvWarps) {
     // ------------------------------------------------------------ converters
     // An 8-row group of one plane (2 KB of FP32) is read by one warp as 128 float4 chunks
     // (lane l takes chunks l, l+32, l+64, l+96: half a warp per row, conflict free), then
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1) fused_sketch_kernel(const __grid_
     for (int t = blockIdx.x; t < ntiles && ok && !sh->abort; t += gridDim.x, ++t_local) {
       typename Src::PT p = bt.P(item_of(t));
       if (!wait_bar(&sh->a_full, t_local & 1, sh, p.status)) { ok = false; break; }
-      for (int gi = cw; gi < 64; gi += 4) {
+      for (int gi = cw; gi < 64; gi += kConvWarps) {
         const int plane = gi >> 4, grp = gi & 15;
         if (p.pure && plane == 0) continue;
         uint8_t* gb = sA + plane * 32768 + grp * 2048;
@@ -401,15 +402,17 @@ __global__ void __launch_bounds__(kThreads, 1) fused_sketch_kernel(const __grid_
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int c = lane + 32 * i, r = c >> 4, f = c & 15;
+          // hi = bf16(x) two at a time; hi in FP32 is the upper half of the pattern, so the
+          // remainders x - hi (exact) need no conversion back
           const float x[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
           uint32_t hw[2], lw[2];
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
-            const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * k]), h1 = __float2bfloat16_rn(x[2 * k + 1]);
-            const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * k] - __bfloat162float(h0));
-            const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * k + 1] - __bfloat162float(h1));
-            hw[k] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            lw[k] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * k], x[2 * k + 1]);
+            memcpy(&hw[k], &h, 4);
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(x[2 * k] - __uint_as_float(hw[k] << 16),
+                                                            x[2 * k + 1] - __uint_as_float(hw[k] & 0xffff0000u));
+            memcpy(&lw[k], &lo, 4);
           }
           const int off = r * 128 + ((((f >> 1) ^ r) & 7) << 4) + (f & 1) * 8;
           *reinterpret_cast<uint2*>(gb + off) = make_uint2(hw[0], hw[1]);
