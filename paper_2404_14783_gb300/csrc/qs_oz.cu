@@ -410,6 +410,49 @@ __global__ void __launch_bounds__(256) oz_slice_b_long_kernel(const double* b0, 
   }
 }
 
+// The same slices when one launch covers the whole K (c0 = 0, kw >= 4 kq, kq even), from the
+// planes of B: element (k, jj) of plane p sits in R(B) at row pa kq + k and column q nq + jj
+// with pa = p xor q, for q = 0..3, with the sign of block (pa, q); its column exponent is the
+// same for the four (that of column jj of B), so its digits are taken once and stored four
+// times (a sign change flips the BF16 sign bits).  64 (k) x 32 (jj) tiles of one plane per
+// CTA: read along jj (coalesced), written along k, two values of k per thread.  The padding
+// (columns of R(B) past 4 nq, rows past 4 kq) is cleared separately.
+__global__ void __launch_bounds__(256) oz_slice_b_planes_kernel(const double* b0, const double* b1, const double* b2,
+                                                                const double* b3, int64_t ldb, int kq, int nq, int kw,
+                                                                const int* __restrict__ fexp,
+                                                                __nv_bfloat16* __restrict__ slices, int np) {
+  const double* const B[4] = {b0, b1, b2, b3};
+  const int p = blockIdx.z;
+  const double* src = pick(B, p);
+  __shared__ double tile[32][65];   // [jj][k]
+  const int kb = blockIdx.x * 64, jb = blockIdx.y * 32, tx = threadIdx.x, ty = threadIdx.y;
+  for (int u = ty; u < 64; u += 8) {
+    const int k = kb + u, jj = jb + tx;
+    tile[tx][u] = (src && k < kq && jj < nq) ? src[(int64_t)k * ldb + jj] : 0.0;
+  }
+  __syncthreads();
+  uint32_t* out = reinterpret_cast<uint32_t*>(slices);
+  for (int u = ty; u < 32; u += 8) {
+    const int jj = jb + u, k = kb + 2 * tx;
+    if (jj >= nq || k >= kq) continue;   // kq even: k + 1 < kq as well
+    float t0[kS], t1[kS];
+    const int f = fexp[jj];
+    digits(tile[u][2 * tx], f, t0);
+    digits(tile[u][2 * tx + 1], f, t1);
+    uint32_t bits[kS];
+#pragma unroll
+    for (int b = 0; b < kS; ++b) bits[b] = (uint32_t)slice_bits(t0[b], b) | ((uint32_t)slice_bits(t1[b], b) << 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int pa = p ^ q;
+      const uint32_t flip = kRSign[pa][q] < 0 ? 0x80008000u : 0u;
+      const int64_t j = (int64_t)q * nq + jj, c = (int64_t)pa * kq + k;
+#pragma unroll
+      for (int b = 0; b < kS; ++b) out[(((int64_t)b * np + j) * kw + c) >> 1] = bits[b] ^ flip;
+    }
+  }
+}
+
 // C_q[i][jj] (+)= sum over z (in order) of the partial tiles part[z][i][q nq + jj]; the first
 // K chunk stores, the later ones add, so the result does not depend on the schedule.
 __global__ void oz_reduce_kernel(const double* __restrict__ part, int nz, int64_t zstride, int np, int64_t rows,
@@ -896,8 +939,25 @@ static cudaError_t splitk(const TA* const A[4], int64_t lda, int conj_a, int64_t
   for (int64_t c0 = 0; c0 < kr; c0 += kc) {
     const int kw = (int)std::min<int64_t>(kc, rup(kr - c0, kBK));
     slice_a<TA>(A, lda, conj_a, rows, kq, (int)c0, (int)kc, g.mp, ea, sa, st);
-    oz_slice_b_long_kernel<<<dim3((unsigned)(kc / 64), (unsigned)(g.np / 32)), dim3(32, 8), 0, st>>>(
-        B[0], B[1], B[2], B[3], ldb, (int)kq, (int)nq, (int)c0, (int)kc, fb, sb, (int)g.np);
+    if (c0 == 0 && kc >= kr && kq % 2 == 0) {
+      // whole K in one chunk: digits once per element of B, padding cleared by memsets
+      const size_t row_bytes = (size_t)kc * 2;
+      for (int b = 0; b < kS && g.np > 4 * nq; ++b) {
+        e = cudaMemsetAsync(reinterpret_cast<uint8_t*>(sb) + ((size_t)b * g.np + 4 * nq) * row_bytes, 0,
+                            (size_t)(g.np - 4 * nq) * row_bytes, st);
+        if (e != cudaSuccess) return e;
+      }
+      if (kc > kr) {
+        e = cudaMemset2DAsync(reinterpret_cast<uint8_t*>(sb) + (size_t)kr * 2, row_bytes, 0, (size_t)(kc - kr) * 2,
+                              (size_t)kS * g.np, st);
+        if (e != cudaSuccess) return e;
+      }
+      oz_slice_b_planes_kernel<<<dim3((unsigned)((kq + 63) / 64), (unsigned)((nq + 31) / 32), 4), dim3(32, 8), 0,
+                                 st>>>(B[0], B[1], B[2], B[3], ldb, (int)kq, (int)nq, (int)kc, fb, sb, (int)g.np);
+    } else {
+      oz_slice_b_long_kernel<<<dim3((unsigned)(kc / 64), (unsigned)(g.np / 32)), dim3(32, 8), 0, st>>>(
+          B[0], B[1], B[2], B[3], ldb, (int)kq, (int)nq, (int)c0, (int)kc, fb, sb, (int)g.np);
+    }
     count_launch();
     const int ksteps_total = kw / kBK;
     const int nz = (ksteps_total + kSplitSteps - 1) / kSplitSteps;
