@@ -736,8 +736,14 @@ def main():
     if "fp32" in res:
         clk = (res["clocks"] or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
         fp32_peak = N_SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+        # the SIMT sketch runs on 64 x 64 quaternion tiles: Y = A Omega pads s, W = Psi A pads l
+        pad = lambda v: -(-v // 64) * 64
+        m_, n_, s_, l_ = w["m"], w["n"], w["s"], w["l"]
+        issued32 = flops * (pad(m_) * pad(s_) * n_ + pad(l_) * pad(n_) * m_) / (m_ * n_ * (s_ + l_))
         out["fp32_path"] = {"sketch_ms": res["fp32"]["sketch_ms"], "reps": res["fp32"]["reps"],
                             "sketch_tflops": flops / (res["fp32"]["sketch_ms"] * 1e-3) / 1e12,
+                            "issued_tflops": issued32 / (res["fp32"]["sketch_ms"] * 1e-3) / 1e12,
+                            "frac_issued_of_fp32_peak": issued32 / (res["fp32"]["sketch_ms"] * 1e-3) / 1e12 / fp32_peak,
                             "fp32_alu_peak_tflops": fp32_peak,
                             "frac_of_fp32_peak": flops / (res["fp32"]["sketch_ms"] * 1e-3) / 1e12 / fp32_peak,
                             "final_rel_error": res["fp32"]["err"],
