@@ -98,8 +98,13 @@ typedef enum {
  *   DF64  : every Gram matrix, every s x s factorisation and product, H = Y D, P = Psi H and
  *           X = P^dagger W accumulate in double-float (an unevaluated sum of two FP32
  *           numbers, about 48 significant bits, on the FP32 pipes); H, X and the
- *           truncation factors are stored in FP64.  Agrees with FP64 to a few units of
- *           2^-48 times the conditioning of the step.
+ *           truncation factors are stored in FP64.  The tall products (T = Y R^-1, H = Y D,
+ *           P = Psi H, the Gram T* T, X) run on the tensor cores instead when 4 max(s, l)
+ *           <= 1536: each operand is cut into eight exact BF16 slices of 6 bits on per-row
+ *           and per-column power-of-two scales, the slice products up to level 9 are summed
+ *           exactly in FP32 and the levels are added in double-float -- the same accuracy
+ *           class.  Agrees with FP64 to a few units of 2^-48 times the conditioning of the
+ *           step.
  *   FP64  : the same steps in native FP64 arithmetic (FP32 inputs widened exactly);
  *           H and X stored in FP64.  GB300 runs FP64 at about 1/60 of its FP32 rate.
  *   MIXED : double-float by default, but a factorisation runs in FP32 when a kappa estimate
