@@ -33,9 +33,13 @@
 // (N = 256, 192, 128 or 64) per K step of 16 instead of 36 with N = 64, the A operand read
 // once per stack.
 //
-// Kernels: oz_slice_b (R(B), K-major slices, column exponents), oz_rowexp and oz_slice_a
-// (row exponents, slices of A through a shared-memory transpose so that both the reads of A
-// or A* and the writes of the slices are coalesced), and oz_gemm_kernel:
+// Kernels: oz_colexp / oz_slice_b (R(B), K-major slices, column exponents), oz_rowexp and
+// oz_slice_a (row exponents, slices of A through a shared-memory transpose so that both the
+// reads of A or A* and the writes of the slices are coalesced), their long-K forms
+// (exponents over K ranges by atomicMax, oz_slice_b_long by tiles, or oz_slice_b_planes when
+// one chunk covers K: the digits of each element of B once, stored as its four signed copies
+// in R(B)), oz_reduce_kernel (the split-K partial tiles added in K order), and
+// oz_gemm_kernel:
 //   one CTA per 128 x 64 tile of the real C; 320 threads;
 //   warp 0   TMA producer: per K step of 32, the 8 slices of the A tile (128 x 32) and of
 //            the B tile (64 x 32), 64-byte rows and swizzle, 96 KB per stage, 2 stages;
